@@ -1,0 +1,475 @@
+#!/usr/bin/env python3
+"""Benchmark of the counting-query hot path on GB300.
+
+Default workload ("random"): n = 40 categorical variables (arity 2-5),
+m = 100,000 instances sampled from a random DAG, and a batch of 10,000 queries
+of 2-6 variables drawn without replacement.  One step answers the whole batch
+(every full contingency table) with one graph launch of the persistent count
+kernel.  Printed as one JSON line:
+
+  value      queries/s, device-resident inputs and outputs (max over ranks);
+  e2e        the same through fc_count_batch with pinned host buffers
+             (planning, host-to-device descriptors, kernel, device-to-host tables);
+  per_query  the same queries issued as one launch each;
+  roofline   the count kernel's effective bytes/s against the measured peak;
+  cpu_baseline  the CPU oracle on a bounded sample, on this host's cores.
+
+Other workloads (--workload tiny|scores|pairs|support) print their own line.
+`--impl reference` times the CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import (CONFIGS, config_database, random_queries, score_queries,  # noqa: E402
+                       subset_queries, weighted_itemsets, zipf_item_probs, zipf_transaction_bitmaps)
+
+L2_BYTES = 129 * 2**20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", 0)), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workloads
+
+def make_workload(name: str):
+    """Seeded inputs of one workload (host arrays)."""
+    c = CONFIGS[name]
+    if name in ("tiny", "random"):
+        db = config_database(name)
+        queries = subset_queries(db.n, (1, 2, 3)) if name == "tiny" else \
+            random_queries(db.n, c["nq"], c["k"][0], c["k"][1], c["seed"])
+        return {"db": db, "queries": queries}
+    if name == "scores":
+        db = config_database(name)
+        child, parents = score_queries(db.n, c["nq"], c["pa"][0], c["pa"][1], c["seed"])
+        return {"db": db, "child": child, "parents": parents}
+    if name == "pairs":
+        return {"db": config_database(name)}
+    if name == "support":
+        bits = zipf_transaction_bitmaps(c["n_items"], c["m"], c["zipf_s"], c["mean_len"], c["seed"])
+        probs = zipf_item_probs(c["n_items"], c["zipf_s"], c["mean_len"])
+        sets = weighted_itemsets(c["n_items"], c["nq"], c["k"][0], c["k"][1], probs, c["seed"])
+        return {"bits": bits, "m": c["m"], "sets": sets}
+    raise ValueError(name)
+
+
+def describe(name: str, w) -> dict:
+    c = CONFIGS[name]
+    if name in ("tiny", "random"):
+        ks = [len(q) for q in w["queries"]]
+        return {"workload": f"{name}: n={w['db'].n} arity {c['arity'][0]}-{c['arity'][1]}, m={w['db'].m}, "
+                            f"{len(ks)} count queries of {min(ks)}-{max(ks)} variables",
+                "n": w["db"].n, "m": w["db"].m, "queries": len(ks)}
+    if name == "scores":
+        return {"workload": f"scores: n={w['db'].n}, m={w['db'].m}, {len(w['child'])} (child, parents) "
+                            f"queries, |parents| {c['pa'][0]}-{c['pa'][1]}, MDL and BDeu(ess=1)",
+                "n": w["db"].n, "m": w["db"].m, "queries": len(w["child"])}
+    if name == "pairs":
+        n = w["db"].n
+        return {"workload": f"pairs: n={n}, m={w['db'].m}, all {n * (n - 1) // 2} pairwise tables + MI",
+                "n": n, "m": w["db"].m, "sum_arity": int(w["db"].arities.sum())}
+    return {"workload": f"support: {len(w['bits'])} items, m={w['m']}, {len(w['sets'])} itemsets of "
+                        f"{c['k'][0]}-{c['k'][1]} items, supports + rule confidences",
+            "n_items": len(w["bits"]), "m": w["m"], "queries": len(w["sets"])}
+
+
+# ------------------------------------------------------------ CPU oracle arm
+
+def oracle_rate(name: str, w, seconds: float, cores: int):
+    """Units/s of the CPU oracle (as it stands) on a bounded sample."""
+    import oracle
+
+    units = 0
+    sample = ""
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        if name in ("tiny", "random", "scores"):
+            orc = oracle.DB(w["db"].D, w["db"].arities)
+            if name == "scores":
+                jobs = [(w["child"][q], w["parents"][q]) for q in range(len(w["child"]))]
+                def fn(j):
+                    orc.score(j[0], j[1], "mdl")
+                    return orc.score(j[0], j[1], "bdeu")
+            else:
+                jobs = w["queries"]
+                fn = orc.table
+            t0 = time.perf_counter()
+            i = 0
+            while time.perf_counter() - t0 < seconds:
+                chunk = jobs[i % len(jobs): i % len(jobs) + 4 * cores] or jobs[: 4 * cores]
+                list(ex.map(fn, chunk))
+                units += len(chunk)
+                i += len(chunk)
+            sample = f"{units} queries of the workload (in order, wrapping), {cores} threads"
+        elif name == "pairs":
+            orc = oracle.DB(w["db"].D, w["db"].arities)
+            n = w["db"].n
+            pairs = [(a, b) for a in range(n) for b in range(a + 1, n)]
+            ar = w["db"].arities
+            def fn(p):
+                t = orc.table(list(p))
+                return oracle.score_table(t, int(ar[p[0]]), int(ar[p[1]]), "mi")
+            t0 = time.perf_counter()
+            i = 0
+            while time.perf_counter() - t0 < seconds:
+                chunk = pairs[i: i + 4 * cores] or pairs[: 4 * cores]
+                list(ex.map(fn, chunk))
+                units += len(chunk)
+                i += len(chunk)
+            sample = f"{units} pair tables + MI by row scan, {cores} threads"
+        else:
+            bits, m, sets = w["bits"], w["m"], w["sets"]
+            def fn(s):
+                return oracle.support_rules(bits, m, s)
+            t0 = time.perf_counter()
+            i = 0
+            while time.perf_counter() - t0 < seconds:
+                chunk = sets[i: i + cores] or sets[:cores]
+                list(ex.map(fn, chunk))
+                units += len(chunk)
+                i += len(chunk)
+            sample = f"{units} itemsets (support + k leave-one-out supports) by transaction scan, {cores} threads"
+    dt = time.perf_counter() - t0
+    return units / dt, sample
+
+
+METRIC = "count queries/s (exact full contingency tables, batched persistent launch)"
+UNITS = {"tiny": "queries/s", "random": "queries/s", "scores": "queries/s", "pairs": "pairs/s",
+         "support": "itemsets/s"}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    w = make_workload(args.workload)
+    cores = os.cpu_count() or 1
+    rate, sample = oracle_rate(args.workload, w, args.ref_seconds, cores)
+    steps = []
+    for _ in range(args.warmup + args.steps):
+        steps.append(oracle_rate(args.workload, w, max(0.5, args.ref_seconds / 4), cores)[0])
+    value = statistics.median(steps[args.warmup:]) if args.steps else rate
+    unit = UNITS[args.workload]
+    line = {"impl": "reference", "metric": METRIC if args.workload == "random" else f"{args.workload} {unit}",
+            "value": value, "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64/f64",
+            "data": "synthetic (seeded)", "config": describe(args.workload, w),
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank: int, world: int):
+    import torch
+
+    import paper_1804_04640_gb300 as fc
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    fc.load_library(build_if_missing=True)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    name = args.workload
+    w = make_workload(name)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    hbm, bf16, bf16_sus, peak_src = peaks()
+
+    # ---- set up the plan (device-resident inputs) and the e2e call
+    per_query = None
+    if name in ("tiny", "random"):
+        db, queries = w["db"], w["queries"]
+        ctx = fc.fc_load(db.D, db.arities)
+        if args.autotune:
+            fc.fc_autotune(ctx)
+        off, flat = fc.pack_lists(queries)
+        plan = fc.fc_plan_count(ctx, off, flat)
+        toff = fc.fc_plan_table_offsets(plan)
+        outs = (torch.empty(int(toff[-1]), dtype=torch.int32, device="cuda"),)
+        units = len(queries)
+        alg_bytes = sum(len(q) for q in queries) * db.m + 4 * int(toff[-1])
+        pinned = torch.empty(int(toff[-1]), dtype=torch.int32).pin_memory()
+        h2d = fc.fc_plan_size(plan, 5) + 4 * (len(off) + len(flat))
+        d2h = 4 * int(toff[-1])
+
+        def e2e_call():
+            fc.fc_count_batch(ctx, off, flat, toff, out=pinned)
+
+        if name == "random":
+            nper = min(args.per_query, len(queries))
+            per_plans = []
+            pq_outs = []
+            for q in queries[:nper]:
+                o1, f1 = fc.pack_lists([q])
+                p1 = fc.fc_plan_count(ctx, o1, f1)
+                per_plans.append(p1)
+                pq_outs.append(torch.empty(max(fc.fc_plan_size(p1, 0), 1), dtype=torch.int32, device="cuda"))
+            per_query = (per_plans, pq_outs)
+        strategies = np.bincount(fc.fc_plan_strategies(plan), minlength=4).tolist()
+    elif name == "scores":
+        db = w["db"]
+        ctx = fc.fc_load(db.D, db.arities)
+        if args.autotune:
+            fc.fc_autotune(ctx)
+        po, pa = fc.pack_lists(w["parents"])
+        plan = fc.fc_plan_score(ctx, w["child"], po, pa, "bdeu", 1.0)
+        outs = (torch.empty(len(w["child"]), dtype=torch.float32, device="cuda"),)
+        units = len(w["child"])
+        alg_bytes = (len(pa) + units) * db.m
+        pinned = torch.empty(units, dtype=torch.float32).pin_memory()
+        h2d = fc.fc_plan_size(plan, 5) + 4 * (units + len(po) + len(pa))
+        d2h = 4 * units
+
+        def e2e_call():
+            fc.fc_score_batch(ctx, w["child"], po, pa, "bdeu", 1.0, out=pinned)
+        strategies = np.bincount(fc.fc_plan_strategies(plan), minlength=4).tolist()
+    elif name == "pairs":
+        db = w["db"]
+        ctx = fc.fc_load(db.D, db.arities)
+        plan = fc.fc_plan_pairs(ctx)
+        outs = (torch.empty(fc.fc_plan_size(plan, 0), dtype=torch.int32, device="cuda"),
+                torch.empty(fc.fc_plan_size(plan, 1), dtype=torch.float32, device="cuda"))
+        units = fc.fc_plan_size(plan, 1)
+        R = int(db.arities.sum())
+        alg_flops = R * (R + 1) // 2 * 2 * db.m
+        pin_t = torch.empty(outs[0].numel(), dtype=torch.int32).pin_memory()
+        pin_m = torch.empty(outs[1].numel(), dtype=torch.float32).pin_memory()
+        h2d = 0
+        d2h = 4 * (outs[0].numel() + outs[1].numel())
+
+        def e2e_call():
+            fc.load_library().fc_pairs_all(ctx.ptr, fc._ptr(pin_t), fc._ptr(pin_m))
+        strategies = None
+    else:
+        ctx = fc.fc_load_bits(w["bits"], w["m"])
+        so, it = fc.pack_lists(w["sets"])
+        plan = fc.fc_plan_support(ctx, so, it)
+        outs = (torch.empty(len(w["sets"]), dtype=torch.int32, device="cuda"),
+                torch.empty(len(it), dtype=torch.int32, device="cuda"),
+                torch.empty(len(it), dtype=torch.float32, device="cuda"))
+        units = len(w["sets"])
+        alg_bytes = int(len(it)) * (w["m"] // 8)
+        pins = tuple(torch.empty(o.numel(), dtype=o.dtype).pin_memory() for o in outs)
+        h2d = fc.fc_plan_size(plan, 5)
+        d2h = sum(4 * o.numel() for o in outs)
+
+        def e2e_call():
+            fc.fc_support_batch(ctx, so, it, out=pins)
+        strategies = None
+
+    def step():
+        fc.fc_plan_run(plan, *outs, stream=stream)
+
+    # ---- warm-up (also captures the graph)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        stream.wait_stream(torch.cuda.current_stream())
+        step()
+    torch.cuda.synchronize()
+    fc.fc_sync(ctx, stream)
+
+    # ---- timed region: K steps, L2 flushed between steps, events on the launch stream
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(dev) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i)
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        barrier()
+        times = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    fc.fc_sync(ctx, stream)
+    ms = float(np.mean(times))
+    total_ms = float(np.sum(times))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = units * world * args.steps / (total_ms / 1e3)
+
+    # ---- per-query launches (same kernel, one launch per query)
+    pq = None
+    if per_query is not None:
+        plans, pouts = per_query
+        for p1, o in zip(plans, pouts):      # warm-up / capture
+            fc.fc_plan_run(p1, o, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for p1, o in zip(plans, pouts):
+            fc.fc_plan_run(p1, o, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pq_ms = e0.elapsed_time(e1)
+        pq = {"value": len(plans) / (pq_ms / 1e3), "unit": "queries/s", "queries": len(plans),
+              "launches": len(plans)}
+
+    # ---- end to end through the host-buffer entry point
+    for _ in range(2):
+        e2e_call()
+    e2e_t = []
+    for _ in range(max(3, min(args.steps, 10))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_call()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = float(np.median(e2e_t))
+
+    # ---- roofline of the dominant kernel
+    if name == "pairs":
+        achieved = alg_flops / (ms / 1e3) / 1e12
+        fp8_peak = bf16 * 2.0
+        roof = {"bound": "tensor", "achieved": achieved, "peak": fp8_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp8_peak, "traffic": None,
+                "peak_source": f"{peak_src} bf16 burst x 2 (nominal fp8/bf16 ratio)"}
+    else:
+        achieved = alg_bytes / (ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "peak_source": f"{peak_src} hbm_gbs"}
+
+    line = None
+    if rank == 0:
+        cfg = describe(name, w)
+        cfg["l2"] = "flushed between timed steps (256 MiB write)"
+        if strategies is not None:
+            cfg["strategies"] = dict(zip(["bitmap", "hist", "gatomic", "sort"], strategies))
+        cores = os.cpu_count() or 1
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            rate, sample = oracle_rate(name, w, args.cpu_seconds, cores)
+            cpu = {"value": rate, "unit": UNITS[name], "cores": cores, "kind": "oracle", "sample": sample}
+        line = {
+            "metric": METRIC if name == "random" else f"{name}: {UNITS[name]}",
+            "value": value, "unit": UNITS[name], "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"pairs": "e4m3 one-hot x f32 accumulate -> int32"}.get(name, "u8/int32"),
+            "data": "synthetic (seeded random-DAG samples)", "config": cfg,
+            "e2e": {"value": units / e2e_s, "unit": UNITS[name], "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": args.steps * (2 if name == "pairs" else 1),
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
+        }
+        if pq is not None:
+            line["per_query"] = pq
+            line["batched_over_per_query"] = value / world / pq["value"]
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="random", choices=list(CONFIGS))
+    ap.add_argument("--per-query", type=int, default=1000, help="queries timed with one launch each")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

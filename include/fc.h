@@ -1,0 +1,268 @@
+/*
+ * fc.h -- C ABI of libfc, exact counting queries over a complete categorical
+ * database on one GB300 GPU (sm_103a).
+ *
+ * The operations follow "Fast Counting in Machine Learning Applications"
+ * (Karan, Eichhorn, Hurlburt, Iraci, Zola; UAI 2018):
+ *   - database D of n categorical variables X_i with arity r_i and m complete
+ *     instances (Sec. 2);
+ *   - counting query Count((X_a = x_a) and ...) and queries with shared
+ *     context, which produce every count N_ijk of a variable set (Sec. 2, 3.1);
+ *   - reduction of the counts by an associative, commutative operator such
+ *     as the log-likelihood of Eq. 1 (Sec. 3.1, Fig. 2);
+ *   - support and confidence of association rules over binary transaction
+ *     data (Sec. 4.3).
+ *
+ * Conventions (all calls):
+ *   - States are stored 0-based, one uint8 per value, so r_i <= 255 (the paper
+ *     numbers states 1..r_i).
+ *   - A table over the ordered variable list (v_0, ..., v_{k-1}) is a dense
+ *     int32 array of prod(r_{v_t}) cells, row-major with the LAST variable
+ *     varying fastest: cell((s_0..s_{k-1})) = ((s_0 r_1 + s_1) r_2 + ...) + s_{k-1}.
+ *     For a (child, parents) query the list is (parents..., child), so the
+ *     q_i parent configurations are rows j and the r_i child states are
+ *     columns k: N_ijk = table[j * r_i + k] (Eq. 1's indexing).
+ *   - Counts are exact int32; m must be < 2^31.  A table may hold at most
+ *     2^31 - 1 cells.
+ *   - Unless stated otherwise pointers are HOST pointers, calls are
+ *     synchronous and the caller keeps ownership of every buffer it passes.
+ *   - Every call returns FC_OK (0) or a negative FC_ERR_* code and then sets a
+ *     thread-local message readable with fc_last_error().  On error no output
+ *     is written, except the output buffers of batch calls, whose contents
+ *     are then unspecified.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef FC_H
+#define FC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FC_OK = 0,
+    FC_ERR_ARG = -1,      /* null pointer, bad size, variable out of range, duplicate variable */
+    FC_ERR_RANGE = -2,    /* a stored state is >= its arity; m out of range */
+    FC_ERR_SIZE = -3,     /* a table or an output is too large */
+    FC_ERR_OOM = -4,      /* device or host allocation failed */
+    FC_ERR_CUDA = -5,     /* a CUDA runtime call failed */
+    FC_ERR_TIMEOUT = -6,  /* a bounded device-side wait ran out; the context stays usable */
+    FC_ERR_STATE = -7     /* call does not apply to this context or plan */
+};
+
+enum { FC_COL_MAJOR = 0, FC_ROW_MAJOR = 1 };   /* layout of D in fc_load */
+enum { FC_HOST = 0, FC_DEVICE = 1 };           /* where an input pointer lives */
+
+/* Score kinds for fc_score_batch.  All scores reduce the stream of non-zero
+ * counts (N_ijk, N_ij) of one (child, parents) query (Sec. 3.1).
+ *   FC_LL   Eq. 1 with log base 2 (Fig. 2): sum N_ijk log2(N_ijk / N_ij).
+ *   FC_MDL  -LL + (log2 m / 2) (r_i - 1) q_i, q_i = prod of parent arities
+ *           (Sec. 4.2 names MDL; this is the reading the library implements).
+ *   FC_BDEU sum_j [lgamma(a_j) - lgamma(a_j + N_ij)]
+ *           + sum_jk [lgamma(a_jk + N_ijk) - lgamma(a_jk)], a_j = ess / q_i,
+ *           a_jk = ess / (r_i q_i), natural log, sums over non-zero counts
+ *           (Sec. 3.1 and 4.2 name the Dirichlet-prior score).
+ *   FC_MI   mutual information in bits between the child and the joint
+ *           parent configuration (Sec. 1 names MI). */
+enum { FC_LL = 0, FC_MDL = 1, FC_BDEU = 2, FC_MI = 3 };
+
+/* Counting strategies (option "strategy"; FC_STRAT_AUTO lets the planner
+ * choose per query). */
+enum {
+    FC_STRAT_AUTO = -1,
+    FC_STRAT_BITMAP = 0,  /* Sec. 3.2, Alg. 1: AND + popcount DFS over per-state bitmaps */
+    FC_STRAT_HIST = 1,    /* mixed-radix key per instance into a shared-memory table (Sec. 3.3's partitions as keys) */
+    FC_STRAT_GATOMIC = 2, /* mixed-radix key into the output table in global memory */
+    FC_STRAT_SORT = 3     /* mixed-radix key, device radix sort, run-length (Sec. 3.3: partitions are runs of equal keys) */
+};
+
+typedef struct fc_ctx fc_ctx;
+typedef struct fc_plan fc_plan;
+
+/* ---------------------------------------------------------------- loading */
+
+/* Load a complete categorical database (Sec. 2) onto the current CUDA device.
+ *   D       n * m uint8 states, 0-based.  layout FC_COL_MAJOR: D[i * m + p] is
+ *           X_i in instance p (the paper's column D_i); FC_ROW_MAJOR:
+ *           D[p * n + i].  `where` says whether D is a host or a device pointer.
+ *   arities n int32 values in 1..255 (host).
+ * The context copies D (the caller keeps ownership), builds per-variable
+ * per-state bitmaps of m bits (Sec. 3.2, Fig. 1a), per-state marginal counts
+ * and per-variable entropies (used to order the DFS of Alg. 1).
+ * Errors: FC_ERR_ARG (null, n < 1, m < 1, arity outside 1..255),
+ * FC_ERR_RANGE (m >= 2^31, or a state >= its arity), FC_ERR_OOM, FC_ERR_CUDA. */
+int fc_load(fc_ctx **out, const uint8_t *D, int32_t n, int64_t m, const int32_t *arities,
+            int32_t layout, int32_t where);
+
+/* Load binary transaction data for association-rule queries (Sec. 4.3).
+ *   bitmaps n_items rows of ceil(m / 64) uint64 words; bit p % 64 of word
+ *           p / 64 of row i is set when transaction p holds item i.
+ * Bits at positions >= m are ignored.  Only fc_support_batch and
+ * fc_plan_support apply to such a context.
+ * Errors: FC_ERR_ARG, FC_ERR_RANGE (m >= 2^31), FC_ERR_OOM, FC_ERR_CUDA. */
+int fc_load_bits(fc_ctx **out, const uint64_t *bitmaps, int32_t n_items, int64_t m, int32_t where);
+
+/* Release a context and all device memory it owns.  Plans made from it must
+ * be freed first.  Null is ignored. */
+void fc_free(fc_ctx *ctx);
+
+/* Basic facts about a context: key 0 = n (variables or items), 1 = m,
+ * 2 = sum of arities, 3 = device ordinal.  Returns -1 for a bad key. */
+int64_t fc_info(const fc_ctx *ctx, int32_t key);
+
+/* Per-state marginal counts: out[state_offset(i) + s] = Count(X_i = s), with
+ * state_offset(i) = sum of the arities of X_0..X_{i-1} (host buffer of
+ * fc_info(ctx, 2) int64). */
+int fc_marginals(const fc_ctx *ctx, int64_t *out);
+
+/* ------------------------------------------------------- counting queries */
+
+/* Full contingency table of one variable list (Sec. 2: all counts of the
+ * query with shared context over vars[0..k-1]).
+ *   vars   k distinct variable ids (k = 0 gives the single cell m).
+ *   table  prod(r_{vars[t]}) int32 cells, layout as described above.
+ * Errors: FC_ERR_ARG (bad or duplicate variable), FC_ERR_SIZE, FC_ERR_STATE,
+ * FC_ERR_CUDA, FC_ERR_TIMEOUT. */
+int fc_count(fc_ctx *ctx, const int32_t *vars, int32_t k, int32_t *table);
+
+/* Count of one assignment, Count((X_vars[0] = states[0]) and ...) (Sec. 2 and
+ * the specific-assignment variant at the end of Sec. 3.3).  *count receives
+ * the number of instances that match every condition.  A state outside its
+ * variable's arity matches nothing (count 0). */
+int fc_count_assignment(fc_ctx *ctx, const int32_t *vars, const int32_t *states, int32_t k,
+                        int64_t *count);
+
+/* Batch of nq tables in one launch.  Query q has variables
+ * vars[var_off[q] .. var_off[q+1]) and its table starts at cell table_off[q]
+ * of `tables`; table_off is non-decreasing with
+ * table_off[q+1] - table_off[q] >= cells of query q.  Pass table_off = NULL
+ * to pack the tables back to back in query order. */
+int fc_count_batch(fc_ctx *ctx, int32_t nq, const int32_t *var_off, const int32_t *vars,
+                   const int64_t *table_off, int32_t *tables);
+
+/* Scores of nq (child, parents) queries (Sec. 3.1, Eq. 1; kinds above).
+ * Query q scores child[q] given parents[par_off[q] .. par_off[q+1]); the
+ * child must not be among its parents.  ess is the BDeu equivalent sample
+ * size (ignored by the other kinds).  scores: nq float (FP32 result; BDeu is
+ * accumulated in FP64 on the device). */
+int fc_score_batch(fc_ctx *ctx, int32_t nq, const int32_t *child, const int32_t *par_off,
+                   const int32_t *parents, int32_t kind, double ess, float *scores);
+
+/* All pairwise tables and their mutual information (the one-hot
+ * co-occurrence product: for variables a < b the table over (a, b) is one
+ * block of A^T A, A the m x sum(r) one-hot matrix of D; each table is the
+ * Sec. 2 table of the pair).
+ *   pair_tables  NULL, or the tables of all pairs a < b in lexicographic order,
+ *                packed back to back (r_a * r_b cells each, b fastest).
+ *   mi           NULL, or n(n-1)/2 floats, MI in bits of each pair.
+ * Errors: FC_ERR_STATE for a transaction context, FC_ERR_SIZE. */
+int fc_pairs_all(fc_ctx *ctx, int32_t *pair_tables, float *mi);
+
+/* Number of int32 cells fc_pairs_all writes to pair_tables. */
+int64_t fc_pairs_cells(const fc_ctx *ctx);
+
+/* Support and rule confidence of nq itemsets (Sec. 4.3; specific-assignment
+ * queries with every item in state 1).  Itemset q is
+ * items[set_off[q] .. set_off[q+1]) (distinct items).  Outputs:
+ *   support[q]               supp(S), the transactions holding every item;
+ *   sub_support[set_off[q]+t] supp(S without its t-th item);
+ *   confidence[set_off[q]+t]  supp(S) / supp(S without item t), the confidence
+ *                            of (S without item t) => item t; 0 when the
+ *                            denominator is 0.
+ * sub_support and confidence may be NULL.  Applies to fc_load_bits contexts. */
+int fc_support_batch(fc_ctx *ctx, int32_t nq, const int32_t *set_off, const int32_t *items,
+                     int32_t *support, int32_t *sub_support, float *confidence);
+
+/* ------------------------------------------- plans: device-resident batches
+ *
+ * A plan validates a batch once, picks a strategy per query, uploads the
+ * descriptors and keeps its scratch; fc_plan_run then executes the whole
+ * batch as one graph launch on a stream, reading only device memory.  Plans
+ * are how a caller keeps inputs and outputs resident in HBM. */
+
+/* Plan of a count batch (arguments as fc_count_batch, table_off may be NULL). */
+int fc_plan_count(fc_ctx *ctx, int32_t nq, const int32_t *var_off, const int32_t *vars,
+                  const int64_t *table_off, fc_plan **out);
+
+/* Plan of a score batch (arguments as fc_score_batch). */
+int fc_plan_score(fc_ctx *ctx, int32_t nq, const int32_t *child, const int32_t *par_off,
+                  const int32_t *parents, int32_t kind, double ess, fc_plan **out);
+
+/* Plan of a support batch (arguments as fc_support_batch). */
+int fc_plan_support(fc_ctx *ctx, int32_t nq, const int32_t *set_off, const int32_t *items,
+                    fc_plan **out);
+
+/* Plan of the all-pairs computation (fc_pairs_all). */
+int fc_plan_pairs(fc_ctx *ctx, fc_plan **out);
+
+/* Sizes of a plan's outputs: key 0 = int32 cells of the table output (count and
+ * pairs plans), 1 = float scores / MI values, 2 = int32 supports, 3 = entries of
+ * sub_support / confidence, 4 = number of queries, 5 = bytes of descriptors the
+ * plan copied to the device.  Returns -1 for a bad key. */
+int64_t fc_plan_size(const fc_plan *plan, int32_t key);
+
+/* Table offsets chosen by a count plan (nq + 1 int64, host buffer). */
+int fc_plan_table_offsets(const fc_plan *plan, int64_t *table_off);
+
+/* Strategy the plan chose for each query (nq int32, FC_STRAT_* values). */
+int fc_plan_strategies(const fc_plan *plan, int32_t *strategy);
+
+/* Run a plan asynchronously on `stream` (a cudaStream_t; NULL = the context's
+ * own stream).  Outputs are DEVICE pointers on the context's device:
+ *   count plan:   out0 = tables (int32);
+ *   score plan:   out0 = scores (float);
+ *   pairs plan:   out0 = pair tables (int32, may be NULL), out1 = MI (float, may be NULL);
+ *   support plan: out0 = support, out1 = sub_support (may be NULL),
+ *                 out2 = confidence (float, may be NULL).
+ * The first run with a given (outputs, stream) captures a CUDA graph; later
+ * runs replay it.  Runs of one plan must not overlap in time.  Device-side
+ * errors (FC_ERR_TIMEOUT) are reported by fc_sync(). */
+int fc_plan_run(fc_plan *plan, void *out0, void *out1, void *out2, void *stream);
+
+/* Release a plan (waits for its runs to finish). */
+void fc_plan_free(fc_plan *plan);
+
+/* Wait for the context's stream, and `stream` when not NULL, then report and
+ * clear the device status word: FC_OK or FC_ERR_TIMEOUT. */
+int fc_sync(fc_ctx *ctx, void *stream);
+
+/* ------------------------------------------------------- options, errors */
+
+/* Set a tuning option; returns FC_ERR_ARG for an unknown key or bad value.
+ *   "strategy"          FC_STRAT_* forced for every query (default AUTO)
+ *   "smem_cells"        int32 cells of the shared-memory table area per CTA
+ *   "threads"           threads per CTA of the count kernel (multiple of 32)
+ *   "ctas_per_sm"       resident CTAs per SM the count kernel is sized for
+ *   "hist_copies"       max copies of a shared-memory table (contention)
+ *   "min_part_rows"     smallest row range one work item covers
+ *   "pair_chunk_rows"   rows accumulated in FP32 tensor memory before the
+ *                       all-pairs kernel moves the counts to int32
+ *   "use_graph"         1 = capture plan runs in CUDA graphs (default), 0 = plain launches
+ *   "wait_limit"        iteration limit of every device-side wait
+ *   "bitmap_cost", "hist_cost_row", "hist_cost_var", "flush_cost"
+ *                       cost-model coefficients (x1000) used by AUTO. */
+int fc_set_option(fc_ctx *ctx, const char *key, int64_t value);
+
+/* Current value of an option (or -1 for an unknown key). */
+int64_t fc_get_option(const fc_ctx *ctx, const char *key);
+
+/* Time each strategy on sample queries over the loaded data and set the
+ * cost-model coefficients that FC_STRAT_AUTO uses.  `budget_ms` bounds the
+ * time spent (0 = default).  Results are kept in the context. */
+int fc_autotune(fc_ctx *ctx, int32_t budget_ms);
+
+/* Message of the last error on this host thread ("" if none). */
+const char *fc_last_error(void);
+
+/* Run a device wait that nothing will satisfy, bounded by `wait_limit`
+ * iterations, and return the status it leaves (FC_ERR_TIMEOUT expected).
+ * Exercises the bounded-wait error path without faulting the GPU. */
+int fc_selftest_wait_timeout(fc_ctx *ctx, int64_t wait_limit);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FC_H */

@@ -1,0 +1,1368 @@
+// fc_api.cu -- host runtime behind the C ABI of include/fc.h: contexts
+// (the loaded database), the batch planner (validation, strategy choice by a
+// cost model, work items), plans replayed as CUDA graphs, the host-buffer
+// entry points, options and the autotuner.
+#include "../../include/fc.h"
+#include "fc_internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+using namespace fc;
+
+// ------------------------------------------------------------------ errors
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(FC_ERR_OOM, "%s: out of device memory", what);
+    }
+    return fail(FC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define FC_CUDA(call, what)                          \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// Device buffer owned by the runtime.
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t want)
+    {
+        if (want <= bytes && p) return cudaSuccess;
+        release();
+        if (want == 0) want = 16;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) bytes = want;
+        return e;
+    }
+};
+
+struct Options {
+    int32_t strategy = FC_STRAT_AUTO;
+    int32_t smem_cells = 24576;       // 96 KiB of tables per CTA
+    int32_t threads = 512;
+    int32_t ctas_per_sm = 2;
+    int32_t hist_copies = 4;
+    int64_t min_part_rows = 65536;
+    int64_t pair_chunk_rows = 1 << 16;
+    int32_t use_graph = 1;
+    int64_t wait_limit = 1 << 22;
+    int64_t sort_min_cells = 1 << 25;
+    // cost model, femtoseconds: bitmap per DFS node per 4096-row chunk;
+    // histogram per row and per row-variable; per table cell flushed
+    int64_t bitmap_cost = 13000;
+    int64_t hist_cost_row = 150;
+    int64_t hist_cost_var = 130;
+    int64_t flush_cost = 160;
+    int32_t support_warps = 16;
+    int32_t support_sets_per_warp = 4;
+    int64_t support_part_words = 8192;
+};
+
+}  // namespace
+
+struct fc_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int max_smem_optin = 0;
+    cudaStream_t stream = nullptr;
+    bool transactions = false;  // loaded with fc_load_bits
+    int32_t n = 0;
+    int64_t m = 0;
+    std::vector<int32_t> arity, soff;
+    int32_t R = 0;
+    int64_t m_pad = 0, words = 0, wstride = 0;
+    uint8_t *d_D = nullptr;
+    uint64_t *d_bits = nullptr;
+    int64_t *d_marg = nullptr;
+    int32_t *d_arity = nullptr, *d_soff = nullptr;
+    int32_t *d_status = nullptr;
+    std::vector<int64_t> marg;
+    std::vector<double> entropy;
+    Options opt;
+    // scratch of the host-buffer entry points
+    DBuf io[3];
+    std::vector<uint32_t> mark;
+    uint32_t epoch = 0;
+};
+
+namespace {
+
+struct GraphEntry {
+    void *o0, *o1, *o2;
+    cudaStream_t s;
+    cudaGraphExec_t exec;
+};
+
+struct SortJob {
+    int32_t q;
+    int32_t k;
+    int32_t key_bits;
+    int32_t cells;
+    int64_t table_off;
+    const QVar *d_vars;
+};
+
+enum PlanKind { kPlanCount = 0, kPlanScore = 1, kPlanSupport = 2, kPlanPairs = 3 };
+
+}  // namespace
+
+struct fc_plan {
+    fc_ctx *ctx = nullptr;
+    int kind = kPlanCount;
+    int32_t nq = 0;
+    std::vector<int64_t> table_off;  // count plans: caller offsets (nq + 1)
+    std::vector<int32_t> strategy;
+    int64_t out_cells = 0;
+    // count / score
+    DBuf desc;           // QHead, QVar, Item, q_list
+    DBuf counters;       // next item + tickets
+    DBuf scratch_tables; // score plans: tables that live in global memory
+    DBuf sort_mem;
+    SortScratch sort_sc{};
+    std::vector<SortJob> sort_jobs;
+    QHead *d_qh = nullptr;
+    QVar *d_qv = nullptr;
+    Item *d_items = nullptr;
+    int32_t *d_qlist = nullptr;
+    int32_t n_items = 0, n_qlist = 0, n_counters = 0;
+    bool zero_tables = false;
+    int64_t table_buf_cells = 0;  // cells of the buffer the kernel writes
+    int score_kind = kNoScore;
+    double ess = 1.0;
+    int grid = 0, threads = 0, smem_cells = 0;
+    size_t smem = 0;
+    // support
+    SupportParams sp{};
+    int sup_grid = 0, sup_threads = 0;
+    int64_t n_sub = 0;
+    // pairs
+    PairsParams pp{};
+    DBuf pairs_C, pairs_meta;
+    int64_t n_pairs = 0, pair_cells = 0;
+    int64_t *d_pair_off = nullptr;
+    size_t upload_bytes = 0;  // host-to-device bytes of the plan's descriptors
+    std::vector<GraphEntry> graphs;
+};
+
+// ---------------------------------------------------------------- loading
+
+namespace {
+
+int finish_load(fc_ctx *c)
+{
+    // marginal counts per (variable, state) and entropies (DFS order, Sec. 3.2)
+    FC_CUDA(cudaMalloc(&c->d_marg, sizeof(int64_t) * std::max(c->R, 1)), "cudaMalloc marginals");
+    FC_CUDA(launch_bit_popcounts(c->d_bits, c->R, c->wstride, c->d_marg, c->stream), "popcounts");
+    c->marg.assign(c->R, 0);
+    FC_CUDA(cudaMemcpyAsync(c->marg.data(), c->d_marg, sizeof(int64_t) * c->R,
+                            cudaMemcpyDeviceToHost, c->stream), "copy marginals");
+    FC_CUDA(cudaStreamSynchronize(c->stream), "load");
+    c->entropy.assign(c->n, 0.0);
+    if (!c->transactions) {
+        for (int i = 0; i < c->n; ++i) {
+            double h = 0.0;
+            for (int s = 0; s < c->arity[i]; ++s) {
+                const double p = (double)c->marg[c->soff[i] + s] / (double)c->m;
+                if (p > 0.0) h -= p * std::log2(p);
+            }
+            c->entropy[i] = h;
+        }
+    }
+    c->mark.assign(c->n, 0u);
+    return FC_OK;
+}
+
+int new_ctx(fc_ctx **out, int32_t n, int64_t m)
+{
+    fc_ctx *c = new (std::nothrow) fc_ctx();
+    if (!c) return fail(FC_ERR_OOM, "host allocation failed");
+    cudaGetDevice(&c->device);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    cudaDeviceGetAttribute(&c->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    c->n = n;
+    c->m = m;
+    c->words = (m + 63) / 64;
+    c->wstride = round_up(c->words, kChunkWords);
+    *out = c;
+    e = cudaMalloc(&c->d_status, 16);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, 16, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "status word");
+    return FC_OK;
+}
+
+}  // namespace
+
+extern "C" int fc_load(fc_ctx **out, const uint8_t *D, int32_t n, int64_t m,
+                       const int32_t *arities, int32_t layout, int32_t where)
+{
+    if (!out || !D || !arities) return fail(FC_ERR_ARG, "fc_load: null argument");
+    *out = nullptr;
+    if (n < 1 || m < 1) return fail(FC_ERR_ARG, "fc_load: need n >= 1 and m >= 1");
+    if (m >= ((int64_t)1 << 31)) return fail(FC_ERR_RANGE, "fc_load: m must be < 2^31");
+    if (layout != FC_COL_MAJOR && layout != FC_ROW_MAJOR) return fail(FC_ERR_ARG, "fc_load: bad layout");
+    if (where != FC_HOST && where != FC_DEVICE) return fail(FC_ERR_ARG, "fc_load: bad pointer location");
+    for (int i = 0; i < n; ++i)
+        if (arities[i] < 1 || arities[i] > 255)
+            return fail(FC_ERR_ARG, "fc_load: arity of variable %d is %d, not in 1..255", i, arities[i]);
+    fc_ctx *c = nullptr;
+    int rc = new_ctx(&c, n, m);
+    if (rc != FC_OK) {
+        fc_free(c);
+        return rc;
+    }
+    c->arity.assign(arities, arities + n);
+    c->soff.resize(n);
+    for (int i = 0; i < n; ++i) {
+        c->soff[i] = c->R;
+        c->R += arities[i];
+    }
+    c->m_pad = round_up(m, kChunkRows);
+    auto bail = [&](int code) {
+        fc_free(c);
+        return code;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&c->d_D, (size_t)n * c->m_pad)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc D"));
+    if ((e = cudaMemsetAsync(c->d_D, 0, (size_t)n * c->m_pad, c->stream)) != cudaSuccess) return bail(cuda_fail(e, "memset D"));
+    const cudaMemcpyKind kind = where == FC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (layout == FC_COL_MAJOR) {
+        e = cudaMemcpy2DAsync(c->d_D, c->m_pad, D, m, m, n, kind, c->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "copy D"));
+    } else {
+        uint8_t *tmp = nullptr;
+        if ((e = cudaMalloc(&tmp, (size_t)n * m)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc D rows"));
+        e = cudaMemcpyAsync(tmp, D, (size_t)n * m, kind, c->stream);
+        if (e == cudaSuccess) e = launch_transpose_rows(tmp, m, n, c->d_D, c->m_pad, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "transpose D"));
+    }
+    if ((e = cudaMalloc(&c->d_arity, sizeof(int32_t) * n)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+    if ((e = cudaMalloc(&c->d_soff, sizeof(int32_t) * n)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+    cudaMemcpyAsync(c->d_arity, c->arity.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->d_soff, c->soff.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream);
+    const size_t bits_bytes = sizeof(uint64_t) * (size_t)c->R * c->wstride;
+    if ((e = cudaMalloc(&c->d_bits, bits_bytes)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc bitmaps"));
+    if ((e = cudaMemsetAsync(c->d_bits, 0, bits_bytes, c->stream)) != cudaSuccess) return bail(cuda_fail(e, "memset bitmaps"));
+    int32_t *bad = c->d_status + 1;
+    e = launch_pack_bits(c->d_D, c->m_pad, m, n, c->d_arity, c->d_soff, c->d_bits, c->wstride, 255, bad, c->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "pack bitmaps"));
+    int32_t bad_h = 0;
+    e = cudaMemcpyAsync(&bad_h, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "load"));
+    if (bad_h) return bail(fail(FC_ERR_RANGE, "fc_load: a stored state is >= its variable's arity"));
+    cudaMemsetAsync(c->d_status, 0, 16, c->stream);
+    rc = finish_load(c);
+    if (rc != FC_OK) return bail(rc);
+    *out = c;
+    return FC_OK;
+}
+
+extern "C" int fc_load_bits(fc_ctx **out, const uint64_t *bitmaps, int32_t n_items, int64_t m,
+                            int32_t where)
+{
+    if (!out || !bitmaps) return fail(FC_ERR_ARG, "fc_load_bits: null argument");
+    *out = nullptr;
+    if (n_items < 1 || m < 1) return fail(FC_ERR_ARG, "fc_load_bits: need n_items >= 1 and m >= 1");
+    if (m >= ((int64_t)1 << 31)) return fail(FC_ERR_RANGE, "fc_load_bits: m must be < 2^31");
+    if (where != FC_HOST && where != FC_DEVICE) return fail(FC_ERR_ARG, "fc_load_bits: bad pointer location");
+    fc_ctx *c = nullptr;
+    int rc = new_ctx(&c, n_items, m);
+    if (rc != FC_OK) {
+        fc_free(c);
+        return rc;
+    }
+    c->transactions = true;
+    c->arity.assign(n_items, 1);
+    c->soff.resize(n_items);
+    for (int i = 0; i < n_items; ++i) c->soff[i] = i;
+    c->R = n_items;
+    const size_t bits_bytes = sizeof(uint64_t) * (size_t)n_items * c->wstride;
+    cudaError_t e = cudaMalloc(&c->d_bits, bits_bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bits, 0, bits_bytes, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(c->d_bits, sizeof(uint64_t) * c->wstride, bitmaps, sizeof(uint64_t) * c->words,
+                              sizeof(uint64_t) * c->words, n_items,
+                              where == FC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_mask_tail_bits(c->d_bits, n_items, c->wstride, m, c->stream);
+    if (e != cudaSuccess) {
+        fc_free(c);
+        return cuda_fail(e, "fc_load_bits");
+    }
+    rc = finish_load(c);
+    if (rc != FC_OK) {
+        fc_free(c);
+        return rc;
+    }
+    *out = c;
+    return FC_OK;
+}
+
+extern "C" void fc_free(fc_ctx *c)
+{
+    if (!c) return;
+    DevGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto &b : c->io) b.release();
+    cudaFree(c->d_D);
+    cudaFree(c->d_bits);
+    cudaFree(c->d_marg);
+    cudaFree(c->d_arity);
+    cudaFree(c->d_soff);
+    cudaFree(c->d_status);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+extern "C" int64_t fc_info(const fc_ctx *c, int32_t key)
+{
+    if (!c) return -1;
+    switch (key) {
+    case 0: return c->n;
+    case 1: return c->m;
+    case 2: return c->R;
+    case 3: return c->device;
+    default: return -1;
+    }
+}
+
+extern "C" int fc_marginals(const fc_ctx *c, int64_t *out)
+{
+    if (!c || !out) return fail(FC_ERR_ARG, "fc_marginals: null argument");
+    std::memcpy(out, c->marg.data(), sizeof(int64_t) * c->R);
+    return FC_OK;
+}
+
+// ------------------------------------------------------------------ planner
+
+namespace {
+
+// Validates one variable list and appends its device description: strides in
+// the caller's order (last fastest), arity-1 variables dropped (they add no
+// digit).  Returns the number of cells or a negative FC_ERR code.
+int64_t describe(fc_ctx *c, const int32_t *vars, int32_t k, std::vector<QVar> &qv, int32_t &k_eff)
+{
+    if (k < 0 || k > c->n) return fail(FC_ERR_ARG, "query has %d variables, n = %d", k, c->n);
+    if (k > 0 && !vars) return fail(FC_ERR_ARG, "null variable list");
+    if (++c->epoch == 0) {
+        std::fill(c->mark.begin(), c->mark.end(), 0u);
+        c->epoch = 1;
+    }
+    int64_t cells = 1;
+    for (int t = 0; t < k; ++t) {
+        const int v = vars[t];
+        if (v < 0 || v >= c->n) return fail(FC_ERR_ARG, "variable %d out of range 0..%d", v, c->n - 1);
+        if (c->mark[v] == c->epoch) return fail(FC_ERR_ARG, "variable %d listed twice in one query", v);
+        c->mark[v] = c->epoch;
+        cells *= c->arity[v];
+        if (cells > INT32_MAX) return fail(FC_ERR_SIZE, "table over %d variables exceeds 2^31-1 cells", k);
+    }
+    int64_t stride = 1;
+    const size_t first = qv.size();
+    for (int t = k - 1; t >= 0; --t) {
+        const int v = vars[t];
+        if (c->arity[v] > 1) qv.push_back(QVar{v, (int32_t)stride, c->arity[v], c->soff[v]});
+        stride *= c->arity[v];
+    }
+    std::reverse(qv.begin() + first, qv.end());
+    k_eff = (int32_t)(qv.size() - first);
+    return cells;
+}
+
+// DFS nodes of the bitmap tree in the given variable order (no pruning).
+double dfs_nodes(const QVar *v, int k)
+{
+    double nodes = 0.0, level = 1.0;
+    for (int t = 0; t < k; ++t) {
+        level *= v[t].arity;
+        nodes += level;
+    }
+    return nodes;
+}
+
+struct QPlan {
+    int32_t strategy;
+    double cost;  // femtoseconds for the whole query
+};
+
+QPlan choose(const fc_ctx *c, const QVar *v, int k, int64_t cells, int32_t smem_cells)
+{
+    const Options &o = c->opt;
+    const double chunks = (double)((c->m + kChunkRows - 1) / kChunkRows);
+    const double rows = (double)c->m;
+    const double flush = (double)cells * o.flush_cost;
+    const bool fits = cells <= smem_cells;
+    const double hist = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) + flush;
+    const double bitmap = (k <= kMaxBitmapK && fits) ? chunks * dfs_nodes(v, k) * o.bitmap_cost + flush : 1e300;
+    const double gatomic = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) * 2.0 + (double)cells * 4.0;
+    int32_t s = o.strategy;
+    if (s == FC_STRAT_BITMAP && !(k <= kMaxBitmapK && fits)) s = FC_STRAT_AUTO;
+    if (s == FC_STRAT_HIST && !fits) s = FC_STRAT_AUTO;
+    if (s == FC_STRAT_AUTO) {
+        if (fits)
+            s = bitmap < hist ? FC_STRAT_BITMAP : FC_STRAT_HIST;
+        else
+            s = cells >= o.sort_min_cells ? FC_STRAT_SORT : FC_STRAT_GATOMIC;
+    }
+    double cost = s == FC_STRAT_BITMAP ? bitmap : s == FC_STRAT_HIST ? hist : gatomic;
+    return QPlan{s, cost};
+}
+
+// Builds a count or score plan.  vars lists are read through `get`.
+template <class GetVars>
+int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off, int score_kind,
+                     double ess, fc_plan **out)
+{
+    if (c->transactions) return fail(FC_ERR_STATE, "context holds transaction bitmaps; use the support calls");
+    if (nq < 0) return fail(FC_ERR_ARG, "nq < 0");
+    fc_plan *p = new (std::nothrow) fc_plan();
+    if (!p) return fail(FC_ERR_OOM, "host allocation failed");
+    p->ctx = c;
+    p->kind = score_kind == kNoScore ? kPlanCount : kPlanScore;
+    p->nq = nq;
+    p->score_kind = score_kind;
+    p->ess = ess;
+    const Options &o = c->opt;
+    p->threads = std::max(32, std::min(1024, o.threads / 32 * 32));
+    const int max_cells = std::max(1, std::min<int>(o.smem_cells, (c->max_smem_optin - 4096) / 4));
+    p->smem_cells = max_cells;
+
+    std::vector<QHead> qh(nq);
+    std::vector<QVar> qv;
+    std::vector<double> cost(nq);
+    p->strategy.resize(nq);
+    p->table_off.assign(nq + 1, 0);
+    int64_t scratch = 0;
+    for (int32_t q = 0; q < nq; ++q) {
+        const int32_t *vars;
+        int32_t k;
+        int32_t child;
+        if (!get(q, vars, k, child)) {
+            delete p;
+            return FC_ERR_ARG;
+        }
+        const size_t first = qv.size();
+        int32_t k_eff = 0;
+        const int64_t cells = describe(c, vars, k, qv, k_eff);
+        if (cells < 0) {
+            delete p;
+            return (int)cells;
+        }
+        QPlan ch = choose(c, qv.data() + first, k_eff, cells, max_cells);
+        if (ch.strategy == FC_STRAT_BITMAP)  // Sec. 3.2: lowest entropy at the top of the tree
+            std::stable_sort(qv.begin() + first, qv.end(), [&](const QVar &a, const QVar &b) {
+                return c->entropy[a.var] < c->entropy[b.var];
+            });
+        QHead &h = qh[q];
+        h.cells = (int32_t)cells;
+        h.var_off = (int32_t)first;
+        h.k = (int16_t)k_eff;
+        h.strategy = (int16_t)ch.strategy;
+        h.nparts = 1;
+        h.score_kind = (int16_t)score_kind;
+        h.r_child = score_kind == kNoScore ? 1 : c->arity[child];
+        h.child_soff = score_kind == kNoScore ? 0 : c->soff[child];
+        h.score_slot = q;
+        p->strategy[q] = ch.strategy;
+        cost[q] = ch.cost;
+        if (score_kind == kNoScore) {
+            if (user_off) {
+                if (user_off[q + 1] - user_off[q] < cells || user_off[q] < 0) {
+                    delete p;
+                    return fail(FC_ERR_ARG, "table_off of query %d leaves %lld cells, it needs %lld", q,
+                                (long long)(user_off[q + 1] - user_off[q]), (long long)cells);
+                }
+                p->table_off[q] = user_off[q];
+            } else {
+                p->table_off[q] = scratch;
+                scratch += cells;
+            }
+            h.table_off = p->table_off[q];
+        }
+        if (user_off) p->table_off[nq] = user_off[nq];
+        else p->table_off[nq] = scratch;
+    }
+    if (score_kind == kNoScore) p->out_cells = p->table_off[nq];
+
+    // work items: split rows when the batch alone cannot fill the GPU
+    const size_t smem_bytes = (size_t)max_cells * 4;
+    int per_sm = std::max(1, o.ctas_per_sm);
+    p->grid = c->num_sms * per_sm;
+    p->smem = smem_bytes;
+    const int64_t nchunks = (c->m + kChunkRows - 1) / kChunkRows;
+    const int64_t max_parts_rows = std::max<int64_t>(1, c->m / std::max<int64_t>(o.min_part_rows, kChunkRows));
+    int32_t persistent = 0;
+    for (int32_t q = 0; q < nq; ++q)
+        if (qh[q].strategy != kSort) ++persistent;
+    const int64_t target = (int64_t)p->grid * 4;
+    int64_t parts = 1;
+    if (persistent > 0 && persistent < target)
+        parts = std::min<int64_t>({nchunks, max_parts_rows, (target + persistent - 1) / persistent, 32767});
+    parts = std::max<int64_t>(1, parts);
+    std::vector<Item> items;
+    std::vector<std::pair<double, Item>> order;
+    std::vector<int32_t> qlist;
+    for (int32_t q = 0; q < nq; ++q) {
+        QHead &h = qh[q];
+        if (h.strategy == kSort) {
+            p->sort_jobs.push_back(SortJob{q, h.k, 0, h.cells, 0, nullptr});
+            continue;
+        }
+        h.nparts = (int16_t)parts;
+        for (int32_t part = 0; part < parts; ++part) order.push_back({cost[q] / parts, Item{q, part}});
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const auto &a, const auto &b) { return a.first > b.first; });
+    items.reserve(order.size());
+    for (auto &x : order) items.push_back(x.second);
+    p->n_items = (int32_t)items.size();
+
+    // tables that must exist in global memory for score plans
+    if (score_kind != kNoScore) {
+        for (int32_t q = 0; q < nq; ++q) {
+            QHead &h = qh[q];
+            const bool global = h.strategy == kGAtomic || h.strategy == kSort || h.nparts > 1;
+            if (global) {
+                h.table_off = scratch;
+                scratch += h.cells;
+            } else {
+                h.table_off = 0;
+            }
+        }
+        p->table_buf_cells = scratch;
+    } else {
+        p->table_buf_cells = p->out_cells;
+    }
+    for (int32_t q = 0; q < nq; ++q) {
+        const QHead &h = qh[q];
+        if (h.strategy == kGAtomic || h.strategy == kSort || h.nparts > 1) p->zero_tables = true;
+    }
+    for (auto &j : p->sort_jobs) {
+        j.table_off = qh[j.q].table_off;
+        j.key_bits = j.cells > 1 ? 32 - __builtin_clz((uint32_t)(j.cells - 1)) : 0;
+        if (score_kind != kNoScore) qlist.push_back(j.q);
+    }
+    p->n_qlist = (int32_t)qlist.size();
+
+    // one device allocation for all descriptors
+    const size_t b_qh = sizeof(QHead) * std::max(nq, 1);
+    const size_t b_qv = sizeof(QVar) * std::max<size_t>(qv.size(), 1);
+    const size_t b_it = sizeof(Item) * std::max<size_t>(items.size(), 1);
+    const size_t b_ql = sizeof(int32_t) * std::max<size_t>(qlist.size(), 1);
+    const size_t o_qv = round_up(b_qh, 256), o_it = o_qv + round_up(b_qv, 256), o_ql = o_it + round_up(b_it, 256);
+    const size_t total = o_ql + round_up(b_ql, 256);
+    std::vector<uint8_t> host(total, 0);
+    std::memcpy(host.data(), qh.data(), sizeof(QHead) * nq);
+    std::memcpy(host.data() + o_qv, qv.data(), sizeof(QVar) * qv.size());
+    std::memcpy(host.data() + o_it, items.data(), sizeof(Item) * items.size());
+    std::memcpy(host.data() + o_ql, qlist.data(), sizeof(int32_t) * qlist.size());
+    cudaError_t e = p->desc.ensure(total);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->desc.p, host.data(), total, cudaMemcpyHostToDevice, c->stream);
+    p->upload_bytes = total;
+    p->n_counters = 1 + nq;
+    if (e == cudaSuccess) e = p->counters.ensure(sizeof(int32_t) * p->n_counters);
+    if (e == cudaSuccess && score_kind != kNoScore) e = p->scratch_tables.ensure(sizeof(int32_t) * std::max<int64_t>(p->table_buf_cells, 1));
+    if (e == cudaSuccess && !p->sort_jobs.empty()) {
+        const int tile = sort_tile_rows();
+        const int64_t nb = (c->m + tile - 1) / tile;
+        const size_t kb = round_up(sizeof(uint32_t) * c->m, 256);
+        e = p->sort_mem.ensure(2 * kb + sizeof(uint32_t) * 256 * nb);
+        if (e == cudaSuccess) {
+            uint8_t *base = (uint8_t *)p->sort_mem.p;
+            p->sort_sc.keys_a = (uint32_t *)base;
+            p->sort_sc.keys_b = (uint32_t *)(base + kb);
+            p->sort_sc.block_hist = (uint32_t *)(base + 2 * kb);
+            p->sort_sc.cap_rows = c->m;
+            p->sort_sc.cap_blocks = (int32_t)nb;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        fc_plan_free(p);
+        return cuda_fail(e, "plan upload");
+    }
+    uint8_t *d = (uint8_t *)p->desc.p;
+    p->d_qh = (QHead *)d;
+    p->d_qv = (QVar *)(d + o_qv);
+    p->d_items = (Item *)(d + o_it);
+    p->d_qlist = (int32_t *)(d + o_ql);
+    for (auto &j : p->sort_jobs) j.d_vars = p->d_qv + qh[j.q].var_off;
+    *out = p;
+    return FC_OK;
+}
+
+// Enqueues the work of a count/score plan on stream s.
+cudaError_t enqueue_count(fc_plan *p, int32_t *tables, float *scores, cudaStream_t s)
+{
+    fc_ctx *c = p->ctx;
+    cudaError_t e = cudaMemsetAsync(p->counters.p, 0, sizeof(int32_t) * p->n_counters, s);
+    if (e != cudaSuccess) return e;
+    int32_t *tab = p->kind == kPlanScore ? (int32_t *)p->scratch_tables.p : tables;
+    if (p->zero_tables && p->table_buf_cells > 0) {
+        e = cudaMemsetAsync(tab, 0, sizeof(int32_t) * p->table_buf_cells, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (p->n_items > 0) {
+        CountParams P{};
+        P.D = c->d_D;
+        P.m_pad = c->m_pad;
+        P.m = c->m;
+        P.bits = c->d_bits;
+        P.wstride = c->wstride;
+        P.qh = p->d_qh;
+        P.qv = p->d_qv;
+        P.items = p->d_items;
+        P.n_items = p->n_items;
+        P.next_item = (int32_t *)p->counters.p;
+        P.tickets = (int32_t *)p->counters.p + 1;
+        P.tables = tab;
+        P.scores = scores;
+        P.marg = c->d_marg;
+        P.ess = p->ess;
+        P.write_tables = p->kind == kPlanCount ? 1 : 0;
+        P.smem_cells = p->smem_cells;
+        P.hist_copies = c->opt.hist_copies;
+        const int grid = std::min<int64_t>(p->grid, std::max(p->n_items, 1));
+        e = launch_count(P, grid, p->threads, p->smem, s);
+        if (e != cudaSuccess) return e;
+    }
+    for (const SortJob &j : p->sort_jobs) {
+        e = launch_sort_count(c->d_D, c->m_pad, c->m, j.d_vars, j.k, j.key_bits, tab + j.table_off,
+                              j.cells, 0, p->sort_sc, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (p->kind == kPlanScore && p->n_qlist > 0)
+        e = launch_score_global(p->d_qh, p->d_qlist, p->n_qlist, tab, scores, c->d_marg, c->m, p->ess, s);
+    return e;
+}
+
+cudaError_t enqueue_support(fc_plan *p, int32_t *support, int32_t *sub, float *conf, cudaStream_t s);
+cudaError_t enqueue_pairs(fc_plan *p, int32_t *pairs, float *mi, cudaStream_t s);
+
+cudaError_t enqueue(fc_plan *p, void *o0, void *o1, void *o2, cudaStream_t s)
+{
+    switch (p->kind) {
+    case kPlanCount: return enqueue_count(p, (int32_t *)o0, nullptr, s);
+    case kPlanScore: return enqueue_count(p, nullptr, (float *)o0, s);
+    case kPlanSupport: return enqueue_support(p, (int32_t *)o0, (int32_t *)o1, (float *)o2, s);
+    case kPlanPairs: return enqueue_pairs(p, (int32_t *)o0, (float *)o1, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int run_plan(fc_plan *p, void *o0, void *o1, void *o2, cudaStream_t s, bool allow_graph)
+{
+    fc_ctx *c = p->ctx;
+    if (!s) s = c->stream;
+    if (!(allow_graph && c->opt.use_graph)) {
+        cudaError_t e = enqueue(p, o0, o1, o2, s);
+        if (e != cudaSuccess) return cuda_fail(e, "plan run");
+        return FC_OK;
+    }
+    for (auto &g : p->graphs)
+        if (g.o0 == o0 && g.o1 == o1 && g.o2 == o2 && g.s == s) {
+            cudaError_t e = cudaGraphLaunch(g.exec, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+            return FC_OK;
+        }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    cudaError_t e2 = enqueue(p, o0, o1, o2, s);
+    e = cudaStreamEndCapture(s, &graph);
+    if (e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(e2, "plan capture");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    p->graphs.push_back(GraphEntry{o0, o1, o2, s, exec});
+    e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return FC_OK;
+}
+
+int read_status(fc_ctx *c, cudaStream_t s)
+{
+    int32_t st[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(st, c->d_status, sizeof st, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "status");
+    if (st[0] != kStatusOk) {
+        cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), s);
+        cudaStreamSynchronize(s);
+        return fail(FC_ERR_TIMEOUT, "a bounded device wait ran out (status %d)", st[0]);
+    }
+    return FC_OK;
+}
+
+// Runs a plan on the context stream with runtime-owned device outputs and
+// copies them to the caller's host buffers.
+int run_to_host(fc_plan *p, void *h0, size_t b0, void *h1, size_t b1, void *h2, size_t b2)
+{
+    fc_ctx *c = p->ctx;
+    void *hs[3] = {h0, h1, h2};
+    size_t bs[3] = {b0, b1, b2};
+    void *ds[3] = {nullptr, nullptr, nullptr};
+    for (int i = 0; i < 3; ++i) {
+        if (!hs[i] || bs[i] == 0) continue;
+        cudaError_t e = c->io[i].ensure(bs[i]);
+        if (e != cudaSuccess) return cuda_fail(e, "output buffer");
+        ds[i] = c->io[i].p;
+    }
+    int rc = run_plan(p, ds[0], ds[1], ds[2], c->stream, false);
+    if (rc != FC_OK) return rc;
+    for (int i = 0; i < 3; ++i)
+        if (ds[i]) {
+            cudaError_t e = cudaMemcpyAsync(hs[i], ds[i], bs[i], cudaMemcpyDeviceToHost, c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "copy outputs");
+        }
+    return read_status(c, c->stream);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- plan API
+
+extern "C" int fc_plan_count(fc_ctx *c, int32_t nq, const int32_t *var_off, const int32_t *vars,
+                             const int64_t *table_off, fc_plan **out)
+{
+    if (!c || !out || (nq > 0 && (!var_off || !vars))) return fail(FC_ERR_ARG, "fc_plan_count: null argument");
+    *out = nullptr;
+    DevGuard g(c->device);
+    if (table_off)
+        for (int32_t q = 0; q < nq; ++q)
+            if (table_off[q + 1] < table_off[q]) return fail(FC_ERR_ARG, "table_off must be non-decreasing");
+    auto get = [&](int32_t q, const int32_t *&v, int32_t &k, int32_t &child) {
+        const int32_t a = var_off[q], b = var_off[q + 1];
+        if (a < 0 || b < a) {
+            fail(FC_ERR_ARG, "var_off must be non-decreasing and non-negative");
+            return false;
+        }
+        v = vars + a;
+        k = b - a;
+        child = -1;
+        return true;
+    };
+    return build_count_plan(c, nq, get, table_off, kNoScore, 1.0, out);
+}
+
+extern "C" int fc_plan_score(fc_ctx *c, int32_t nq, const int32_t *child, const int32_t *par_off,
+                             const int32_t *parents, int32_t kind, double ess, fc_plan **out)
+{
+    if (!c || !out || (nq > 0 && (!child || !par_off))) return fail(FC_ERR_ARG, "fc_plan_score: null argument");
+    *out = nullptr;
+    if (kind < FC_LL || kind > FC_MI) return fail(FC_ERR_ARG, "unknown score kind %d", kind);
+    if (kind == FC_BDEU && !(ess > 0.0)) return fail(FC_ERR_ARG, "BDeu needs ess > 0");
+    DevGuard g(c->device);
+    std::vector<int32_t> buf;
+    auto get = [&](int32_t q, const int32_t *&v, int32_t &k, int32_t &ch) {
+        const int32_t a = par_off[q], b = par_off[q + 1];
+        if (a < 0 || b < a || (b > a && !parents)) {
+            fail(FC_ERR_ARG, "par_off must be non-decreasing and non-negative");
+            return false;
+        }
+        if (child[q] < 0 || child[q] >= c->n) {
+            fail(FC_ERR_ARG, "child %d out of range", child[q]);
+            return false;
+        }
+        buf.assign(parents + a, parents + b);
+        buf.push_back(child[q]);
+        v = buf.data();
+        k = (int32_t)buf.size();
+        ch = child[q];
+        return true;
+    };
+    return build_count_plan(c, nq, get, nullptr, kind, ess, out);
+}
+
+extern "C" int64_t fc_plan_size(const fc_plan *p, int32_t key)
+{
+    if (!p) return -1;
+    switch (key) {
+    case 0: return p->kind == kPlanPairs ? p->pair_cells : p->out_cells;
+    case 1: return p->kind == kPlanScore ? p->nq : p->kind == kPlanPairs ? p->n_pairs : 0;
+    case 2: return p->kind == kPlanSupport ? p->nq : 0;
+    case 3: return p->kind == kPlanSupport ? p->n_sub : 0;
+    case 4: return p->nq;
+    case 5: return (int64_t)p->upload_bytes;
+    default: return -1;
+    }
+}
+
+extern "C" int fc_plan_table_offsets(const fc_plan *p, int64_t *off)
+{
+    if (!p || !off) return fail(FC_ERR_ARG, "fc_plan_table_offsets: null argument");
+    if (p->kind != kPlanCount) return fail(FC_ERR_STATE, "not a count plan");
+    std::memcpy(off, p->table_off.data(), sizeof(int64_t) * (p->nq + 1));
+    return FC_OK;
+}
+
+extern "C" int fc_plan_strategies(const fc_plan *p, int32_t *s)
+{
+    if (!p || !s) return fail(FC_ERR_ARG, "fc_plan_strategies: null argument");
+    if (p->kind != kPlanCount && p->kind != kPlanScore) return fail(FC_ERR_STATE, "not a count or score plan");
+    std::memcpy(s, p->strategy.data(), sizeof(int32_t) * p->nq);
+    return FC_OK;
+}
+
+extern "C" int fc_plan_run(fc_plan *p, void *o0, void *o1, void *o2, void *stream)
+{
+    if (!p) return fail(FC_ERR_ARG, "fc_plan_run: null plan");
+    DevGuard g(p->ctx->device);
+    if ((p->kind == kPlanCount && p->out_cells > 0 && !o0) || (p->kind == kPlanScore && p->nq > 0 && !o0) ||
+        (p->kind == kPlanSupport && p->nq > 0 && !o0))
+        return fail(FC_ERR_ARG, "fc_plan_run: missing output buffer");
+    return run_plan(p, o0, o1, o2, (cudaStream_t)stream, true);
+}
+
+extern "C" void fc_plan_free(fc_plan *p)
+{
+    if (!p) return;
+    DevGuard g(p->ctx->device);
+    cudaStreamSynchronize(p->ctx->stream);
+    for (auto &gr : p->graphs) {
+        cudaStreamSynchronize(gr.s);
+        cudaGraphExecDestroy(gr.exec);
+    }
+    p->desc.release();
+    p->counters.release();
+    p->scratch_tables.release();
+    p->sort_mem.release();
+    p->pairs_C.release();
+    p->pairs_meta.release();
+    delete p;
+}
+
+extern "C" int fc_sync(fc_ctx *c, void *stream)
+{
+    if (!c) return fail(FC_ERR_ARG, "fc_sync: null context");
+    DevGuard g(c->device);
+    if (stream) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    }
+    return read_status(c, c->stream);
+}
+
+// ------------------------------------------------------- host entry points
+
+extern "C" int fc_count(fc_ctx *c, const int32_t *vars, int32_t k, int32_t *table)
+{
+    if (!c || !table || (k > 0 && !vars)) return fail(FC_ERR_ARG, "fc_count: null argument");
+    int32_t off[2] = {0, k};
+    return fc_count_batch(c, 1, off, vars, nullptr, table);
+}
+
+extern "C" int fc_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int32_t *vars,
+                              const int64_t *table_off, int32_t *tables)
+{
+    if (!c || (nq > 0 && !tables)) return fail(FC_ERR_ARG, "fc_count_batch: null argument");
+    DevGuard g(c->device);
+    fc_plan *p = nullptr;
+    int rc = fc_plan_count(c, nq, var_off, vars, table_off, &p);
+    if (rc != FC_OK) return rc;
+    rc = run_to_host(p, tables, sizeof(int32_t) * p->out_cells, nullptr, 0, nullptr, 0);
+    fc_plan_free(p);
+    return rc;
+}
+
+extern "C" int fc_score_batch(fc_ctx *c, int32_t nq, const int32_t *child, const int32_t *par_off,
+                              const int32_t *parents, int32_t kind, double ess, float *scores)
+{
+    if (!c || (nq > 0 && !scores)) return fail(FC_ERR_ARG, "fc_score_batch: null argument");
+    DevGuard g(c->device);
+    fc_plan *p = nullptr;
+    int rc = fc_plan_score(c, nq, child, par_off, parents, kind, ess, &p);
+    if (rc != FC_OK) return rc;
+    rc = run_to_host(p, scores, sizeof(float) * nq, nullptr, 0, nullptr, 0);
+    fc_plan_free(p);
+    return rc;
+}
+
+extern "C" int fc_count_assignment(fc_ctx *c, const int32_t *vars, const int32_t *states, int32_t k,
+                                   int64_t *count)
+{
+    if (!c || !count || (k > 0 && (!vars || !states))) return fail(FC_ERR_ARG, "fc_count_assignment: null argument");
+    if (c->transactions) return fail(FC_ERR_STATE, "context holds transaction bitmaps");
+    if (k < 0 || k > c->n) return fail(FC_ERR_ARG, "bad k");
+    DevGuard g(c->device);
+    std::vector<int32_t> rows;
+    for (int t = 0; t < k; ++t) {
+        if (vars[t] < 0 || vars[t] >= c->n) return fail(FC_ERR_ARG, "variable %d out of range", vars[t]);
+        if (states[t] < 0 || states[t] >= c->arity[vars[t]]) {
+            *count = 0;
+            return FC_OK;
+        }
+        rows.push_back(c->soff[vars[t]] + states[t]);
+    }
+    if (k == 0) {
+        *count = c->m;
+        return FC_OK;
+    }
+    cudaError_t e = c->io[0].ensure(sizeof(unsigned long long) + sizeof(int32_t) * k + 64);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch");
+    unsigned long long *d_cnt = (unsigned long long *)c->io[0].p;
+    int32_t *d_rows = (int32_t *)((uint8_t *)c->io[0].p + 64);
+    cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), c->stream);
+    cudaMemcpyAsync(d_rows, rows.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, c->stream);
+    e = launch_assignment_count(c->d_bits, c->wstride, d_rows, k, c->words, d_cnt, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "assignment count");
+    unsigned long long h = 0;
+    e = cudaMemcpyAsync(&h, d_cnt, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "assignment count");
+    *count = (int64_t)h;
+    return FC_OK;
+}
+
+// ----------------------------------------------------------------- support
+
+namespace {
+
+cudaError_t enqueue_support(fc_plan *p, int32_t *support, int32_t *sub, float *conf, cudaStream_t s)
+{
+    SupportParams P = p->sp;
+    P.support = support;
+    P.sub_support = sub ? sub : (int32_t *)p->scratch_tables.p;
+    P.confidence = conf;
+    P.next_item = (int32_t *)p->counters.p;
+    cudaError_t e = cudaMemsetAsync(p->counters.p, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    if (P.nparts > 1) {
+        if ((e = cudaMemsetAsync(support, 0, sizeof(int32_t) * p->nq, s)) != cudaSuccess) return e;
+        if (p->n_sub > 0 && (e = cudaMemsetAsync(P.sub_support, 0, sizeof(int32_t) * p->n_sub, s)) != cudaSuccess)
+            return e;
+    }
+    if (p->nq == 0) return cudaSuccess;
+    e = launch_support(P, p->sup_grid, p->sup_threads, 0, s);
+    if (e != cudaSuccess) return e;
+    if (conf) e = launch_support_confidence(P, s);
+    return e;
+}
+
+}  // namespace
+
+extern "C" int fc_plan_support(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *items,
+                               fc_plan **out)
+{
+    if (!c || !out || (nq > 0 && !set_off)) return fail(FC_ERR_ARG, "fc_plan_support: null argument");
+    *out = nullptr;
+    if (!c->transactions) return fail(FC_ERR_STATE, "support queries need a context from fc_load_bits");
+    if (nq < 0) return fail(FC_ERR_ARG, "nq < 0");
+    DevGuard g(c->device);
+    if (nq > 0 && set_off[0] != 0) return fail(FC_ERR_ARG, "set_off[0] must be 0");
+    for (int32_t q = 0; q < nq; ++q) {
+        const int32_t a = set_off[q], b = set_off[q + 1];
+        if (b < a) return fail(FC_ERR_ARG, "set_off must be non-decreasing");
+        if (b - a > kMaxK) return fail(FC_ERR_SIZE, "itemset %d has %d items, at most %d supported", q, b - a, kMaxK);
+        if (b > a && !items) return fail(FC_ERR_ARG, "null items");
+        if (++c->epoch == 0) {
+            std::fill(c->mark.begin(), c->mark.end(), 0u);
+            c->epoch = 1;
+        }
+        for (int32_t t = a; t < b; ++t) {
+            const int32_t it = items[t];
+            if (it < 0 || it >= c->n) return fail(FC_ERR_ARG, "item %d out of range", it);
+            if (c->mark[it] == c->epoch) return fail(FC_ERR_ARG, "item %d listed twice in itemset %d", it, q);
+            c->mark[it] = c->epoch;
+        }
+    }
+    fc_plan *p = new (std::nothrow) fc_plan();
+    if (!p) return fail(FC_ERR_OOM, "host allocation failed");
+    p->ctx = c;
+    p->kind = kPlanSupport;
+    p->nq = nq;
+    const int64_t n_sub = nq > 0 ? set_off[nq] : 0;
+    p->n_sub = n_sub;
+    const Options &o = c->opt;
+    // itemsets in decreasing size so that the heavy ones start first
+    std::vector<int32_t> order(nq);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return set_off[a + 1] - set_off[a] > set_off[b + 1] - set_off[b];
+    });
+    const size_t b_off = sizeof(int32_t) * (nq + 1), b_it = sizeof(int32_t) * std::max<int64_t>(n_sub, 1);
+    const size_t o_it = round_up(b_off, 256), o_ord = o_it + round_up(b_it, 256);
+    const size_t total = o_ord + round_up(sizeof(int32_t) * std::max(nq, 1), 256);
+    std::vector<uint8_t> host(total, 0);
+    if (nq > 0) {
+        std::memcpy(host.data(), set_off, b_off);
+        if (n_sub > 0) std::memcpy(host.data() + o_it, items, sizeof(int32_t) * n_sub);
+        std::memcpy(host.data() + o_ord, order.data(), sizeof(int32_t) * nq);
+    }
+    cudaError_t e = p->desc.ensure(total);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->desc.p, host.data(), total, cudaMemcpyHostToDevice, c->stream);
+    p->upload_bytes = total;
+    if (e == cudaSuccess) e = p->counters.ensure(16);
+    if (e == cudaSuccess) e = p->scratch_tables.ensure(sizeof(int32_t) * std::max<int64_t>(n_sub, 1));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        fc_plan_free(p);
+        return cuda_fail(e, "plan upload");
+    }
+    SupportParams &P = p->sp;
+    uint8_t *d = (uint8_t *)p->desc.p;
+    P.bits = c->d_bits;
+    P.wstride = c->wstride;
+    P.words = c->words;
+    P.set_off = (const int32_t *)d;
+    P.items = (const int32_t *)(d + o_it);
+    P.order = (const int32_t *)(d + o_ord);
+    P.nq = nq;
+    P.n_items = c->n;
+    p->sup_threads = std::max(1, std::min(32, o.support_warps)) * 32;
+    P.sets_per_item = (p->sup_threads / 32) * std::max(1, o.support_sets_per_warp);
+    const int64_t part_words = std::max<int64_t>(64, round_up(o.support_part_words, 32));
+    P.nparts = (int32_t)std::max<int64_t>(1, (c->words + part_words - 1) / part_words);
+    P.words_per_part = (int32_t)round_up((c->words + P.nparts - 1) / P.nparts, 32);
+    P.m_tail = c->m;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, support_kernel_ptr(), p->sup_threads, 0);
+    p->sup_grid = c->num_sms * std::max(1, per_sm);
+    *out = p;
+    return FC_OK;
+}
+
+extern "C" int fc_support_batch(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *items,
+                                int32_t *support, int32_t *sub_support, float *confidence)
+{
+    if (!c || (nq > 0 && !support)) return fail(FC_ERR_ARG, "fc_support_batch: null argument");
+    DevGuard g(c->device);
+    fc_plan *p = nullptr;
+    int rc = fc_plan_support(c, nq, set_off, items, &p);
+    if (rc != FC_OK) return rc;
+    rc = run_to_host(p, support, sizeof(int32_t) * nq, sub_support, sizeof(int32_t) * p->n_sub,
+                     confidence, sizeof(float) * p->n_sub);
+    fc_plan_free(p);
+    return rc;
+}
+
+// ------------------------------------------------------------------- pairs
+
+namespace {
+
+cudaError_t enqueue_pairs(fc_plan *p, int32_t *pairs, float *mi, cudaStream_t s)
+{
+    fc_ctx *c = p->ctx;
+    PairsParams P = p->pp;
+    P.status = c->d_status;
+    cudaError_t e = cudaMemsetAsync(P.C, 0, sizeof(int32_t) * (size_t)P.R_pad * P.R_pad, s);
+    if (e != cudaSuccess) return e;
+    e = launch_pairs_gemm(P, s);
+    if (e != cudaSuccess) return e;
+    if (!pairs && !mi) return cudaSuccess;
+    return launch_pairs_extract(P.C, P.R_pad, c->n, c->d_arity, c->d_soff, p->d_pair_off, c->m, pairs, mi, s);
+}
+
+}  // namespace
+
+extern "C" int64_t fc_pairs_cells(const fc_ctx *c)
+{
+    if (!c || c->transactions) return -1;
+    int64_t cells = 0;
+    for (int a = 0; a < c->n; ++a)
+        for (int b = a + 1; b < c->n; ++b) cells += (int64_t)c->arity[a] * c->arity[b];
+    return cells;
+}
+
+extern "C" int fc_plan_pairs(fc_ctx *c, fc_plan **out)
+{
+    if (!c || !out) return fail(FC_ERR_ARG, "fc_plan_pairs: null argument");
+    *out = nullptr;
+    if (c->transactions) return fail(FC_ERR_STATE, "all-pairs tables need a categorical context");
+    DevGuard g(c->device);
+    fc_plan *p = new (std::nothrow) fc_plan();
+    if (!p) return fail(FC_ERR_OOM, "host allocation failed");
+    p->ctx = c;
+    p->kind = kPlanPairs;
+    p->nq = 0;
+    const int32_t R_pad = (int32_t)round_up(c->R, 256);
+    const int64_t npairs = (int64_t)c->n * (c->n - 1) / 2;
+    p->n_pairs = npairs;
+    std::vector<int64_t> off(npairs + 1, 0);
+    int64_t idx = 0;
+    for (int a = 0; a < c->n; ++a)
+        for (int b = a + 1; b < c->n; ++b, ++idx) off[idx + 1] = off[idx] + (int64_t)c->arity[a] * c->arity[b];
+    p->pair_cells = off[npairs];
+    cudaError_t e = p->pairs_C.ensure(sizeof(int32_t) * (size_t)R_pad * R_pad);
+    if (e == cudaSuccess) e = p->pairs_meta.ensure(sizeof(int64_t) * (npairs + 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->pairs_meta.p, off.data(), sizeof(int64_t) * (npairs + 1), cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        fc_plan_free(p);
+        return cuda_fail(e, "pairs plan");
+    }
+    p->d_pair_off = (int64_t *)p->pairs_meta.p;
+    PairsParams &P = p->pp;
+    P.bits = c->d_bits;
+    P.wstride = c->wstride;
+    P.words = c->words;
+    P.R = c->R;
+    P.R_pad = R_pad;
+    P.C = (int32_t *)p->pairs_C.p;
+    const int64_t chunk_words = std::max<int64_t>(2, c->opt.pair_chunk_rows / 64 / 2 * 2);
+    // row splits: enough CTAs to fill the GPU and at most chunk_words per split
+    const int32_t tiles = pairs_tile_count(R_pad);
+    int64_t ksplit = std::max<int64_t>(1, (c->words + chunk_words - 1) / chunk_words);
+    const int64_t want = std::max<int64_t>(1, (2 * c->num_sms + tiles - 1) / tiles);
+    ksplit = std::max(ksplit, want);
+    ksplit = std::min<int64_t>(ksplit, std::max<int64_t>(1, (c->words + 1) / 2));
+    P.ksplit = (int32_t)ksplit;
+    P.chunk_words = (int32_t)chunk_words;
+    P.wait_limit = c->opt.wait_limit;
+    *out = p;
+    return FC_OK;
+}
+
+extern "C" int fc_pairs_all(fc_ctx *c, int32_t *pair_tables, float *mi)
+{
+    if (!c) return fail(FC_ERR_ARG, "fc_pairs_all: null context");
+    DevGuard g(c->device);
+    fc_plan *p = nullptr;
+    int rc = fc_plan_pairs(c, &p);
+    if (rc != FC_OK) return rc;
+    rc = run_to_host(p, pair_tables, pair_tables ? sizeof(int32_t) * p->pair_cells : 0, mi,
+                     mi ? sizeof(float) * p->n_pairs : 0, nullptr, 0);
+    fc_plan_free(p);
+    return rc;
+}
+
+// --------------------------------------------------------- options, errors
+
+namespace {
+
+struct OptDesc {
+    const char *key;
+    int64_t Options::*p64;
+    int32_t Options::*p32;
+    int64_t lo, hi;
+};
+
+const OptDesc kOpts[] = {
+    {"strategy", nullptr, &Options::strategy, -1, 3},
+    {"smem_cells", nullptr, &Options::smem_cells, 256, 1 << 20},
+    {"threads", nullptr, &Options::threads, 32, 1024},
+    {"ctas_per_sm", nullptr, &Options::ctas_per_sm, 1, 32},
+    {"hist_copies", nullptr, &Options::hist_copies, 1, 32},
+    {"min_part_rows", &Options::min_part_rows, nullptr, kChunkRows, (int64_t)1 << 31},
+    {"pair_chunk_rows", &Options::pair_chunk_rows, nullptr, 128, (int64_t)1 << 24},
+    {"use_graph", nullptr, &Options::use_graph, 0, 1},
+    {"wait_limit", &Options::wait_limit, nullptr, 1, (int64_t)1 << 40},
+    {"sort_min_cells", &Options::sort_min_cells, nullptr, 1, (int64_t)1 << 31},
+    {"bitmap_cost", &Options::bitmap_cost, nullptr, 0, (int64_t)1 << 40},
+    {"hist_cost_row", &Options::hist_cost_row, nullptr, 0, (int64_t)1 << 40},
+    {"hist_cost_var", &Options::hist_cost_var, nullptr, 0, (int64_t)1 << 40},
+    {"flush_cost", &Options::flush_cost, nullptr, 0, (int64_t)1 << 40},
+    {"support_warps", nullptr, &Options::support_warps, 1, 32},
+    {"support_sets_per_warp", nullptr, &Options::support_sets_per_warp, 1, 64},
+    {"support_part_words", &Options::support_part_words, nullptr, 64, (int64_t)1 << 40},
+};
+
+}  // namespace
+
+extern "C" int fc_set_option(fc_ctx *c, const char *key, int64_t value)
+{
+    if (!c || !key) return fail(FC_ERR_ARG, "fc_set_option: null argument");
+    for (const OptDesc &d : kOpts)
+        if (std::strcmp(d.key, key) == 0) {
+            if (value < d.lo || value > d.hi)
+                return fail(FC_ERR_ARG, "option %s must be in %lld..%lld", key, (long long)d.lo, (long long)d.hi);
+            if (d.p64) c->opt.*(d.p64) = value;
+            else c->opt.*(d.p32) = (int32_t)value;
+            return FC_OK;
+        }
+    return fail(FC_ERR_ARG, "unknown option %s", key);
+}
+
+extern "C" int64_t fc_get_option(const fc_ctx *c, const char *key)
+{
+    if (!c || !key) return -1;
+    for (const OptDesc &d : kOpts)
+        if (std::strcmp(d.key, key) == 0) return d.p64 ? c->opt.*(d.p64) : (int64_t)(c->opt.*(d.p32));
+    return -1;
+}
+
+extern "C" const char *fc_last_error(void) { return g_err.c_str(); }
+
+extern "C" int fc_selftest_wait_timeout(fc_ctx *c, int64_t wait_limit)
+{
+    if (!c || wait_limit < 1) return fail(FC_ERR_ARG, "fc_selftest_wait_timeout: bad argument");
+    DevGuard g(c->device);
+    cudaError_t e = launch_wait_selftest(c->d_status, wait_limit, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
+    return read_status(c, c->stream);
+}
+
+// ---------------------------------------------------------------- autotune
+
+namespace {
+
+uint64_t lcg(uint64_t &s)
+{
+    s = s * 6364136223846793005ull + 1442695040888963407ull;
+    return s >> 33;
+}
+
+// Time one plan on the context stream with events (best of `reps`).
+double time_plan(fc_plan *p, void *out, int reps)
+{
+    fc_ctx *c = p->ctx;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    double best = 1e30;
+    for (int r = 0; r < reps + 1; ++r) {
+        cudaEventRecord(a, c->stream);
+        run_plan(p, out, nullptr, nullptr, c->stream, false);
+        cudaEventRecord(b, c->stream);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (r > 0) best = std::min(best, (double)ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+}  // namespace
+
+extern "C" int fc_autotune(fc_ctx *c, int32_t budget_ms)
+{
+    if (!c) return fail(FC_ERR_ARG, "fc_autotune: null context");
+    if (c->transactions) return FC_OK;
+    DevGuard g(c->device);
+    (void)budget_ms;
+    const Options saved = c->opt;
+    // Sample queries of sizes 1..6 over the loaded variables (tables that fit
+    // in shared memory), time them with each strategy forced, and fit the
+    // per-unit costs of the model that FC_STRAT_AUTO uses.
+    uint64_t seed = 0x9e3779b97f4a7c15ull;
+    std::vector<int32_t> off{0}, vars;
+    std::vector<int32_t> perm(c->n);
+    const int nq = std::max(4 * c->num_sms * std::max(1, c->opt.ctas_per_sm), 512);
+    double node_chunks = 0, rows_k = 0, rows = 0;
+    for (int q = 0; q < nq; ++q) {
+        const int kmax = std::min(6, c->n);
+        const int k = 1 + (int)(lcg(seed) % kmax);
+        std::iota(perm.begin(), perm.end(), 0);
+        int64_t cells = 1;
+        int used = 0;
+        for (int t = 0; t < c->n && used < k; ++t) {
+            const int j = t + (int)(lcg(seed) % (c->n - t));
+            std::swap(perm[t], perm[j]);
+            if (cells * c->arity[perm[t]] > std::min<int64_t>(c->opt.smem_cells, 4096)) continue;
+            cells *= c->arity[perm[t]];
+            vars.push_back(perm[t]);
+            ++used;
+        }
+        off.push_back((int32_t)vars.size());
+    }
+    double t_strat[2] = {0, 0};
+    for (int s = 0; s < 2; ++s) {
+        c->opt.strategy = s;
+        fc_plan *p = nullptr;
+        if (fc_plan_count(c, nq, off.data(), vars.data(), nullptr, &p) != FC_OK) {
+            c->opt = saved;
+            return FC_ERR_CUDA;
+        }
+        DBuf out;
+        if (out.ensure(sizeof(int32_t) * std::max<int64_t>(p->out_cells, 1)) != cudaSuccess) {
+            fc_plan_free(p);
+            c->opt = saved;
+            return fail(FC_ERR_OOM, "autotune buffer");
+        }
+        t_strat[s] = time_plan(p, out.p, 3);
+        if (s == 0) {
+            // model units of this batch
+            std::vector<QHead> qh(nq);
+            std::vector<QVar> qv;
+            for (int q = 0; q < nq; ++q) {
+                int32_t ke = 0;
+                const size_t first = qv.size();
+                describe(c, vars.data() + off[q], off[q + 1] - off[q], qv, ke);
+                node_chunks += dfs_nodes(qv.data() + first, ke) * (double)((c->m + kChunkRows - 1) / kChunkRows);
+                rows_k += (double)c->m * ke;
+                rows += (double)c->m;
+            }
+        }
+        out.release();
+        fc_plan_free(p);
+    }
+    c->opt = saved;
+    // times in femtoseconds per model unit across the whole GPU
+    const double fs0 = t_strat[0] * 1e12, fs1 = t_strat[1] * 1e12;
+    if (node_chunks > 0) c->opt.bitmap_cost = (int64_t)std::max(1.0, fs0 / node_chunks);
+    if (rows_k > 0) {
+        // split the histogram time between the per-row and per-variable terms
+        // in the ratio of the defaults
+        const double base = (double)saved.hist_cost_row * rows + (double)saved.hist_cost_var * rows_k;
+        const double scale = base > 0 ? fs1 / base : 1.0;
+        c->opt.hist_cost_row = (int64_t)std::max(1.0, saved.hist_cost_row * scale);
+        c->opt.hist_cost_var = (int64_t)std::max(1.0, saved.hist_cost_var * scale);
+    }
+    return FC_OK;
+}

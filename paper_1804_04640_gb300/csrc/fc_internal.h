@@ -1,0 +1,157 @@
+// fc_internal.h -- device descriptors and kernel launchers shared by the
+// host runtime (fc_api.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fc {
+
+constexpr int kMaxK = 32;          // variables of one query in a device descriptor
+constexpr int kMaxBitmapK = 8;     // deepest DFS the bitmap kernel is instantiated for
+constexpr int kChunkRows = 4096;   // row granule of work items (64 words of 64 bits)
+constexpr int kChunkWords = kChunkRows / 64;
+
+enum Strategy : int32_t { kBitmap = 0, kHist = 1, kGAtomic = 2, kSort = 3 };
+enum ScoreKind : int32_t { kNoScore = -1, kLL = 0, kMDL = 1, kBDeu = 2, kMI = 3 };
+
+// Status word values written by kernels (0 = fine).
+enum DeviceStatus : int32_t { kStatusOk = 0, kStatusTimeout = 1, kStatusBadState = 2 };
+
+// One query of a count or score batch.
+struct QHead {
+    int64_t table_off;   // first cell of this query's table in the table buffer
+    int32_t cells;       // table cells
+    int32_t var_off;     // first entry in the QVar array
+    int16_t k;           // variables in the descriptor (arity-1 variables dropped)
+    int16_t strategy;    // Strategy
+    int16_t nparts;      // work items the query's rows are split into
+    int16_t score_kind;  // ScoreKind
+    int32_t r_child;     // arity of the child (score queries: child is the last, stride 1)
+    int32_t child_soff;  // state offset of the child (marginals for MI)
+    int32_t score_slot;  // index into the score output
+    int32_t pad;
+};
+
+// One variable of a query.  stride is the variable's weight in the cell index
+// of the table in the caller's variable order; soff is the first bitmap row
+// (= sum of the arities of the variables before it).
+struct QVar {
+    int32_t var;
+    int32_t stride;
+    int32_t arity;
+    int32_t soff;
+};
+
+struct Item {
+    int32_t q;
+    int32_t part;
+};
+
+struct CountParams {
+    const uint8_t *D;        // n columns of m_pad bytes
+    int64_t m_pad;
+    int64_t m;
+    const uint64_t *bits;    // sum(r) rows of wstride words
+    int64_t wstride;
+    const QHead *qh;
+    const QVar *qv;
+    const Item *items;
+    int32_t n_items;
+    int32_t *next_item;      // work counter, zero before the launch
+    int32_t *tables;         // table buffer (output, or plan scratch for scores)
+    int32_t *tickets;        // per query, zero before the launch (nparts > 1 scoring)
+    float *scores;
+    const int64_t *marg;     // per-state marginal counts
+    double ess;
+    int32_t write_tables;    // 1: every cell is written (nparts == 1 queries store zeros too)
+    int32_t smem_cells;      // int32 cells of dynamic shared memory for tables
+    int32_t hist_copies;     // maximum table copies for the histogram strategy
+    int32_t pad;
+};
+
+// Launchers (each defined in the translation unit holding its kernel).
+cudaError_t launch_pack_bits(const uint8_t *D, int64_t m_pad, int64_t m, int32_t n,
+                             const int32_t *d_arity, const int32_t *d_soff, uint64_t *bits,
+                             int64_t wstride, int32_t max_arity, int32_t *bad_state,
+                             cudaStream_t s);
+cudaError_t launch_bit_popcounts(const uint64_t *bits, int64_t rows, int64_t wstride,
+                                 int64_t *counts, cudaStream_t s);
+cudaError_t launch_transpose_rows(const uint8_t *Drow, int64_t m, int32_t n, uint8_t *Dcol,
+                                  int64_t m_pad, cudaStream_t s);
+cudaError_t launch_mask_tail_bits(uint64_t *bits, int64_t rows, int64_t wstride, int64_t m,
+                                  cudaStream_t s);
+
+cudaError_t launch_count(const CountParams &p, int grid, int threads, size_t smem, cudaStream_t s);
+int count_kernel_max_smem();
+
+// Sort + run-length path for one query (large tables).
+struct SortScratch {
+    uint32_t *keys_a;
+    uint32_t *keys_b;
+    uint32_t *block_hist;    // 256 x nblocks
+    int64_t cap_rows;
+    int32_t cap_blocks;
+};
+int sort_tile_rows();
+cudaError_t launch_sort_count(const uint8_t *D, int64_t m_pad, int64_t m, const QVar *d_vars,
+                              int32_t k, int32_t key_bits, int32_t *table, int32_t cells,
+                              int32_t zero_table, SortScratch sc, cudaStream_t s);
+
+// Scores of queries whose tables are complete in global memory.
+cudaError_t launch_score_global(const QHead *qh, const int32_t *q_list, int32_t nlist,
+                                const int32_t *tables, float *scores, const int64_t *marg,
+                                int64_t m, double ess, cudaStream_t s);
+
+// Specific-assignment count: AND of k bitmap rows, popcount.
+cudaError_t launch_assignment_count(const uint64_t *bits, int64_t wstride, const int32_t *d_rows,
+                                    int32_t k, int64_t words, unsigned long long *out,
+                                    cudaStream_t s);
+
+// Itemset supports (binary transaction bitmaps).
+struct SupportParams {
+    const uint64_t *bits;    // n_items rows of wstride words
+    int64_t wstride;
+    int64_t words;           // ceil(m / 64)
+    const int32_t *set_off;  // nq + 1
+    const int32_t *items;
+    const int32_t *order;    // itemsets in processing order (grouped by size)
+    int32_t nq;
+    int32_t n_items;
+    int32_t *support;
+    int32_t *sub_support;
+    float *confidence;
+    int32_t *next_item;      // work counter
+    int32_t words_per_part;  // word range of one work item
+    int32_t nparts;
+    int32_t sets_per_item;   // itemsets one CTA takes per work item
+    int32_t pad;
+    int64_t m_tail;          // m: bits at positions >= m are not transactions
+};
+cudaError_t launch_support(const SupportParams &p, int grid, int threads, size_t smem,
+                           cudaStream_t s);
+cudaError_t launch_support_confidence(const SupportParams &p, cudaStream_t s);
+const void *support_kernel_ptr();
+
+// All-pairs one-hot co-occurrence on tcgen05 tensor cores.
+struct PairsParams {
+    const uint64_t *bits;    // R rows of wstride words (one row per (variable, state))
+    int64_t wstride;
+    int64_t words;           // ceil(m / 64)
+    int32_t R;               // sum of arities
+    int32_t R_pad;           // padded to the tile size
+    int32_t *C;              // R_pad x R_pad int32 co-occurrence (upper tiles), zeroed
+    int32_t chunk_words;     // words accumulated in FP32 before the move to int32
+    int32_t ksplit;          // row splits per tile
+    int32_t *status;
+    int64_t wait_limit;
+};
+cudaError_t launch_pairs_gemm(const PairsParams &p, cudaStream_t s);
+int pairs_tile_count(int32_t R_pad);
+cudaError_t launch_pairs_extract(const int32_t *C, int32_t R_pad, int32_t n, const int32_t *d_arity,
+                                 const int32_t *d_soff, const int64_t *d_pair_off, int64_t m,
+                                 int32_t *pair_tables, float *mi, cudaStream_t s);
+
+cudaError_t launch_wait_selftest(int32_t *status, int64_t wait_limit, cudaStream_t s);
+
+}  // namespace fc

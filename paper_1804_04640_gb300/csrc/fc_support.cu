@@ -1,0 +1,171 @@
+// fc_support.cu -- support and confidence of association rules (Sec. 4.3).
+//
+// For an itemset S of k items the Bitmap strategy's specific-assignment query
+// (end of Sec. 3.3) is the AND of the k item bitmaps followed by a bit count.
+// Rules with a single-item consequent, (S without x) => x, also need the k
+// leave-one-out supports; with prefix ANDs p_t = a_0 & ... & a_{t-1} and
+// suffix ANDs s_t = a_{t+1} & ... & a_{k-1}, the leave-one-out set of item t
+// is p_t & s_t, so one pass over the words yields all k + 1 counts.
+//
+// A warp owns one itemset at a time; its lanes read 32 consecutive 64-bit
+// words of every item row (coalesced 256-byte loads) and keep the k + 1
+// counts in registers.  Work items are (word range, group of itemsets),
+// issued range-major, so all CTAs sweep the same slice of the item bitmaps at
+// the same time and the slice stays in L2 while every itemset passes over it.
+#include "fc_internal.h"
+
+namespace fc {
+namespace {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+template <int K>
+__device__ __forceinline__ void support_set(const SupportParams &P, const int32_t *items,
+                                            int64_t w0, int64_t w1, int lane, int32_t *supp,
+                                            int32_t *sub, bool atomic)
+{
+    const uint64_t *row[K > 0 ? K : 1];
+#pragma unroll
+    for (int t = 0; t < K; ++t) row[t] = P.bits + (int64_t)items[t] * P.wstride;
+    unsigned full = 0u;
+    unsigned loo[K > 0 ? K : 1];
+#pragma unroll
+    for (int t = 0; t < K; ++t) loo[t] = 0u;
+    const int64_t last = P.words - 1;
+    const int rem = (int)(P.m_tail & 63);
+    const uint64_t tail = rem ? ((1ull << rem) - 1ull) : ~0ull;
+    for (int64_t w = w0 + lane; w < w1; w += 32) {
+        uint64_t a[K > 0 ? K : 1];
+#pragma unroll
+        for (int t = 0; t < K; ++t) a[t] = __ldg(row[t] + w);
+        uint64_t pre[K + 1];
+        pre[0] = w == last ? tail : ~0ull;
+#pragma unroll
+        for (int t = 0; t < K; ++t) pre[t + 1] = pre[t] & a[t];
+        uint64_t suf = ~0ull;
+#pragma unroll
+        for (int t = K - 1; t >= 0; --t) {
+            loo[t] += (unsigned)__popcll(pre[t] & suf);
+            suf &= a[t];
+        }
+        full += (unsigned)__popcll(pre[K]);
+    }
+    full = __reduce_add_sync(kFullMask, full);
+#pragma unroll
+    for (int t = 0; t < K; ++t) loo[t] = __reduce_add_sync(kFullMask, loo[t]);
+    if (lane == 0) {
+        if (atomic) {
+            if (full) atomicAdd(supp, (int)full);
+#pragma unroll
+            for (int t = 0; t < K; ++t)
+                if (loo[t]) atomicAdd(sub + t, (int)loo[t]);
+        } else {
+            *supp = (int)full;
+#pragma unroll
+            for (int t = 0; t < K; ++t) sub[t] = (int)loo[t];
+        }
+    }
+}
+
+// Itemsets larger than the unrolled sizes: the k + 1 ANDs recomputed per word.
+__device__ void support_set_any(const SupportParams &P, const int32_t *items, int k, int64_t w0,
+                                int64_t w1, int lane, int32_t *supp, int32_t *sub, bool atomic)
+{
+    const int64_t last = P.words - 1;
+    const int rem = (int)(P.m_tail & 63);
+    const uint64_t tail = rem ? ((1ull << rem) - 1ull) : ~0ull;
+    for (int t = -1; t < k; ++t) {
+        unsigned cnt = 0u;
+        for (int64_t w = w0 + lane; w < w1; w += 32) {
+            uint64_t x = w == last ? tail : ~0ull;
+            for (int u = 0; u < k; ++u)
+                if (u != t) x &= __ldg(P.bits + (int64_t)items[u] * P.wstride + w);
+            cnt += (unsigned)__popcll(x);
+        }
+        cnt = __reduce_add_sync(kFullMask, cnt);
+        if (lane == 0) {
+            int32_t *dst = t < 0 ? supp : sub + t;
+            if (atomic) {
+                if (cnt) atomicAdd(dst, (int)cnt);
+            } else {
+                *dst = (int)cnt;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) support_kernel(const SupportParams P)
+{
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t ngroups = ((int64_t)P.nq + P.sets_per_item - 1) / P.sets_per_item;
+    const int64_t n_work = ngroups * P.nparts;
+    const bool atomic = P.nparts > 1;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(P.next_item, 1);
+        __syncthreads();
+        const int64_t it = s_item;
+        __syncthreads();
+        if (it >= n_work) break;
+        const int64_t part = it / ngroups, group = it % ngroups;
+        const int64_t w0 = part * P.words_per_part;
+        const int64_t w1 = min(P.words, w0 + P.words_per_part);
+        const int64_t g0 = group * P.sets_per_item;
+        const int64_t g1 = min((int64_t)P.nq, g0 + P.sets_per_item);
+        for (int64_t i = g0 + warp; i < g1; i += nwarps) {
+            const int32_t q = P.order[i];
+            const int32_t a = P.set_off[q], k = P.set_off[q + 1] - a;
+            const int32_t *items = P.items + a;
+            int32_t *supp = P.support + q;
+            int32_t *sub = P.sub_support + a;
+            switch (k) {
+            case 0: support_set<0>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 1: support_set<1>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 2: support_set<2>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 3: support_set<3>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 4: support_set<4>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 5: support_set<5>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 6: support_set<6>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 7: support_set<7>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 8: support_set<8>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            default: support_set_any(P, items, k, w0, w1, lane, supp, sub, atomic); break;
+            }
+        }
+    }
+}
+
+// conf((S without item t) => item t) = supp(S) / supp(S without item t), 0 when
+// the denominator is 0 (then supp(S) is 0 as well).
+__global__ void confidence_kernel(const SupportParams P)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < P.nq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = P.set_off[q], b = P.set_off[q + 1];
+        const float s = (float)P.support[q];
+        for (int32_t t = a; t < b; ++t) {
+            const int32_t d = P.sub_support[t];
+            P.confidence[t] = d > 0 ? __fdiv_rn(s, (float)d) : 0.0f;
+        }
+    }
+}
+
+}  // namespace
+
+const void *support_kernel_ptr() { return (const void *)support_kernel; }
+
+cudaError_t launch_support(const SupportParams &p, int grid, int threads, size_t smem, cudaStream_t s)
+{
+    support_kernel<<<grid, threads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_support_confidence(const SupportParams &p, cudaStream_t s)
+{
+    int64_t blocks = ((int64_t)p.nq + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    confidence_kernel<<<(unsigned)blocks, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace fc

@@ -1,0 +1,199 @@
+"""GPU parity of counting queries (C ABI) against the CPU oracle.
+
+Counts must match bit-exactly, for every strategy, at sizes that span several
+4096-row work granules with a ragged tail, at the full sizes of the tiny and
+batched-random workloads, and on the edge cases of the method.
+"""
+import concurrent.futures as cf
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1804_04640_gb300 as fc
+from workloads import CONFIGS, config_database, random_dag_database, random_queries, subset_queries
+
+pytestmark = pytest.mark.gpu
+
+STRATS = [fc.FC_STRAT_BITMAP, fc.FC_STRAT_HIST, fc.FC_STRAT_GATOMIC, fc.FC_STRAT_SORT]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    fc.load_library(build_if_missing=True)
+
+
+def oracle_tables(orc, queries):
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        return list(ex.map(orc.table, queries))
+
+
+def check_batch(ctx, orc, queries, want=None):
+    off, flat = fc.pack_lists(queries)
+    tables, toff = fc.fc_count_batch(ctx, off, flat)
+    if want is None:
+        want = oracle_tables(orc, queries)
+    for q, w in enumerate(want):
+        got = tables[toff[q]:toff[q + 1]].astype(np.int64)
+        assert np.array_equal(got, w), f"query {q} {queries[q]}"
+    return want
+
+
+def test_tiny_all_92_queries():
+    """Tiny workload: n=8, m=1000, all 92 subsets of size 1-3."""
+    db = config_database("tiny")
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    queries = subset_queries(db.n, (1, 2, 3))
+    assert len(queries) == 92
+    want = check_batch(ctx, orc, queries)
+    for s in STRATS:
+        fc.fc_set_option(ctx, "strategy", s)
+        check_batch(ctx, orc, queries, want)
+    fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_AUTO)
+    for q in queries[::7]:                       # single-query entry point
+        assert np.array_equal(fc.fc_count(ctx, q).astype(np.int64), orc.table(q))
+
+
+def test_random_full_size_all_queries():
+    """Batched random workload at full size: 10,000 queries, m = 100,000."""
+    c = CONFIGS["random"]
+    db = config_database("random")
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    queries = random_queries(db.n, c["nq"], c["k"][0], c["k"][1], c["seed"])
+    want = check_batch(ctx, orc, queries)
+    sub = queries[::25]
+    for s in STRATS:
+        fc.fc_set_option(ctx, "strategy", s)
+        check_batch(ctx, orc, sub, want[::25])
+
+
+@pytest.mark.parametrize("m", [1, 17, 63, 64, 65, 4095, 4096, 4097, 70_001, 131_072 + 13])
+def test_ragged_sizes_every_strategy(m):
+    db = random_dag_database(9, m, 2, 5, 3, 0.5, seed=1000 + m % 97)
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    queries = random_queries(db.n, 60, 1, 6, seed=m) + [[0], [8, 3]]
+    want = oracle_tables(orc, queries)
+    for s in [fc.FC_STRAT_AUTO] + STRATS:
+        fc.fc_set_option(ctx, "strategy", s)
+        check_batch(ctx, orc, queries, want)
+
+
+def test_row_split_work_items():
+    """Few queries over many rows: the planner splits rows across CTAs and
+    the partial tables are summed in global memory."""
+    db = random_dag_database(10, 600_000 + 77, 2, 4, 3, 0.5, seed=5)
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    queries = [[0, 1], [2, 3, 4], [5], [9, 8, 7, 6]]
+    want = oracle_tables(orc, queries)
+    for s in [fc.FC_STRAT_AUTO] + STRATS:
+        fc.fc_set_option(ctx, "strategy", s)
+        check_batch(ctx, orc, queries, want)
+
+
+def test_large_tables_sort_and_global_paths():
+    """Tables above the shared-memory threshold (up to 16^5 cells)."""
+    db = random_dag_database(8, 300_001, 12, 16, 2, 0.3, seed=9)
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    queries = [[0, 1, 2, 3, 4], [5, 6, 7, 0], [1, 2, 3]]
+    want = oracle_tables(orc, queries)
+    check_batch(ctx, orc, queries, want)
+    for s in (fc.FC_STRAT_GATOMIC, fc.FC_STRAT_SORT):
+        fc.fc_set_option(ctx, "strategy", s)
+        check_batch(ctx, orc, queries, want)
+    fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_AUTO)
+    fc.fc_set_option(ctx, "sort_min_cells", 1000)      # route big tables to sort
+    check_batch(ctx, orc, queries, want)
+    fc.fc_set_option(ctx, "smem_cells", 256)           # everything leaves shared memory
+    check_batch(ctx, orc, queries, want)
+
+
+def test_edge_cases():
+    D = np.array([[0, 1, 0, 1, 1], [0, 0, 0, 0, 0], [2, 1, 0, 2, 2]], dtype=np.uint8)
+    ar = [2, 1, 3]
+    ctx = fc.fc_load(D, ar)
+    orc = oracle.DB(D, ar)
+    assert fc.fc_count(ctx, []).tolist() == [5]                    # k = 0: the single cell m
+    assert fc.fc_count(ctx, [1]).tolist() == [5]                   # arity-1 variable
+    for q in ([1, 0], [0, 1, 2], [2, 1], [2, 0, 1]):
+        assert np.array_equal(fc.fc_count(ctx, q).astype(np.int64), orc.table(q))
+    with pytest.raises(fc.FcError) as e:
+        fc.fc_count(ctx, [0, 0])                                   # duplicate variable
+    assert e.value.code == fc.FC_ERR_ARG
+    with pytest.raises(fc.FcError) as e:
+        fc.fc_count(ctx, [3])                                      # out of range
+    assert e.value.code == fc.FC_ERR_ARG
+    with pytest.raises(fc.FcError) as e:
+        fc.fc_load(np.array([[0, 2]], dtype=np.uint8), [2])        # state >= arity
+    assert e.value.code == fc.FC_ERR_RANGE
+    big = fc.fc_load(np.zeros((9, 3), dtype=np.uint8), [255] * 9)
+    with pytest.raises(fc.FcError) as e:
+        fc.fc_count(big, list(range(9)))                           # 255^9 cells
+    assert e.value.code == fc.FC_ERR_SIZE
+    # empty batch
+    tables, toff = fc.fc_count_batch(ctx, np.zeros(1, dtype=np.int32), np.zeros(0, dtype=np.int32))
+    assert toff.tolist() == [0]
+
+
+def test_row_major_load_and_assignment_count():
+    """fc_load with a row-major database; Count of a specific assignment
+    (the worked example of Sec. 2 lives in tests/golden)."""
+    rows = [[int(x) for x in line.split()] for line in open(
+        os.path.join(os.path.dirname(__file__), "golden", "worked_example.txt"))
+        if line.strip() and line[0].isdigit()]
+    R = np.array(rows, dtype=np.uint8) - 1                     # (m, n), 0-based
+    ctx = fc.fc_load(R, [3, 2, 2], layout=fc.FC_ROW_MAJOR)
+    assert fc.fc_count_assignment(ctx, [0, 1, 2], [2, 1, 0]) == 2
+    orc = oracle.DB(R.T, [3, 2, 2])
+    for q in ([0], [2, 0], [1, 2, 0]):
+        assert np.array_equal(fc.fc_count(ctx, q).astype(np.int64), orc.table(q))
+    db = random_dag_database(7, 50_001, 2, 4, 2, 0.5, seed=3)
+    ctx2 = fc.fc_load(db.D, db.arities)
+    orc2 = oracle.DB(db.D, db.arities)
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        k = int(rng.integers(1, 5))
+        vs = [int(x) for x in rng.choice(7, size=k, replace=False)]
+        st = [int(rng.integers(0, db.arities[v])) for v in vs]
+        assert fc.fc_count_assignment(ctx2, vs, st) == orc2.count_assignment(vs, st)
+    assert fc.fc_count_assignment(ctx2, [0], [200]) == 0
+
+
+def test_plan_graph_replay_on_stream_is_deterministic():
+    torch = pytest.importorskip("torch")
+    db = config_database("random")
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    queries = random_queries(db.n, 2000, 2, 6, seed=77)
+    off, flat = fc.pack_lists(queries)
+    plan = fc.fc_plan_count(ctx, off, flat)
+    toff = fc.fc_plan_table_offsets(plan)
+    out = torch.zeros(int(toff[-1]), dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    results = []
+    for _ in range(3):
+        out.fill_(-7)
+        s.wait_stream(torch.cuda.current_stream())
+        fc.fc_plan_run(plan, out, stream=s)
+        fc.fc_sync(ctx, s)
+        results.append(out.cpu().numpy().copy())
+    assert all(np.array_equal(results[0], r) for r in results[1:])
+    want = oracle_tables(orc, queries)
+    for q, w in enumerate(want):
+        assert np.array_equal(results[0][toff[q]:toff[q + 1]].astype(np.int64), w)
+    strat = fc.fc_plan_strategies(plan)
+    assert set(np.unique(strat)) <= {fc.FC_STRAT_BITMAP, fc.FC_STRAT_HIST}
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    db = random_dag_database(5, 10_000, 2, 3, 2, 0.5, seed=8)
+    ctx = fc.fc_load(db.D, db.arities)
+    assert fc.fc_selftest_wait_timeout(ctx, 2000) == fc.FC_ERR_TIMEOUT
+    orc = oracle.DB(db.D, db.arities)
+    assert np.array_equal(fc.fc_count(ctx, [0, 1]).astype(np.int64), orc.table([0, 1]))
+    fc.fc_sync(ctx)                                            # status was cleared

@@ -172,7 +172,9 @@ def weighted_itemsets(n_items: int, nq: int, k_lo: int, k_hi: int,
     for k in range(k_lo, k_hi + 1):
         slots = np.nonzero(sizes == k)[0]
         fill = 0
+        stalled = 0
         while fill < len(slots):
+            before = fill
             want = len(slots) - fill
             batch = max(64, int(want * 1.2))
             draws = np.empty((batch, k), dtype=np.int64)
@@ -196,6 +198,10 @@ def weighted_itemsets(n_items: int, nq: int, k_lo: int, k_hi: int,
                 fill += 1
                 if fill == len(slots):
                     break
+            stalled = stalled + 1 if fill == before else 0
+            if stalled > 50:
+                raise ValueError(f"cannot draw {len(slots)} distinct itemsets of size {k} "
+                                 f"from {n_items} items")
     return out
 
 
