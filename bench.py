@@ -268,6 +268,7 @@ def run_gpu(args, rank: int, world: int):
         ctx = fc.fc_load(db.D, db.arities)
         if args.autotune:
             fc.fc_autotune(ctx)
+        fc.fc_set_option(ctx, "strategy", args.strategy)
         off, flat = fc.pack_lists(queries)
         plan = fc.fc_plan_count(ctx, off, flat)
         toff = fc.fc_plan_table_offsets(plan)
@@ -297,6 +298,7 @@ def run_gpu(args, rank: int, world: int):
         ctx = fc.fc_load(db.D, db.arities)
         if args.autotune:
             fc.fc_autotune(ctx)
+        fc.fc_set_option(ctx, "strategy", args.strategy)
         po, pa = fc.pack_lists(w["parents"])
         plan = fc.fc_plan_score(ctx, w["child"], po, pa, "bdeu", 1.0)
         outs = (torch.empty(len(w["child"]), dtype=torch.float32, device="cuda"),)
@@ -422,6 +424,8 @@ def run_gpu(args, rank: int, world: int):
         cfg["l2"] = "flushed between timed steps (256 MiB write)"
         if strategies is not None:
             cfg["strategies"] = dict(zip(["bitmap", "hist", "gatomic", "sort"], strategies))
+            cfg["cost_model_fs"] = {k: fc.fc_get_option(ctx, k) for k in
+                                    ("bitmap_cost", "hist_cost_row", "hist_cost_var")}
         cores = os.cpu_count() or 1
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -460,6 +464,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--strategy", type=int, default=-1, help="force one counting strategy (-1 = planner's choice)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -100,10 +100,12 @@ struct Options {
     int64_t sort_min_cells = 1 << 25;
     // cost model, femtoseconds: bitmap per DFS node per 4096-row chunk;
     // histogram per row and per row-variable; per table cell flushed
-    int64_t bitmap_cost = 13000;
-    int64_t hist_cost_row = 150;
-    int64_t hist_cost_var = 130;
+    int64_t bitmap_cost = 200000;
+    int64_t hist_cost_row = 143;
+    int64_t hist_cost_var = 124;
     int64_t flush_cost = 160;
+    int32_t stage_slots = 16;         // bitmap rows a warp stages per chunk
+    int32_t bitmap_threads = 256;
     int32_t support_warps = 16;
     int32_t support_sets_per_warp = 4;
     int64_t support_part_words = 8192;
@@ -176,6 +178,8 @@ struct fc_plan {
     Item *d_items = nullptr;
     int32_t *d_qlist = nullptr;
     int32_t n_items = 0, n_qlist = 0, n_counters = 0;
+    int32_t *d_bq = nullptr;
+    int32_t n_bq = 0, tasks_per_query = 1, bm_grid = 0, bm_threads = 0, stage_slots = 0;
     bool zero_tables = false;
     int64_t table_buf_cells = 0;  // cells of the buffer the kernel writes
     int score_kind = kNoScore;
@@ -442,6 +446,23 @@ struct QPlan {
     double cost;  // femtoseconds for the whole query
 };
 
+// The bitmap DFS visits variables in ascending entropy (Sec. 3.2); a warp
+// stages the state bitmaps of every level but the first.
+void entropy_order(const fc_ctx *c, QVar *v, int k)
+{
+    std::stable_sort(v, v + k, [&](const QVar &a, const QVar &b) { return c->entropy[a.var] < c->entropy[b.var]; });
+}
+
+bool bitmap_ok(const fc_ctx *c, const QVar *v, int k)
+{
+    if (k < 1 || k > kMaxBitmapK) return false;
+    std::vector<QVar> o(v, v + k);
+    entropy_order(c, o.data(), k);
+    int slots = 0;
+    for (int t = 1; t < k; ++t) slots += o[t].arity;
+    return slots <= c->opt.stage_slots;
+}
+
 QPlan choose(const fc_ctx *c, const QVar *v, int k, int64_t cells, int32_t smem_cells)
 {
     const Options &o = c->opt;
@@ -449,11 +470,19 @@ QPlan choose(const fc_ctx *c, const QVar *v, int k, int64_t cells, int32_t smem_
     const double rows = (double)c->m;
     const double flush = (double)cells * o.flush_cost;
     const bool fits = cells <= smem_cells;
+    const bool bm = bitmap_ok(c, v, k);
+    double nodes = 0.0;
+    if (bm) {
+        std::vector<QVar> ord(v, v + k);
+        entropy_order(c, ord.data(), k);
+        nodes = dfs_nodes(ord.data(), k);
+    }
     const double hist = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) + flush;
-    const double bitmap = (k <= kMaxBitmapK && fits) ? chunks * dfs_nodes(v, k) * o.bitmap_cost + flush : 1e300;
+    const double bitmap = bm ? chunks * nodes * o.bitmap_cost + flush : 1e300;
     const double gatomic = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) * 2.0 + (double)cells * 4.0;
     int32_t s = o.strategy;
-    if (s == FC_STRAT_BITMAP && !(k <= kMaxBitmapK && fits)) s = FC_STRAT_AUTO;
+    if (k == 0) s = fits ? FC_STRAT_HIST : FC_STRAT_GATOMIC;
+    if (s == FC_STRAT_BITMAP && !bm) s = FC_STRAT_AUTO;
     if (s == FC_STRAT_HIST && !fits) s = FC_STRAT_AUTO;
     if (s == FC_STRAT_AUTO) {
         if (fits)
@@ -506,10 +535,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
             return (int)cells;
         }
         QPlan ch = choose(c, qv.data() + first, k_eff, cells, max_cells);
-        if (ch.strategy == FC_STRAT_BITMAP)  // Sec. 3.2: lowest entropy at the top of the tree
-            std::stable_sort(qv.begin() + first, qv.end(), [&](const QVar &a, const QVar &b) {
-                return c->entropy[a.var] < c->entropy[b.var];
-            });
+        if (ch.strategy == FC_STRAT_BITMAP) entropy_order(c, qv.data() + first, k_eff);
         QHead &h = qh[q];
         h.cells = (int32_t)cells;
         h.var_off = (int32_t)first;
@@ -550,7 +576,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     const int64_t max_parts_rows = std::max<int64_t>(1, c->m / std::max<int64_t>(o.min_part_rows, kChunkRows));
     int32_t persistent = 0;
     for (int32_t q = 0; q < nq; ++q)
-        if (qh[q].strategy != kSort) ++persistent;
+        if (qh[q].strategy == kHist || qh[q].strategy == kGAtomic) ++persistent;
     const int64_t target = (int64_t)p->grid * 4;
     int64_t parts = 1;
     if (persistent > 0 && persistent < target)
@@ -559,10 +585,15 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     std::vector<Item> items;
     std::vector<std::pair<double, Item>> order;
     std::vector<int32_t> qlist;
+    std::vector<std::pair<double, int32_t>> bmo;
     for (int32_t q = 0; q < nq; ++q) {
         QHead &h = qh[q];
         if (h.strategy == kSort) {
             p->sort_jobs.push_back(SortJob{q, h.k, 0, h.cells, 0, nullptr});
+            continue;
+        }
+        if (h.strategy == kBitmap) {
+            bmo.push_back({cost[q], q});
             continue;
         }
         h.nparts = (int16_t)parts;
@@ -573,12 +604,29 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     items.reserve(order.size());
     for (auto &x : order) items.push_back(x.second);
     p->n_items = (int32_t)items.size();
+    // bitmap queries: warp tasks of a few 4096-row chunks, heaviest queries first
+    std::stable_sort(bmo.begin(), bmo.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    std::vector<int32_t> bq;
+    for (auto &x : bmo) bq.push_back(x.second);
+    p->n_bq = (int32_t)bq.size();
+    p->bm_threads = std::max(32, std::min(1024, o.bitmap_threads / 32 * 32));
+    p->stage_slots = o.stage_slots;
+    if (p->n_bq > 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bitmap_kernel_ptr(), p->bm_threads,
+                                                      bitmap_smem_bytes(p->bm_threads, p->stage_slots));
+        p->bm_grid = c->num_sms * std::max(1, per_sm);
+        const int64_t warps = (int64_t)p->bm_grid * (p->bm_threads / 32);
+        const int64_t want = (8 * warps + p->n_bq - 1) / p->n_bq;
+        p->tasks_per_query = (int32_t)std::max<int64_t>(1, std::min<int64_t>(nchunks, want));
+        for (int32_t q : bq) qh[q].nparts = (int16_t)std::min<int64_t>(p->tasks_per_query, 32767);
+    }
 
     // tables that must exist in global memory for score plans
     if (score_kind != kNoScore) {
         for (int32_t q = 0; q < nq; ++q) {
             QHead &h = qh[q];
-            const bool global = h.strategy == kGAtomic || h.strategy == kSort || h.nparts > 1;
+            const bool global = h.strategy != kHist || h.nparts > 1;
             if (global) {
                 h.table_off = scratch;
                 scratch += h.cells;
@@ -592,7 +640,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     }
     for (int32_t q = 0; q < nq; ++q) {
         const QHead &h = qh[q];
-        if (h.strategy == kGAtomic || h.strategy == kSort || h.nparts > 1) p->zero_tables = true;
+        if (h.strategy != kHist || h.nparts > 1) p->zero_tables = true;
     }
     for (auto &j : p->sort_jobs) {
         j.table_off = qh[j.q].table_off;
@@ -606,17 +654,20 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     const size_t b_qv = sizeof(QVar) * std::max<size_t>(qv.size(), 1);
     const size_t b_it = sizeof(Item) * std::max<size_t>(items.size(), 1);
     const size_t b_ql = sizeof(int32_t) * std::max<size_t>(qlist.size(), 1);
+    const size_t b_bq = sizeof(int32_t) * std::max<size_t>(bq.size(), 1);
     const size_t o_qv = round_up(b_qh, 256), o_it = o_qv + round_up(b_qv, 256), o_ql = o_it + round_up(b_it, 256);
-    const size_t total = o_ql + round_up(b_ql, 256);
+    const size_t o_bq = o_ql + round_up(b_ql, 256);
+    const size_t total = o_bq + round_up(b_bq, 256);
     std::vector<uint8_t> host(total, 0);
     std::memcpy(host.data(), qh.data(), sizeof(QHead) * nq);
     std::memcpy(host.data() + o_qv, qv.data(), sizeof(QVar) * qv.size());
     std::memcpy(host.data() + o_it, items.data(), sizeof(Item) * items.size());
     std::memcpy(host.data() + o_ql, qlist.data(), sizeof(int32_t) * qlist.size());
+    std::memcpy(host.data() + o_bq, bq.data(), sizeof(int32_t) * bq.size());
     cudaError_t e = p->desc.ensure(total);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->desc.p, host.data(), total, cudaMemcpyHostToDevice, c->stream);
     p->upload_bytes = total;
-    p->n_counters = 1 + nq;
+    p->n_counters = 2 + nq;
     if (e == cudaSuccess) e = p->counters.ensure(sizeof(int32_t) * p->n_counters);
     if (e == cudaSuccess && score_kind != kNoScore) e = p->scratch_tables.ensure(sizeof(int32_t) * std::max<int64_t>(p->table_buf_cells, 1));
     if (e == cudaSuccess && !p->sort_jobs.empty()) {
@@ -643,6 +694,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     p->d_qv = (QVar *)(d + o_qv);
     p->d_items = (Item *)(d + o_it);
     p->d_qlist = (int32_t *)(d + o_ql);
+    p->d_bq = (int32_t *)(d + o_bq);
     for (auto &j : p->sort_jobs) j.d_vars = p->d_qv + qh[j.q].var_off;
     *out = p;
     return FC_OK;
@@ -659,7 +711,7 @@ cudaError_t enqueue_count(fc_plan *p, int32_t *tables, float *scores, cudaStream
         e = cudaMemsetAsync(tab, 0, sizeof(int32_t) * p->table_buf_cells, s);
         if (e != cudaSuccess) return e;
     }
-    if (p->n_items > 0) {
+    if (p->n_items > 0 || p->n_bq > 0) {
         CountParams P{};
         P.D = c->d_D;
         P.m_pad = c->m_pad;
@@ -671,7 +723,12 @@ cudaError_t enqueue_count(fc_plan *p, int32_t *tables, float *scores, cudaStream
         P.items = p->d_items;
         P.n_items = p->n_items;
         P.next_item = (int32_t *)p->counters.p;
-        P.tickets = (int32_t *)p->counters.p + 1;
+        P.next_task = (int32_t *)p->counters.p + 1;
+        P.tickets = (int32_t *)p->counters.p + 2;
+        P.bq = p->d_bq;
+        P.n_bq = p->n_bq;
+        P.tasks_per_query = p->tasks_per_query;
+        P.stage_slots = p->stage_slots;
         P.tables = tab;
         P.scores = scores;
         P.marg = c->d_marg;
@@ -679,9 +736,15 @@ cudaError_t enqueue_count(fc_plan *p, int32_t *tables, float *scores, cudaStream
         P.write_tables = p->kind == kPlanCount ? 1 : 0;
         P.smem_cells = p->smem_cells;
         P.hist_copies = c->opt.hist_copies;
-        const int grid = std::min<int64_t>(p->grid, std::max(p->n_items, 1));
-        e = launch_count(P, grid, p->threads, p->smem, s);
-        if (e != cudaSuccess) return e;
+        if (p->n_bq > 0) {
+            e = launch_bitmap(P, p->bm_grid, p->bm_threads, s);
+            if (e != cudaSuccess) return e;
+        }
+        if (p->n_items > 0) {
+            const int grid = std::min<int64_t>(p->grid, std::max(p->n_items, 1));
+            e = launch_count(P, grid, p->threads, p->smem, s);
+            if (e != cudaSuccess) return e;
+        }
     }
     for (const SortJob &j : p->sort_jobs) {
         e = launch_sort_count(c->d_D, c->m_pad, c->m, j.d_vars, j.k, j.key_bits, tab + j.table_off,
@@ -1216,6 +1279,8 @@ const OptDesc kOpts[] = {
     {"hist_cost_row", &Options::hist_cost_row, nullptr, 0, (int64_t)1 << 40},
     {"hist_cost_var", &Options::hist_cost_var, nullptr, 0, (int64_t)1 << 40},
     {"flush_cost", &Options::flush_cost, nullptr, 0, (int64_t)1 << 40},
+    {"stage_slots", nullptr, &Options::stage_slots, 1, 64},
+    {"bitmap_threads", nullptr, &Options::bitmap_threads, 32, 1024},
     {"support_warps", nullptr, &Options::support_warps, 1, 32},
     {"support_sets_per_warp", nullptr, &Options::support_sets_per_warp, 1, 64},
     {"support_part_words", &Options::support_part_words, nullptr, 64, (int64_t)1 << 40},

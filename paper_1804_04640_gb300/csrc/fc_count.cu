@@ -1,29 +1,34 @@
-// fc_count.cu -- the batched counting kernel.
+// fc_count.cu -- the batched counting kernels.
 //
-// One persistent launch serves a whole batch of queries with shared context
-// (Sec. 2: every count N_ijk of a variable set).  CTAs pull work items
-// (query, row range) from an atomic counter; each item is counted with the
-// strategy the planner chose for its query:
+// A batch of queries with shared context (Sec. 2: every count N_ijk of a
+// variable set) runs as two persistent launches, each pulling work from an
+// atomic counter so that no CTA or warp ever waits for another:
 //
-//   kBitmap  Sec. 3.2, Alg. 1.  A warp owns 4096 instances at a time (two
-//            64-bit words per lane).  It walks the tree of state combinations
-//            depth first; each node ANDs its parent's partial bitmap (kept in
-//            registers) with the bitmap of the next variable's state and the
-//            subtree is skipped when the AND is empty in every lane (zero
-//            support pruning).  Leaves are popcounted, reduced over the warp
-//            and added to the table in shared memory.  Variables are visited
-//            in ascending entropy (Sec. 3.2).
-//   kHist    the partitions of Alg. 2-3 identified by their mixed-radix key:
-//            each instance's key (its cell index) is built from 16-byte
-//            column loads and counted with a shared-memory atomic; tables
-//            are replicated per warp group when shared memory allows.
-//   kGAtomic the same keys counted straight into the table in global memory
-//            (tables too large for shared memory).
+//   bitmap_kernel (Sec. 3.2, Alg. 1), warp-granular tasks (query, chunk
+//     range).  A warp owns 4096 instances at a time (two 64-bit words per
+//     lane) and walks the tree of state combinations depth first; each node
+//     ANDs its parent's partial bitmap with the bitmap of the next variable's
+//     state, and a subtree is skipped when that AND is empty in every lane
+//     (zero-support pruning).  Variables are visited in ascending entropy
+//     (Sec. 3.2).  The state bitmaps of levels 1..k-1, which the tree re-reads
+//     once per parent configuration, are staged per lane in shared memory for
+//     the chunk; leaves are popcounted, reduced over the warp and added to the
+//     table in global memory (L2 atomics).
 //
-// When a query's counts feed a score, the reduction of Sec. 3.1 (Eq. 1, Fig.
-// 2) runs in the same launch: from shared memory when one item holds the
-// query's whole table, else by the last CTA to finish one of the query's
-// items (an atomic ticket; no CTA ever waits for another).
+//   count_kernel, CTA-granular items (query, row range) for the strategies
+//     that key every instance:
+//     kHist    the partitions of Alg. 2-3 identified by their mixed-radix key
+//              (the instance's cell index) and counted with shared-memory
+//              atomics.  Keys are built two rows per 32-bit register (SWAR):
+//              shared-memory tables have fewer than 2^16 cells, so a 16-bit
+//              lane never overflows and one multiply-add updates two keys.
+//     kGAtomic the same keys, counted straight into the table in global
+//              memory (tables too large for shared memory).
+//
+// When a query's counts feed a score, the reduction of Sec. 3.1 (Eq. 1,
+// Fig. 2) runs in the same launch: from shared memory when one item holds the
+// query's whole table, else by the last CTA or warp to finish one of the
+// query's pieces (an atomic ticket).
 #include "fc_internal.h"
 #include "fc_score.cuh"
 
@@ -39,8 +44,13 @@ __device__ __forceinline__ int32_t tab_ld(const int32_t *t, int64_t i)
         return t[i];
 }
 
-// Score of one complete table (parents-major, child-last, r child states),
-// computed by the whole block; returns the value in thread 0.
+struct ScoreAcc {
+    Kahan k;
+    double d;
+};
+
+// Per-thread part of a score over rows j0, j0 + step, ... of a complete table
+// (parents-major, child-last, r child states).
 //   LL  = sum N_ijk log2(N_ijk / N_ij) = -(1/ln2) sum N_ijk log1p((N_ij - N_ijk) / N_ijk):
 //         every term has the same sign and the integer difference is exact.
 //   MDL = -LL + (log2 m / 2)(r - 1) q.
@@ -50,30 +60,29 @@ __device__ __forceinline__ int32_t tab_ld(const int32_t *t, int64_t i)
 //         int64 numerator; this equals the usual sum because sum p_j p_k x_jk = 0,
 //         and every term is >= 0.
 template <bool kGlobal>
-__device__ float block_score(const int32_t *tab, int32_t cells, int32_t r, int kind,
-                             const int64_t *marg_child, int64_t m, double ess, Kahan *red_k,
-                             double *red_d)
+__device__ ScoreAcc score_part(const int32_t *tab, int32_t cells, int32_t r, int kind,
+                               const int64_t *marg_child, int64_t m, double ess, int64_t j0,
+                               int64_t step)
 {
     const int64_t q = cells / r;
-    Kahan acc{0.0f, 0.0f};
-    double accd = 0.0;
+    ScoreAcc acc{{0.0f, 0.0f}, 0.0};
     const double aj = ess / (double)q, ajk = ess / ((double)r * (double)q);
     const double lg_aj = kind == kBDeu ? lgamma(aj) : 0.0;
     const double lg_ajk = kind == kBDeu ? lgamma(ajk) : 0.0;
-    for (int64_t j = threadIdx.x; j < q; j += blockDim.x) {
+    for (int64_t j = j0; j < q; j += step) {
         int64_t nij = 0;
         for (int k = 0; k < r; ++k) nij += tab_ld<kGlobal>(tab, j * r + k);
         if (nij == 0) continue;
         if (kind == kLL || kind == kMDL) {
             for (int k = 0; k < r; ++k) {
                 const int32_t n = tab_ld<kGlobal>(tab, j * r + k);
-                if (n > 0) kahan_add(acc, (float)n * log1pf((float)(nij - n) / (float)n));
+                if (n > 0) kahan_add(acc.k, (float)n * log1pf((float)(nij - n) / (float)n));
             }
         } else if (kind == kBDeu) {
-            accd += lg_aj - lgamma(aj + (double)nij);
+            acc.d += lg_aj - lgamma(aj + (double)nij);
             for (int k = 0; k < r; ++k) {
                 const int32_t n = tab_ld<kGlobal>(tab, j * r + k);
-                if (n > 0) accd += lgamma(ajk + (double)n) - lg_ajk;
+                if (n > 0) acc.d += lgamma(ajk + (double)n) - lg_ajk;
             }
         } else {  // kMI
             const float pj = (float)nij / (float)m;
@@ -83,57 +92,89 @@ __device__ float block_score(const int32_t *tab, int32_t cells, int32_t r, int k
                 const int32_t n = tab_ld<kGlobal>(tab, j * r + k);
                 const long long num = (long long)n * m - (long long)nij * nk;
                 const float x = (float)num / ((float)nij * (float)nk);
-                kahan_add(acc, pj * ((float)nk / (float)m) * mi_term(x));
+                kahan_add(acc.k, pj * ((float)nk / (float)m) * mi_term(x));
             }
         }
     }
-    // block reduction of (Kahan, double)
+    return acc;
+}
+
+__device__ __forceinline__ void warp_merge(ScoreAcc &acc)
+{
     for (int o = 16; o > 0; o >>= 1) {
-        Kahan other{__shfl_xor_sync(kFull, acc.s, o), __shfl_xor_sync(kFull, acc.c, o)};
-        kahan_merge(acc, other);
-        accd += __shfl_xor_sync(kFull, accd, o);
+        Kahan other{__shfl_xor_sync(kFull, acc.k.s, o), __shfl_xor_sync(kFull, acc.k.c, o)};
+        kahan_merge(acc.k, other);
+        acc.d += __shfl_xor_sync(kFull, acc.d, o);
     }
+}
+
+__device__ float score_finish(const ScoreAcc &t, int kind, int64_t m, int32_t r, int64_t q)
+{
+    const float sum = __fsub_rn(t.k.s, t.k.c);
+    if (kind == kLL) return -sum * kInvLn2;
+    if (kind == kMDL)
+        return (float)((double)sum * (double)kInvLn2 + 0.5 * log2((double)m) * (double)(r - 1) * (double)q);
+    if (kind == kBDeu) return (float)t.d;
+    return sum * kInvLn2;
+}
+
+// Whole block; the result is returned in thread 0.
+template <bool kGlobal>
+__device__ float block_score(const int32_t *tab, int32_t cells, int32_t r, int kind,
+                             const int64_t *marg_child, int64_t m, double ess, ScoreAcc *red)
+{
+    ScoreAcc acc = score_part<kGlobal>(tab, cells, r, kind, marg_child, m, ess, threadIdx.x, blockDim.x);
+    warp_merge(acc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        red_k[warp] = acc;
-        red_d[warp] = accd;
-    }
+    if (lane == 0) red[warp] = acc;
     __syncthreads();
     float out = 0.0f;
     if (threadIdx.x == 0) {
-        Kahan t{0.0f, 0.0f};
-        double td = 0.0;
+        ScoreAcc t{{0.0f, 0.0f}, 0.0};
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            kahan_merge(t, red_k[w]);
-            td += red_d[w];
+            kahan_merge(t.k, red[w].k);
+            t.d += red[w].d;
         }
-        const float sum = __fsub_rn(t.s, t.c);
-        if (kind == kLL)
-            out = -sum * kInvLn2;
-        else if (kind == kMDL)
-            out = (float)((double)sum * (double)kInvLn2 +
-                          0.5 * log2((double)m) * (double)(r - 1) * (double)q);
-        else if (kind == kBDeu)
-            out = (float)td;
-        else
-            out = sum * kInvLn2;
+        out = score_finish(t, kind, m, r, cells / r);
     }
     __syncthreads();
     return out;
 }
 
+// One warp; the result is returned in lane 0.
+__device__ float warp_score(const int32_t *tab, int32_t cells, int32_t r, int kind,
+                            const int64_t *marg_child, int64_t m, double ess)
+{
+    ScoreAcc acc = score_part<true>(tab, cells, r, kind, marg_child, m, ess, threadIdx.x & 31, 32);
+    warp_merge(acc);
+    return score_finish(acc, kind, m, r, cells / r);
+}
+
 // ------------------------------------------------------------ bitmap (Alg. 1)
 
+constexpr int kBitmapWarps = 32;  // upper bound on warps per CTA of bitmap_kernel
+
+struct Level {
+    const uint64_t *row;     // level 0: first state's bitmap at this chunk (global)
+    int32_t arity;
+    int32_t stride;
+    int32_t slot;            // levels >= 1: first staged slot
+};
+
+// One tree node per loop iteration.  acc holds the lane's two words of the
+// AND of the states chosen above this level.
 template <int K, int L>
 struct Dfs {
-    static __device__ __forceinline__ void run(const uint64_t *__restrict__ bits,
-                                               int64_t wstride, const QVar *vs, int64_t w,
+    static __device__ __forceinline__ void run(const Level *lv, const ulonglong2 *stage, int64_t wstride,
                                                ulonglong2 acc, int cell, int32_t *tab, int lane)
     {
-        const QVar v = vs[L];
-        const uint64_t *row = bits + (int64_t)v.soff * wstride + w;
+        const Level v = lv[L];
         for (int s = 0; s < v.arity; ++s) {
-            const ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2 *>(row + (int64_t)s * wstride));
+            ulonglong2 b;
+            if constexpr (L == 0)
+                b = __ldg(reinterpret_cast<const ulonglong2 *>(v.row + (int64_t)s * wstride));
+            else
+                b = stage[(v.slot + s) * 32 + lane];
             ulonglong2 x;
             x.x = acc.x & b.x;
             x.y = acc.y & b.y;
@@ -143,56 +184,142 @@ struct Dfs {
                 if (lane == 0 && cnt) atomicAdd(&tab[cell + s * v.stride], (int)cnt);
             } else {
                 if (__any_sync(kFull, (x.x | x.y) != 0ull))
-                    Dfs<K, L + 1>::run(bits, wstride, vs, w, x, cell + s * v.stride, tab, lane);
+                    Dfs<K, L + 1>::run(lv, stage, wstride, x, cell + s * v.stride, tab, lane);
             }
         }
     }
 };
 
 template <int K>
-__device__ __forceinline__ void bitmap_chunks(const CountParams &P, const QVar *vs, int64_t c0,
-                                              int64_t c1, int32_t *tab)
+__device__ __noinline__ void bitmap_task(const CountParams &P, const QVar *qv, int64_t c0, int64_t c1,
+                                         ulonglong2 *stage, int32_t *tab, int lane)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const ulonglong2 all = make_ulonglong2(~0ull, ~0ull);
-    for (int64_t c = c0 + warp; c < c1; c += nwarps) {
+    for (int64_t c = c0; c < c1; ++c) {
         const int64_t w = c * kChunkWords + 2 * lane;
-        Dfs<K, 0>::run(P.bits, P.wstride, vs, w, all, 0, tab, lane);
+        // level 0 is read in place; levels 1..K-1 are staged per lane
+        Level lv[K];
+        int slot = 0;
+#pragma unroll
+        for (int d = 0; d < K; ++d) {
+            const QVar v = qv[d];
+            const uint64_t *row = P.bits + (int64_t)v.soff * P.wstride + w;
+            lv[d] = Level{row, v.arity, v.stride, slot};
+            if (d > 0) {
+                for (int s = 0; s < v.arity; ++s)
+                    stage[(slot + s) * 32 + lane] =
+                        __ldg(reinterpret_cast<const ulonglong2 *>(row + (int64_t)s * P.wstride));
+                slot += v.arity;
+            }
+        }
+        Dfs<K, 0>::run(lv, stage, P.wstride, make_ulonglong2(~0ull, ~0ull), 0, tab, lane);
+        __syncwarp();
     }
 }
 
-__device__ void bitmap_rows(const CountParams &P, const QVar *vs, int k, int64_t c0, int64_t c1,
-                            int32_t *tab)
+__global__ void __launch_bounds__(256) bitmap_kernel(const CountParams P)
 {
-    switch (k) {
-    case 1: bitmap_chunks<1>(P, vs, c0, c1, tab); break;
-    case 2: bitmap_chunks<2>(P, vs, c0, c1, tab); break;
-    case 3: bitmap_chunks<3>(P, vs, c0, c1, tab); break;
-    case 4: bitmap_chunks<4>(P, vs, c0, c1, tab); break;
-    case 5: bitmap_chunks<5>(P, vs, c0, c1, tab); break;
-    case 6: bitmap_chunks<6>(P, vs, c0, c1, tab); break;
-    case 7: bitmap_chunks<7>(P, vs, c0, c1, tab); break;
-    case 8: bitmap_chunks<8>(P, vs, c0, c1, tab); break;
-    default: break;  // the planner never sends deeper queries here
+    extern __shared__ __align__(16) ulonglong2 stage_all[];
+    __shared__ QVar s_qv[kBitmapWarps][kMaxBitmapK];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    ulonglong2 *stage = stage_all + (size_t)warp * P.stage_slots * 32;
+    const int64_t nchunks = (P.m + kChunkRows - 1) / kChunkRows;
+    const int64_t n_tasks = (int64_t)P.n_bq * P.tasks_per_query;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(P.next_task, 1);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= n_tasks) break;
+        const int qi = t / P.tasks_per_query, part = t % P.tasks_per_query;
+        const int q = P.bq[qi];
+        const QHead h = P.qh[q];
+        const int k = h.k;
+        if (lane < k) s_qv[warp][lane] = P.qv[h.var_off + lane];
+        __syncwarp();
+        const int64_t c0 = nchunks * part / P.tasks_per_query;
+        const int64_t c1 = nchunks * (part + 1) / P.tasks_per_query;
+        int32_t *tab = P.tables + h.table_off;
+        const QVar *qv = s_qv[warp];
+        switch (k) {
+        case 1: bitmap_task<1>(P, qv, c0, c1, stage, tab, lane); break;
+        case 2: bitmap_task<2>(P, qv, c0, c1, stage, tab, lane); break;
+        case 3: bitmap_task<3>(P, qv, c0, c1, stage, tab, lane); break;
+        case 4: bitmap_task<4>(P, qv, c0, c1, stage, tab, lane); break;
+        case 5: bitmap_task<5>(P, qv, c0, c1, stage, tab, lane); break;
+        case 6: bitmap_task<6>(P, qv, c0, c1, stage, tab, lane); break;
+        case 7: bitmap_task<7>(P, qv, c0, c1, stage, tab, lane); break;
+        case 8: bitmap_task<8>(P, qv, c0, c1, stage, tab, lane); break;
+        default: break;  // the planner never sends other depths here
+        }
+        if (h.score_kind != kNoScore) {
+            __threadfence();
+            int last = 0;
+            if (lane == 0) last = atomicAdd(&P.tickets[q], 1) == P.tasks_per_query - 1;
+            last = __shfl_sync(kFull, last, 0);
+            if (last) {
+                __threadfence();
+                const float s = warp_score(tab, h.cells, h.r_child, h.score_kind, P.marg + h.child_soff,
+                                           P.m, P.ess);
+                if (lane == 0) P.scores[h.score_slot] = s;
+            }
+        }
+        __syncwarp();
     }
 }
 
 // ---------------------------------------------------- mixed-radix key counts
 
-__device__ __forceinline__ void add_bytes(uint32_t (&key)[16], const uint4 x, uint32_t st)
+// SWAR keys: 16 rows per thread; register pair (2i, 2i+1) holds rows
+// {4i, 4i+2} and {4i+1, 4i+3} in its low and high 16-bit halves.  Valid when
+// every key is below 2^16.
+__device__ __forceinline__ void key_rows_swar(const CountParams &P, const QVar *vs, int k,
+                                              int64_t r0, int64_t r1, int32_t *tab)
 {
-    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+    const int64_t ngroups = (r1 - r0) >> 4;
+    for (int64_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
+        const int64_t p = r0 + (g << 4);
+        uint32_t acc[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+        for (int j = 0; j < 8; ++j) acc[j] = 0u;
+        int t = 0;
+        for (; t + 2 <= k; t += 2) {  // two columns in flight
+            const QVar v0 = vs[t], v1 = vs[t + 1];
+            const uint4 x0 = __ldg(reinterpret_cast<const uint4 *>(P.D + (int64_t)v0.var * P.m_pad + p));
+            const uint4 x1 = __ldg(reinterpret_cast<const uint4 *>(P.D + (int64_t)v1.var * P.m_pad + p));
+            const uint32_t w0[4] = {x0.x, x0.y, x0.z, x0.w}, w1[4] = {x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
-        for (int j = 0; j < 4; ++j) key[4 * i + j] += ((w[i] >> (8 * j)) & 0xffu) * st;
+            for (int i = 0; i < 4; ++i) {
+                acc[2 * i] += (w0[i] & 0x00FF00FFu) * (uint32_t)v0.stride + (w1[i] & 0x00FF00FFu) * (uint32_t)v1.stride;
+                acc[2 * i + 1] += ((w0[i] >> 8) & 0x00FF00FFu) * (uint32_t)v0.stride +
+                                  ((w1[i] >> 8) & 0x00FF00FFu) * (uint32_t)v1.stride;
+            }
+        }
+        if (t < k) {
+            const QVar v0 = vs[t];
+            const uint4 x0 = __ldg(reinterpret_cast<const uint4 *>(P.D + (int64_t)v0.var * P.m_pad + p));
+            const uint32_t w0[4] = {x0.x, x0.y, x0.z, x0.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                acc[2 * i] += (w0[i] & 0x00FF00FFu) * (uint32_t)v0.stride;
+                acc[2 * i + 1] += ((w0[i] >> 8) & 0x00FF00FFu) * (uint32_t)v0.stride;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            atomicAdd(&tab[acc[j] & 0xFFFFu], 1);
+            atomicAdd(&tab[acc[j] >> 16], 1);
+        }
+    }
+    for (int64_t p = r0 + (ngroups << 4) + threadIdx.x; p < r1; p += blockDim.x) {
+        uint32_t key = 0u;
+        for (int t = 0; t < k; ++t)
+            key += (uint32_t)P.D[(int64_t)vs[t].var * P.m_pad + p] * (uint32_t)vs[t].stride;
+        atomicAdd(&tab[key], 1);
     }
 }
 
-// Keys of instances [r0, r1) counted into `tab` (shared or global memory).
-// r0 is a multiple of kChunkRows, so every 16-row group is 16-byte aligned.
-__device__ __forceinline__ void key_rows(const CountParams &P, const QVar *vs, int k, int64_t r0,
-                                         int64_t r1, int32_t *tab)
+// Scalar keys (any table size up to 2^31 cells), counted in global memory.
+__device__ __forceinline__ void key_rows_global(const CountParams &P, const QVar *vs, int k,
+                                                int64_t r0, int64_t r1, int32_t *tab)
 {
     const int64_t ngroups = (r1 - r0) >> 4;
     for (int64_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
@@ -203,7 +330,11 @@ __device__ __forceinline__ void key_rows(const CountParams &P, const QVar *vs, i
         for (int t = 0; t < k; ++t) {
             const QVar v = vs[t];
             const uint4 x = __ldg(reinterpret_cast<const uint4 *>(P.D + (int64_t)v.var * P.m_pad + p));
-            add_bytes(key, x, (uint32_t)v.stride);
+            const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) key[4 * i + j] += ((w[i] >> (8 * j)) & 0xffu) * (uint32_t)v.stride;
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) atomicAdd(&tab[key[j]], 1);
@@ -216,16 +347,13 @@ __device__ __forceinline__ void key_rows(const CountParams &P, const QVar *vs, i
     }
 }
 
-// ------------------------------------------------------- the persistent loop
-
-__global__ void __launch_bounds__(1024) count_kernel(const CountParams P)
+__global__ void __launch_bounds__(512, 2) count_kernel(const CountParams P)
 {
     extern __shared__ __align__(16) int32_t smem_tab[];
     __shared__ QVar s_vars[kMaxK];
     __shared__ int s_item;
     __shared__ int s_last;
-    __shared__ Kahan s_red_k[32];
-    __shared__ double s_red_d[32];
+    __shared__ ScoreAcc s_red[32];
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int64_t nchunks = (P.m + kChunkRows - 1) / kChunkRows;
 
@@ -242,14 +370,13 @@ __global__ void __launch_bounds__(1024) count_kernel(const CountParams P)
         const int64_t c1 = nchunks * (W.part + 1) / h.nparts;
         const int64_t r0 = c0 * kChunkRows;
         const int64_t r1 = min(P.m, c1 * kChunkRows);
-        const bool in_smem = h.strategy == kHist || h.strategy == kBitmap;
+        const bool in_smem = h.strategy == kHist;
         int copies = 1;
-        if (h.strategy == kHist) {
+        if (in_smem) {
             copies = min(P.hist_copies, P.smem_cells / max(h.cells, 1));
             copies = max(1, min(copies, nwarps));
-        }
-        if (in_smem)
             for (int c = threadIdx.x; c < h.cells * copies; c += blockDim.x) smem_tab[c] = 0;
+        }
         __syncthreads();
 
         if (k == 0) {
@@ -260,12 +387,10 @@ __global__ void __launch_bounds__(1024) count_kernel(const CountParams P)
                 else
                     atomicAdd(&P.tables[h.table_off], (int32_t)(r1 - r0));
             }
-        } else if (h.strategy == kHist) {
-            key_rows(P, s_vars, k, r0, r1, smem_tab + (warp % copies) * h.cells);
-        } else if (h.strategy == kBitmap) {
-            bitmap_rows(P, s_vars, k, c0, c1, smem_tab);
+        } else if (in_smem) {
+            key_rows_swar(P, s_vars, k, r0, r1, smem_tab + (warp % copies) * h.cells);
         } else {
-            key_rows(P, s_vars, k, r0, r1, P.tables + h.table_off);
+            key_rows_global(P, s_vars, k, r0, r1, P.tables + h.table_off);
         }
         __syncthreads();
 
@@ -286,8 +411,7 @@ __global__ void __launch_bounds__(1024) count_kernel(const CountParams P)
         if (h.score_kind != kNoScore) {
             const int64_t *mc = P.marg + h.child_soff;
             if (h.nparts == 1 && in_smem) {
-                const float s = block_score<false>(smem_tab, h.cells, h.r_child, h.score_kind, mc,
-                                                   P.m, P.ess, s_red_k, s_red_d);
+                const float s = block_score<false>(smem_tab, h.cells, h.r_child, h.score_kind, mc, P.m, P.ess, s_red);
                 if (threadIdx.x == 0) P.scores[h.score_slot] = s;
             } else {
                 __threadfence();
@@ -296,9 +420,8 @@ __global__ void __launch_bounds__(1024) count_kernel(const CountParams P)
                 __syncthreads();
                 if (s_last) {
                     __threadfence();
-                    const float s = block_score<true>(P.tables + h.table_off, h.cells, h.r_child,
-                                                      h.score_kind, mc, P.m, P.ess, s_red_k,
-                                                      s_red_d);
+                    const float s = block_score<true>(P.tables + h.table_off, h.cells, h.r_child, h.score_kind,
+                                                      mc, P.m, P.ess, s_red);
                     if (threadIdx.x == 0) P.scores[h.score_slot] = s;
                 }
             }
@@ -311,24 +434,38 @@ __global__ void score_global_kernel(const QHead *__restrict__ qh, const int32_t 
                                     const int32_t *__restrict__ tables, float *scores,
                                     const int64_t *__restrict__ marg, int64_t m, double ess)
 {
-    __shared__ Kahan s_red_k[32];
-    __shared__ double s_red_d[32];
+    __shared__ ScoreAcc s_red[32];
     const QHead h = qh[q_list[blockIdx.x]];
     const float s = block_score<true>(tables + h.table_off, h.cells, h.r_child, h.score_kind,
-                                      marg + h.child_soff, m, ess, s_red_k, s_red_d);
+                                      marg + h.child_soff, m, ess, s_red);
     if (threadIdx.x == 0) scores[h.score_slot] = s;
 }
 
 }  // namespace
 
-int count_kernel_max_smem() { return 200 * 1024; }
+const void *count_kernel_ptr() { return (const void *)count_kernel; }
+const void *bitmap_kernel_ptr() { return (const void *)bitmap_kernel; }
+
+size_t bitmap_smem_bytes(int threads, int stage_slots)
+{
+    return (size_t)(threads / 32) * stage_slots * 32 * sizeof(ulonglong2);
+}
 
 cudaError_t launch_count(const CountParams &p, int grid, int threads, size_t smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_kernel<<<grid, threads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bitmap(const CountParams &p, int grid, int threads, cudaStream_t s)
+{
+    if (threads > kBitmapWarps * 32) return cudaErrorInvalidValue;
+    const size_t smem = bitmap_smem_bytes(threads, p.stage_slots);
+    cudaError_t e = cudaFuncSetAttribute(bitmap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    bitmap_kernel<<<grid, threads, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -68,6 +68,12 @@ struct CountParams {
     int32_t smem_cells;      // int32 cells of dynamic shared memory for tables
     int32_t hist_copies;     // maximum table copies for the histogram strategy
     int32_t pad;
+    // bitmap strategy: warp-granular tasks (query, chunk range)
+    const int32_t *bq;       // bitmap queries in processing order
+    int32_t n_bq;
+    int32_t tasks_per_query;
+    int32_t *next_task;      // warp task counter, zero before the launch
+    int32_t stage_slots;     // state bitmaps a warp stages (levels 1..k-1)
 };
 
 // Launchers (each defined in the translation unit holding its kernel).
@@ -83,7 +89,10 @@ cudaError_t launch_mask_tail_bits(uint64_t *bits, int64_t rows, int64_t wstride,
                                   cudaStream_t s);
 
 cudaError_t launch_count(const CountParams &p, int grid, int threads, size_t smem, cudaStream_t s);
-int count_kernel_max_smem();
+cudaError_t launch_bitmap(const CountParams &p, int grid, int threads, cudaStream_t s);
+size_t bitmap_smem_bytes(int threads, int stage_slots);
+const void *count_kernel_ptr();
+const void *bitmap_kernel_ptr();
 
 // Sort + run-length path for one query (large tables).
 struct SortScratch {
