@@ -261,6 +261,41 @@ const char *fc_last_error(void);
  * Exercises the bounded-wait error path without faulting the GPU. */
 int fc_selftest_wait_timeout(fc_ctx *ctx, int64_t wait_limit);
 
+/* ------------------------------------------------- allocation-free variant
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot let a library allocate device memory: code recording a CUDA graph
+ * under a global-mode stream capture (where cudaMalloc is refused), programs
+ * whose device memory is owned by their own pool allocator, and
+ * latency-critical paths that cannot afford the device synchronisation that
+ * cudaMalloc and cudaFree may cause.
+ *
+ * One contingency table, counted by the sort + run-length strategy
+ * (FC_STRAT_SORT), without any context and without allocating.  Its scratch
+ * (key buffers and radix-sort histograms) is a fixed 8.25 MiB array compiled
+ * into the library, which every GPU that loads the library keeps until the
+ * process exits.
+ *   D       DEVICE pointer, column-major: state of X_i in instance p at
+ *           D[i * ld + p], 0-based.  An instance with a state outside its
+ *           variable's arity is not counted.
+ *   n, m    variables and instances; m must be at most 2^20 (1,048,576),
+ *           larger m returns FC_ERR_SIZE.  ld >= m.
+ *   arities n HOST int32 values in 1..255; vars: k HOST int32 distinct ids.
+ *   table   DEVICE pointer to prod(r_{vars[t]}) int32 cells, layout as in
+ *           fc_count; it is zeroed and then filled on `stream`.
+ *   stream  cudaStream_t the work is enqueued on (NULL = the legacy default
+ *           stream).  The call returns once the work is enqueued.
+ * The first call on a device looks up the scratch array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture begins.  All calls share the one scratch array and it
+ * keeps the last call's contents, so calls whose work overlaps on the GPU
+ * (other streams, other host threads) race and give wrong counts: serialise
+ * them.  No call allocates or frees memory.
+ * Errors: FC_ERR_ARG, FC_ERR_SIZE, FC_ERR_CUDA. */
+int fc_count_sorted_noalloc(const uint8_t *D, int32_t n, int64_t m, int64_t ld,
+                            const int32_t *arities, const int32_t *vars, int32_t k,
+                            int32_t *table, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ EXPORTS = (
     "fc_support_batch", "fc_plan_count", "fc_plan_score", "fc_plan_support", "fc_plan_pairs",
     "fc_plan_size", "fc_plan_table_offsets", "fc_plan_strategies", "fc_plan_run", "fc_plan_free",
     "fc_sync", "fc_set_option", "fc_get_option", "fc_autotune", "fc_last_error",
-    "fc_selftest_wait_timeout",
+    "fc_selftest_wait_timeout", "fc_count_sorted_noalloc",
 )
 
 
@@ -94,6 +94,8 @@ def load_library(build_if_missing: bool = False):
         "fc_autotune": (ctypes.c_int, [_vp, ctypes.c_int32]),
         "fc_last_error": (ctypes.c_char_p, []),
         "fc_selftest_wait_timeout": (ctypes.c_int, [_vp, ctypes.c_int64]),
+        "fc_count_sorted_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _i32p,
+                                                   _i32p, ctypes.c_int32, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -373,6 +375,20 @@ def fc_last_error() -> str:
 def fc_selftest_wait_timeout(ctx: Handle, wait_limit: int) -> int:
     """Status of a device wait that nothing satisfies (FC_ERR_TIMEOUT expected)."""
     return int(load_library().fc_selftest_wait_timeout(ctx.ptr, int(wait_limit)))
+
+
+def fc_count_sorted_noalloc(D, arities, vars_, table, stream=None):
+    """One table by sort + run-length with the library's fixed scratch (no
+    allocation).  D: CUDA uint8 tensor (n, ld) column-major, rows of at least
+    m instances; table: CUDA int32 tensor of prod(arities[vars]) cells.  The
+    call is asynchronous on `stream`."""
+    if not (_is_cuda(D) and _is_cuda(table)):
+        raise FcError(FC_ERR_ARG, "fc_count_sorted_noalloc needs CUDA tensors for D and table")
+    ar, v = _host(arities, np.int32), _host(vars_, np.int32)
+    n, ld = int(D.shape[0]), int(D.stride(0))
+    m = int(D.shape[1])
+    _check(load_library().fc_count_sorted_noalloc(_ptr(D), n, m, ld, _ptr(ar, _i32p), _ptr(v, _i32p), len(v),
+                                                  _ptr(table), _stream_ptr(stream)))
 
 
 # ----------------------------------------------------------------- helpers

@@ -34,6 +34,21 @@ int fail(int code, const char *fmt, ...)
     return code;
 }
 
+}  // namespace
+
+int fc::set_error(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+namespace {
+
 int cuda_fail(cudaError_t e, const char *what)
 {
     if (e == cudaErrorMemoryAllocation) {

@@ -163,4 +163,7 @@ cudaError_t launch_pairs_extract(const int32_t *C, int32_t R_pad, int32_t n, con
 
 cudaError_t launch_wait_selftest(int32_t *status, int64_t wait_limit, cudaStream_t s);
 
+// Records the thread-local message returned by fc_last_error(); returns code.
+int set_error(int code, const char *fmt, ...);
+
 }  // namespace fc

@@ -14,6 +14,17 @@
 // p' adds p' + 1, so a zeroed cell ends up holding the run length.
 #include "fc_internal.h"
 
+#include <mutex>
+
+#include "../../include/fc.h"
+
+// Scratch of the allocation-free entry point fc_count_sorted_noalloc: two key
+// buffers and the per-tile digit histograms of the radix sort, sized for at
+// most 2^20 instances (8.25 MiB).  Every GPU that loads the library holds it
+// until the process exits.  Host code must not use this name as an address:
+// the device address comes from cudaGetSymbolAddress (see below).
+static __device__ __align__(256) uint32_t g_noalloc_scratch[2 * (1 << 20) + 256 * ((1 << 20) / 4096)];
+
 namespace fc {
 namespace {
 
@@ -133,11 +144,16 @@ __global__ void scatter_kernel(const uint32_t *__restrict__ in, uint32_t *__rest
     }
 }
 
-__global__ void run_length_kernel(const uint32_t *__restrict__ sorted, int64_t m, int32_t *table)
+// A key that occurs in several runs (possible only for keys outside the
+// table, see keys_byval_kernel) still adds up to its count: every run adds
+// its own length.  Keys >= cells are not counted.
+__global__ void run_length_kernel(const uint32_t *__restrict__ sorted, int64_t m, int32_t *table,
+                                  uint32_t cells)
 {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m;
          p += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t key = sorted[p];
+        if (key >= cells) continue;
         if (p == 0 || sorted[p - 1] != key) atomicAdd(&table[key], (int32_t)(-p));
         if (p == m - 1 || sorted[p + 1] != key) atomicAdd(&table[key], (int32_t)(p + 1));
     }
@@ -178,8 +194,117 @@ cudaError_t launch_sort_count(const uint8_t *D, int64_t m_pad, int64_t m, const 
         a = b;
         b = t;
     }
-    run_length_kernel<<<grid_for(m, 256), 256, 0, s>>>(a, m, table);
+    run_length_kernel<<<grid_for(m, 256), 256, 0, s>>>(a, m, table, (uint32_t)cells);
     return cudaGetLastError();
 }
 
+
+// ------------------------------------------------- allocation-free variant
+
+namespace {
+
+constexpr int64_t kNoAllocMaxRows = (int64_t)1 << 20;
+constexpr int kNoAllocMaxDevices = 64;
+
+struct KeyDesc {
+    int32_t k;
+    QVar v[kMaxK];
+};
+
+// Keys with the descriptors passed by value (no device-side descriptor
+// buffer).  An instance whose state is outside its variable's arity gets the
+// key 0xFFFFFFFF and is not counted.
+__global__ void keys_byval_kernel(const uint8_t *__restrict__ D, int64_t ld, int64_t m, const KeyDesc d,
+                                  uint32_t *keys)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t key = 0u;
+        bool bad = false;
+        for (int t = 0; t < d.k; ++t) {
+            const uint32_t st = D[(int64_t)d.v[t].var * ld + p];
+            bad |= st >= (uint32_t)d.v[t].arity;
+            key += st * (uint32_t)d.v[t].stride;
+        }
+        keys[p] = bad ? 0xFFFFFFFFu : key;
+    }
+}
+
+std::mutex g_noalloc_mu;
+uint32_t *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the lookup allocates nothing).
+cudaError_t noalloc_scratch(int dev, uint32_t **out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = (uint32_t *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
 }  // namespace fc
+
+extern "C" int fc_count_sorted_noalloc(const uint8_t *D, int32_t n, int64_t m, int64_t ld,
+                                       const int32_t *arities, const int32_t *vars, int32_t k,
+                                       int32_t *table, void *stream)
+{
+    using namespace fc;
+    if (!D || !arities || !table || (k > 0 && !vars))
+        return set_error(FC_ERR_ARG, "fc_count_sorted_noalloc: null argument");
+    if (n < 1 || m < 0 || ld < m || k < 0 || k > kMaxK)
+        return set_error(FC_ERR_ARG, "fc_count_sorted_noalloc: bad n, m, ld or k");
+    if (m > kNoAllocMaxRows)
+        return set_error(FC_ERR_SIZE, "fc_count_sorted_noalloc counts at most %lld instances, got %lld",
+                         (long long)kNoAllocMaxRows, (long long)m);
+    KeyDesc d{};
+    d.k = k;
+    int64_t cells = 1;
+    for (int t = 0; t < k; ++t) {
+        const int v = vars[t];
+        if (v < 0 || v >= n) return set_error(FC_ERR_ARG, "variable %d out of range", v);
+        for (int u = 0; u < t; ++u)
+            if (vars[u] == v) return set_error(FC_ERR_ARG, "variable %d listed twice", v);
+        if (arities[v] < 1 || arities[v] > 255) return set_error(FC_ERR_ARG, "arity of variable %d not in 1..255", v);
+        cells *= arities[v];
+        if (cells > INT32_MAX) return set_error(FC_ERR_SIZE, "table exceeds 2^31-1 cells");
+    }
+    int64_t stride = 1;
+    for (int t = k - 1; t >= 0; --t) {
+        d.v[t] = QVar{vars[t], (int32_t)stride, arities[vars[t]], 0};
+        stride *= arities[vars[t]];
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
+        return set_error(FC_ERR_CUDA, "fc_count_sorted_noalloc: no usable current device");
+    uint32_t *scratch = nullptr;
+    if ((e = noalloc_scratch(dev, &scratch)) != cudaSuccess)
+        return set_error(FC_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((e = cudaMemsetAsync(table, 0, (size_t)cells * sizeof(int32_t), s)) != cudaSuccess)
+        return set_error(FC_ERR_CUDA, "zeroing the table: %s", cudaGetErrorString(e));
+    if (m == 0) return FC_OK;
+    const int nblocks = (int)((m + kTile - 1) / kTile);
+    uint32_t *a = scratch, *b = scratch + kNoAllocMaxRows, *hist = scratch + 2 * kNoAllocMaxRows;
+    const int key_bits = cells > 1 ? 32 - __builtin_clz((uint32_t)(cells - 1)) : 0;
+    keys_byval_kernel<<<grid_for(m, 256), 256, 0, s>>>(D, ld, m, d, a);
+    for (int shift = 0; shift < key_bits; shift += 8) {
+        digit_hist_kernel<<<nblocks, kThreads, 0, s>>>(a, m, shift, hist, nblocks);
+        exclusive_scan_kernel<<<1, 1024, 0, s>>>(hist, (int64_t)nblocks * 256);
+        scatter_kernel<<<nblocks, kThreads, 0, s>>>(a, b, m, shift, hist, nblocks);
+        uint32_t *t = a;
+        a = b;
+        b = t;
+    }
+    run_length_kernel<<<grid_for(m, 256), 256, 0, s>>>(a, m, table, (uint32_t)cells);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return set_error(FC_ERR_CUDA, "fc_count_sorted_noalloc launch: %s", cudaGetErrorString(e));
+    return FC_OK;
+}
