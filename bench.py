@@ -292,7 +292,7 @@ def run_gpu(args, rank: int, world: int):
                 per_plans.append(p1)
                 pq_outs.append(torch.empty(max(fc.fc_plan_size(p1, 0), 1), dtype=torch.int32, device="cuda"))
             per_query = (per_plans, pq_outs)
-        strategies = np.bincount(fc.fc_plan_strategies(plan), minlength=4).tolist()
+        strategies = np.bincount(fc.fc_plan_strategies(plan), minlength=5).tolist()
     elif name == "scores":
         db = w["db"]
         ctx = fc.fc_load(db.D, db.arities)
@@ -310,7 +310,7 @@ def run_gpu(args, rank: int, world: int):
 
         def e2e_call():
             fc.fc_score_batch(ctx, w["child"], po, pa, "bdeu", 1.0, out=pinned)
-        strategies = np.bincount(fc.fc_plan_strategies(plan), minlength=4).tolist()
+        strategies = np.bincount(fc.fc_plan_strategies(plan), minlength=5).tolist()
     elif name == "pairs":
         db = w["db"]
         ctx = fc.fc_load(db.D, db.arities)
@@ -423,7 +423,7 @@ def run_gpu(args, rank: int, world: int):
         cfg = describe(name, w)
         cfg["l2"] = "flushed between timed steps (256 MiB write)"
         if strategies is not None:
-            cfg["strategies"] = dict(zip(["bitmap", "hist", "gatomic", "sort"], strategies))
+            cfg["strategies"] = dict(zip(["bitmap", "hist", "gatomic", "sort", "marginal"], strategies))
             cfg["cost_model_fs"] = {k: fc.fc_get_option(ctx, k) for k in
                                     ("bitmap_cost", "hist_cost_row", "hist_cost_var")}
         cores = os.cpu_count() or 1
@@ -463,7 +463,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip fc_autotune (strategy thresholds from the default cost model)")
     ap.add_argument("--strategy", type=int, default=-1, help="force one counting strategy (-1 = planner's choice)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -75,7 +75,9 @@ enum {
     FC_STRAT_BITMAP = 0,  /* Sec. 3.2, Alg. 1: AND + popcount DFS over per-state bitmaps */
     FC_STRAT_HIST = 1,    /* mixed-radix key per instance into a shared-memory table (Sec. 3.3's partitions as keys) */
     FC_STRAT_GATOMIC = 2, /* mixed-radix key into the output table in global memory */
-    FC_STRAT_SORT = 3     /* mixed-radix key, device radix sort, run-length (Sec. 3.3: partitions are runs of equal keys) */
+    FC_STRAT_SORT = 3,    /* mixed-radix key, device radix sort, run-length (Sec. 3.3: partitions are runs of equal keys) */
+    FC_STRAT_MARGINAL = 4 /* one variable: the per-state counts precomputed at load (Sec. 3.3, precomputed
+                             single-variable partitions); chosen automatically, never forced */
 };
 
 typedef struct fc_ctx fc_ctx;

@@ -116,6 +116,7 @@ struct Options {
     // cost model, femtoseconds: bitmap per DFS node per 4096-row chunk;
     // histogram per row and per row-variable; per table cell flushed
     int64_t bitmap_cost = 200000;
+    int64_t bitmap_chunk_cost = 0;    // per 4096-row chunk of a bitmap query
     int64_t hist_cost_row = 143;
     int64_t hist_cost_var = 124;
     int64_t flush_cost = 160;
@@ -493,10 +494,11 @@ QPlan choose(const fc_ctx *c, const QVar *v, int k, int64_t cells, int32_t smem_
         nodes = dfs_nodes(ord.data(), k);
     }
     const double hist = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) + flush;
-    const double bitmap = bm ? chunks * nodes * o.bitmap_cost + flush : 1e300;
+    const double bitmap = bm ? chunks * ((double)o.bitmap_chunk_cost + nodes * o.bitmap_cost) + flush : 1e300;
     const double gatomic = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) * 2.0 + (double)cells * 4.0;
     int32_t s = o.strategy;
     if (k == 0) s = fits ? FC_STRAT_HIST : FC_STRAT_GATOMIC;
+    if (k == 1 && fits && (s == FC_STRAT_AUTO || s == FC_STRAT_HIST)) return QPlan{FC_STRAT_MARGINAL, flush};
     if (s == FC_STRAT_BITMAP && !bm) s = FC_STRAT_AUTO;
     if (s == FC_STRAT_HIST && !fits) s = FC_STRAT_AUTO;
     if (s == FC_STRAT_AUTO) {
@@ -592,6 +594,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     int32_t persistent = 0;
     for (int32_t q = 0; q < nq; ++q)
         if (qh[q].strategy == kHist || qh[q].strategy == kGAtomic) ++persistent;
+    // (marginal items hold no rows, so they never split)
     const int64_t target = (int64_t)p->grid * 4;
     int64_t parts = 1;
     if (persistent > 0 && persistent < target)
@@ -611,8 +614,9 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
             bmo.push_back({cost[q], q});
             continue;
         }
-        h.nparts = (int16_t)parts;
-        for (int32_t part = 0; part < parts; ++part) order.push_back({cost[q] / parts, Item{q, part}});
+        const int64_t qparts = h.strategy == kMarginal ? 1 : parts;
+        h.nparts = (int16_t)qparts;
+        for (int32_t part = 0; part < qparts; ++part) order.push_back({cost[q] / qparts, Item{q, part}});
     }
     std::stable_sort(order.begin(), order.end(),
                      [](const auto &a, const auto &b) { return a.first > b.first; });
@@ -627,10 +631,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     p->bm_threads = std::max(32, std::min(1024, o.bitmap_threads / 32 * 32));
     p->stage_slots = o.stage_slots;
     if (p->n_bq > 0) {
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bitmap_kernel_ptr(), p->bm_threads,
-                                                      bitmap_smem_bytes(p->bm_threads, p->stage_slots));
-        p->bm_grid = c->num_sms * std::max(1, per_sm);
+        p->bm_grid = c->num_sms * bitmap_ctas_per_sm(p->bm_threads, p->stage_slots);
         const int64_t warps = (int64_t)p->bm_grid * (p->bm_threads / 32);
         const int64_t want = (8 * warps + p->n_bq - 1) / p->n_bq;
         p->tasks_per_query = (int32_t)std::max<int64_t>(1, std::min<int64_t>(nchunks, want));
@@ -641,7 +642,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     if (score_kind != kNoScore) {
         for (int32_t q = 0; q < nq; ++q) {
             QHead &h = qh[q];
-            const bool global = h.strategy != kHist || h.nparts > 1;
+            const bool global = (h.strategy != kHist && h.strategy != kMarginal) || h.nparts > 1;
             if (global) {
                 h.table_off = scratch;
                 scratch += h.cells;
@@ -655,7 +656,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     }
     for (int32_t q = 0; q < nq; ++q) {
         const QHead &h = qh[q];
-        if (h.strategy != kHist || h.nparts > 1) p->zero_tables = true;
+        if ((h.strategy != kHist && h.strategy != kMarginal) || h.nparts > 1) p->zero_tables = true;
     }
     for (auto &j : p->sort_jobs) {
         j.table_off = qh[j.q].table_off;
@@ -1244,10 +1245,19 @@ extern "C" int fc_plan_pairs(fc_ctx *c, fc_plan **out)
     const int64_t chunk_words = std::max<int64_t>(2, c->opt.pair_chunk_rows / 64 / 2 * 2);
     // row splits: enough CTAs to fill the GPU and at most chunk_words per split
     const int32_t tiles = pairs_tile_count(R_pad);
-    int64_t ksplit = std::max<int64_t>(1, (c->words + chunk_words - 1) / chunk_words);
-    const int64_t want = std::max<int64_t>(1, (2 * c->num_sms + tiles - 1) / tiles);
-    ksplit = std::max(ksplit, want);
-    ksplit = std::min<int64_t>(ksplit, std::max<int64_t>(1, (c->words + 1) / 2));
+    // one CTA per SM: pick the split count that fills whole waves, at least
+    // two waves and at least the splits the chunk bound asks for
+    const int64_t need = std::max<int64_t>(1, (c->words + chunk_words - 1) / chunk_words);
+    const int64_t max_split = std::max<int64_t>(1, (c->words + 1) / 2);
+    int64_t ksplit = need;
+    for (int64_t waves = 2; waves < 64; ++waves) {
+        const int64_t s = waves * c->num_sms / tiles;
+        if (s >= need && s * tiles >= waves * c->num_sms - tiles / 2) {
+            ksplit = s;
+            break;
+        }
+    }
+    ksplit = std::max<int64_t>(1, std::min(ksplit, max_split));
     P.ksplit = (int32_t)ksplit;
     P.chunk_words = (int32_t)chunk_words;
     P.wait_limit = c->opt.wait_limit;
@@ -1291,6 +1301,7 @@ const OptDesc kOpts[] = {
     {"wait_limit", &Options::wait_limit, nullptr, 1, (int64_t)1 << 40},
     {"sort_min_cells", &Options::sort_min_cells, nullptr, 1, (int64_t)1 << 31},
     {"bitmap_cost", &Options::bitmap_cost, nullptr, 0, (int64_t)1 << 40},
+    {"bitmap_chunk_cost", &Options::bitmap_chunk_cost, nullptr, 0, (int64_t)1 << 40},
     {"hist_cost_row", &Options::hist_cost_row, nullptr, 0, (int64_t)1 << 40},
     {"hist_cost_var", &Options::hist_cost_var, nullptr, 0, (int64_t)1 << 40},
     {"flush_cost", &Options::flush_cost, nullptr, 0, (int64_t)1 << 40},
@@ -1368,8 +1379,41 @@ double time_plan(fc_plan *p, void *out, int reps)
     return best;
 }
 
+// Least squares for y ~ a x0 + b x1 with a, b >= 0.
+void fit2(const std::vector<double> &x0, const std::vector<double> &x1, const std::vector<double> &y,
+          double &a, double &b)
+{
+    double s00 = 0, s01 = 0, s11 = 0, t0 = 0, t1 = 0;
+    for (size_t i = 0; i < y.size(); ++i) {
+        s00 += x0[i] * x0[i];
+        s01 += x0[i] * x1[i];
+        s11 += x1[i] * x1[i];
+        t0 += x0[i] * y[i];
+        t1 += x1[i] * y[i];
+    }
+    const double det = s00 * s11 - s01 * s01;
+    if (det > 1e-12 * s00 * s11) {
+        a = (t0 * s11 - t1 * s01) / det;
+        b = (t1 * s00 - t0 * s01) / det;
+    } else {
+        a = s00 > 0 ? t0 / s00 : 0;
+        b = 0;
+    }
+    if (a < 0) {
+        a = 0;
+        b = s11 > 0 ? t1 / s11 : 0;
+    } else if (b < 0) {
+        b = 0;
+        a = s00 > 0 ? t0 / s00 : 0;
+    }
+}
+
 }  // namespace
 
+// Times, for each query size k, a batch of random queries over the loaded
+// variables with each strategy forced, then fits the cost model that
+// FC_STRAT_AUTO uses:  histogram = rows (a + b k),  bitmap = chunks (c0 + c1
+// nodes), nodes being the DFS tree size of the query in entropy order.
 extern "C" int fc_autotune(fc_ctx *c, int32_t budget_ms)
 {
     if (!c) return fail(FC_ERR_ARG, "fc_autotune: null context");
@@ -1377,72 +1421,78 @@ extern "C" int fc_autotune(fc_ctx *c, int32_t budget_ms)
     DevGuard g(c->device);
     (void)budget_ms;
     const Options saved = c->opt;
-    // Sample queries of sizes 1..6 over the loaded variables (tables that fit
-    // in shared memory), time them with each strategy forced, and fit the
-    // per-unit costs of the model that FC_STRAT_AUTO uses.
+    const int kmax = std::min(6, c->n);
+    const int nq = std::max(2048, 8 * c->num_sms * std::max(1, saved.ctas_per_sm));
+    const double chunks = (double)((c->m + kChunkRows - 1) / kChunkRows);
+    const double rows = (double)c->m;
     uint64_t seed = 0x9e3779b97f4a7c15ull;
-    std::vector<int32_t> off{0}, vars;
+    std::vector<double> hx0, hx1, hy, bx0, bx1, by;
     std::vector<int32_t> perm(c->n);
-    const int nq = std::max(4 * c->num_sms * std::max(1, c->opt.ctas_per_sm), 512);
-    double node_chunks = 0, rows_k = 0, rows = 0;
-    for (int q = 0; q < nq; ++q) {
-        const int kmax = std::min(6, c->n);
-        const int k = 1 + (int)(lcg(seed) % kmax);
-        std::iota(perm.begin(), perm.end(), 0);
-        int64_t cells = 1;
-        int used = 0;
-        for (int t = 0; t < c->n && used < k; ++t) {
-            const int j = t + (int)(lcg(seed) % (c->n - t));
-            std::swap(perm[t], perm[j]);
-            if (cells * c->arity[perm[t]] > std::min<int64_t>(c->opt.smem_cells, 4096)) continue;
-            cells *= c->arity[perm[t]];
-            vars.push_back(perm[t]);
-            ++used;
-        }
-        off.push_back((int32_t)vars.size());
-    }
-    double t_strat[2] = {0, 0};
-    for (int s = 0; s < 2; ++s) {
-        c->opt.strategy = s;
-        fc_plan *p = nullptr;
-        if (fc_plan_count(c, nq, off.data(), vars.data(), nullptr, &p) != FC_OK) {
-            c->opt = saved;
-            return FC_ERR_CUDA;
-        }
-        DBuf out;
-        if (out.ensure(sizeof(int32_t) * std::max<int64_t>(p->out_cells, 1)) != cudaSuccess) {
-            fc_plan_free(p);
-            c->opt = saved;
-            return fail(FC_ERR_OOM, "autotune buffer");
-        }
-        t_strat[s] = time_plan(p, out.p, 3);
-        if (s == 0) {
-            // model units of this batch
-            std::vector<QHead> qh(nq);
-            std::vector<QVar> qv;
-            for (int q = 0; q < nq; ++q) {
-                int32_t ke = 0;
-                const size_t first = qv.size();
-                describe(c, vars.data() + off[q], off[q + 1] - off[q], qv, ke);
-                node_chunks += dfs_nodes(qv.data() + first, ke) * (double)((c->m + kChunkRows - 1) / kChunkRows);
-                rows_k += (double)c->m * ke;
-                rows += (double)c->m;
+    for (int k = 1; k <= kmax; ++k) {
+        std::vector<int32_t> off{0}, vars;
+        double nodes = 0;
+        for (int q = 0; q < nq; ++q) {
+            std::iota(perm.begin(), perm.end(), 0);
+            int64_t cells = 1;
+            int used = 0;
+            for (int t = 0; t < c->n && used < k; ++t) {
+                const int j = t + (int)(lcg(seed) % (c->n - t));
+                std::swap(perm[t], perm[j]);
+                if (cells * c->arity[perm[t]] > saved.smem_cells) continue;
+                cells *= c->arity[perm[t]];
+                vars.push_back(perm[t]);
+                ++used;
             }
+            off.push_back((int32_t)vars.size());
+            std::vector<QVar> qv;
+            int32_t ke = 0;
+            describe(c, vars.data() + off[q], off[q + 1] - off[q], qv, ke);
+            entropy_order(c, qv.data(), ke);
+            nodes += dfs_nodes(qv.data(), ke);
         }
-        out.release();
-        fc_plan_free(p);
+        double t[2] = {-1, -1};
+        for (int s = 0; s < 2; ++s) {
+            c->opt = saved;
+            c->opt.strategy = s;
+            fc_plan *p = nullptr;
+            if (fc_plan_count(c, nq, off.data(), vars.data(), nullptr, &p) != FC_OK) {
+                c->opt = saved;
+                return FC_ERR_CUDA;
+            }
+            bool all = true;
+            for (int32_t q = 0; q < nq; ++q) all = all && p->strategy[q] == s;
+            DBuf out;
+            if (out.ensure(sizeof(int32_t) * std::max<int64_t>(p->out_cells, 1)) != cudaSuccess) {
+                fc_plan_free(p);
+                c->opt = saved;
+                return fail(FC_ERR_OOM, "autotune buffer");
+            }
+            if (all) t[s] = time_plan(p, out.p, 3) * 1e12;  // milliseconds -> femtoseconds
+            out.release();
+            fc_plan_free(p);
+        }
+        if (t[1] > 0) {
+            hx0.push_back(nq * rows);
+            hx1.push_back(nq * rows * k);
+            hy.push_back(t[1]);
+        }
+        if (t[0] > 0) {
+            bx0.push_back(nq * chunks);
+            bx1.push_back(nodes * chunks);
+            by.push_back(t[0]);
+        }
     }
     c->opt = saved;
-    // times in femtoseconds per model unit across the whole GPU
-    const double fs0 = t_strat[0] * 1e12, fs1 = t_strat[1] * 1e12;
-    if (node_chunks > 0) c->opt.bitmap_cost = (int64_t)std::max(1.0, fs0 / node_chunks);
-    if (rows_k > 0) {
-        // split the histogram time between the per-row and per-variable terms
-        // in the ratio of the defaults
-        const double base = (double)saved.hist_cost_row * rows + (double)saved.hist_cost_var * rows_k;
-        const double scale = base > 0 ? fs1 / base : 1.0;
-        c->opt.hist_cost_row = (int64_t)std::max(1.0, saved.hist_cost_row * scale);
-        c->opt.hist_cost_var = (int64_t)std::max(1.0, saved.hist_cost_var * scale);
+    double a = 0, b = 0;
+    if (hy.size() >= 2) {
+        fit2(hx0, hx1, hy, a, b);
+        c->opt.hist_cost_row = (int64_t)std::max(1.0, a);
+        c->opt.hist_cost_var = (int64_t)std::max(1.0, b);
+    }
+    if (by.size() >= 2) {
+        fit2(bx0, bx1, by, a, b);
+        c->opt.bitmap_chunk_cost = (int64_t)std::max(0.0, a);
+        c->opt.bitmap_cost = (int64_t)std::max(1.0, b);
     }
     return FC_OK;
 }

@@ -169,7 +169,29 @@ struct Dfs {
                                                ulonglong2 acc, int cell, int32_t *tab, int lane)
     {
         const Level v = lv[L];
-        for (int s = 0; s < v.arity; ++s) {
+        int s0 = 0;
+        if constexpr (L == K - 1 && L > 0) {
+            // leaves: the first eight child states unrolled, so their shared-memory
+            // loads, popcounts and warp reductions overlap
+            unsigned cnt[8];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                cnt[s] = 0u;
+                if (s < v.arity) {
+                    const ulonglong2 b = stage[(v.slot + s) * 32 + lane];
+                    cnt[s] = (unsigned)(__popcll(acc.x & b.x) + __popcll(acc.y & b.y));
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                if (s < v.arity) {
+                    const unsigned c = __reduce_add_sync(kFull, cnt[s]);
+                    if (lane == 0 && c) atomicAdd(&tab[cell + s * v.stride], (int)c);
+                }
+            }
+            s0 = 8;
+        }
+        for (int s = s0; s < v.arity; ++s) {
             ulonglong2 b;
             if constexpr (L == 0)
                 b = __ldg(reinterpret_cast<const ulonglong2 *>(v.row + (int64_t)s * wstride));
@@ -191,7 +213,7 @@ struct Dfs {
 };
 
 template <int K>
-__device__ __noinline__ void bitmap_task(const CountParams &P, const QVar *qv, int64_t c0, int64_t c1,
+__device__ __forceinline__ void bitmap_task(const CountParams &P, const QVar *qv, int64_t c0, int64_t c1,
                                          ulonglong2 *stage, int32_t *tab, int lane)
 {
     for (int64_t c = c0; c < c1; ++c) {
@@ -317,6 +339,64 @@ __device__ __forceinline__ void key_rows_swar(const CountParams &P, const QVar *
     }
 }
 
+// SWAR keys as byte offsets into an interleaved table: L = 2^lshift copies,
+// cell c of copy j at word c * L + j, and lane l counts into copy l % L.  The
+// copies of one cell sit in consecutive banks, so lanes that hit the same
+// cell do not serialise and (for L = 32) every lane owns a bank.  Strides are
+// pre-scaled by 4L and each 16-bit lane starts at the lane's copy, so a key
+// is one mask or shift away from its atomic's address.  Valid when the
+// interleaved table spans at most 64 KiB (cells x L <= 16384).
+__device__ __forceinline__ void key_rows_swar_bytes(const CountParams &P, const QVar *vs, int k,
+                                                    int64_t r0, int64_t r1, int lshift, int32_t *tab0)
+{
+    char *smem = reinterpret_cast<char *>(tab0);
+    const uint32_t base_bytes = (uint32_t)((threadIdx.x & ((1 << lshift) - 1)) << 2);
+    const int sshift = 2 + lshift;
+    const uint32_t init = base_bytes | (base_bytes << 16);
+    const int64_t ngroups = (r1 - r0) >> 4;
+    for (int64_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
+        const int64_t p = r0 + (g << 4);
+        uint32_t acc[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] = init;
+        int t = 0;
+        for (; t + 2 <= k; t += 2) {  // two columns in flight
+            const QVar v0 = vs[t], v1 = vs[t + 1];
+            const uint4 x0 = __ldg(reinterpret_cast<const uint4 *>(P.D + (int64_t)v0.var * P.m_pad + p));
+            const uint4 x1 = __ldg(reinterpret_cast<const uint4 *>(P.D + (int64_t)v1.var * P.m_pad + p));
+            const uint32_t s0 = (uint32_t)v0.stride << sshift, s1 = (uint32_t)v1.stride << sshift;
+            const uint32_t w0[4] = {x0.x, x0.y, x0.z, x0.w}, w1[4] = {x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                acc[2 * i] += __byte_perm(w0[i], 0u, 0x4240) * s0 + __byte_perm(w1[i], 0u, 0x4240) * s1;
+                acc[2 * i + 1] += __byte_perm(w0[i], 0u, 0x4341) * s0 + __byte_perm(w1[i], 0u, 0x4341) * s1;
+            }
+        }
+        if (t < k) {
+            const QVar v0 = vs[t];
+            const uint4 x0 = __ldg(reinterpret_cast<const uint4 *>(P.D + (int64_t)v0.var * P.m_pad + p));
+            const uint32_t s0 = (uint32_t)v0.stride << sshift;
+            const uint32_t w0[4] = {x0.x, x0.y, x0.z, x0.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                acc[2 * i] += __byte_perm(w0[i], 0u, 0x4240) * s0;
+                acc[2 * i + 1] += __byte_perm(w0[i], 0u, 0x4341) * s0;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            atomicAdd(reinterpret_cast<int *>(smem + (acc[j] & 0xFFFFu)), 1);
+            atomicAdd(reinterpret_cast<int *>(smem + (acc[j] >> 16)), 1);
+        }
+    }
+    for (int64_t p = r0 + (ngroups << 4) + threadIdx.x; p < r1; p += blockDim.x) {
+        uint32_t key = base_bytes;
+        for (int t = 0; t < k; ++t)
+            key += (uint32_t)P.D[(int64_t)vs[t].var * P.m_pad + p] * ((uint32_t)vs[t].stride << sshift);
+        atomicAdd(reinterpret_cast<int *>(smem + key), 1);
+    }
+}
+
 // Scalar keys (any table size up to 2^31 cells), counted in global memory.
 __device__ __forceinline__ void key_rows_global(const CountParams &P, const QVar *vs, int k,
                                                 int64_t r0, int64_t r1, int32_t *tab)
@@ -370,9 +450,17 @@ __global__ void __launch_bounds__(512, 2) count_kernel(const CountParams P)
         const int64_t c1 = nchunks * (W.part + 1) / h.nparts;
         const int64_t r0 = c0 * kChunkRows;
         const int64_t r1 = min(P.m, c1 * kChunkRows);
-        const bool in_smem = h.strategy == kHist;
-        int copies = 1;
-        if (in_smem) {
+        const bool in_smem = h.strategy == kHist || h.strategy == kMarginal;
+        int copies = 1;   // per-warp copies (large tables, unscaled keys)
+        int lshift = -1;  // log2 of the interleaved copies (tables of <= 16384 cells)
+        if (h.strategy == kHist && h.cells <= 16384) {
+            lshift = 0;
+            // L copies plus the folded table must fit: cells (L + 1) <= smem_cells
+            while (lshift < 5 && (h.cells << (lshift + 1)) <= 16384 &&
+                   (h.cells << (lshift + 1)) + h.cells <= P.smem_cells)
+                ++lshift;
+            for (int c = threadIdx.x; c < (h.cells << lshift); c += blockDim.x) smem_tab[c] = 0;
+        } else if (in_smem) {
             copies = min(P.hist_copies, P.smem_cells / max(h.cells, 1));
             copies = max(1, min(copies, nwarps));
             for (int c = threadIdx.x; c < h.cells * copies; c += blockDim.x) smem_tab[c] = 0;
@@ -387,6 +475,13 @@ __global__ void __launch_bounds__(512, 2) count_kernel(const CountParams P)
                 else
                     atomicAdd(&P.tables[h.table_off], (int32_t)(r1 - r0));
             }
+        } else if (h.strategy == kMarginal) {
+            // one variable: its per-state counts were taken at load time
+            const QVar v = s_vars[0];
+            for (int s = threadIdx.x; s < v.arity; s += blockDim.x)
+                smem_tab[s * v.stride] = (int32_t)P.marg[v.soff + s];
+        } else if (lshift >= 0) {
+            key_rows_swar_bytes(P, s_vars, k, r0, r1, lshift, smem_tab);
         } else if (in_smem) {
             key_rows_swar(P, s_vars, k, r0, r1, smem_tab + (warp % copies) * h.cells);
         } else {
@@ -394,11 +489,24 @@ __global__ void __launch_bounds__(512, 2) count_kernel(const CountParams P)
         }
         __syncthreads();
 
+        // the final table: the interleaved copies are summed into the words that
+        // follow them (cells x (L + 1) always fits), lanes reading rotated words
+        int32_t *fin = smem_tab;
+        if (lshift > 0) {
+            const int L = 1 << lshift;
+            fin = smem_tab + (h.cells << lshift);
+            for (int c = threadIdx.x; c < h.cells; c += blockDim.x) {
+                int32_t v = 0;
+                for (int j = 0; j < L; ++j) v += smem_tab[(c << lshift) + ((j + c) & (L - 1))];
+                fin[c] = v;
+            }
+            __syncthreads();
+        }
         if (in_smem) {
             for (int c = threadIdx.x; c < h.cells; c += blockDim.x) {
-                int32_t v = smem_tab[c];
-                for (int j = 1; j < copies; ++j) v += smem_tab[j * h.cells + c];
-                if (copies > 1) smem_tab[c] = v;
+                int32_t v = fin[c];
+                for (int j = 1; j < copies; ++j) v += fin[j * h.cells + c];
+                if (copies > 1) fin[c] = v;
                 if (h.nparts == 1) {
                     if (P.write_tables) P.tables[h.table_off + c] = v;
                 } else if (v) {
@@ -411,7 +519,7 @@ __global__ void __launch_bounds__(512, 2) count_kernel(const CountParams P)
         if (h.score_kind != kNoScore) {
             const int64_t *mc = P.marg + h.child_soff;
             if (h.nparts == 1 && in_smem) {
-                const float s = block_score<false>(smem_tab, h.cells, h.r_child, h.score_kind, mc, P.m, P.ess, s_red);
+                const float s = block_score<false>(fin, h.cells, h.r_child, h.score_kind, mc, P.m, P.ess, s_red);
                 if (threadIdx.x == 0) P.scores[h.score_slot] = s;
             } else {
                 __threadfence();
@@ -449,6 +557,19 @@ const void *bitmap_kernel_ptr() { return (const void *)bitmap_kernel; }
 size_t bitmap_smem_bytes(int threads, int stage_slots)
 {
     return (size_t)(threads / 32) * stage_slots * 32 * sizeof(ulonglong2);
+}
+
+// CTAs of bitmap_kernel one SM holds (the dynamic shared-memory limit of the
+// kernel is raised first, or the occupancy query would report none).
+int bitmap_ctas_per_sm(int threads, int stage_slots)
+{
+    const size_t smem = bitmap_smem_bytes(threads, stage_slots);
+    if (cudaFuncSetAttribute(bitmap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 1;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bitmap_kernel, threads, smem) != cudaSuccess)
+        return 1;
+    return per_sm > 0 ? per_sm : 1;
 }
 
 cudaError_t launch_count(const CountParams &p, int grid, int threads, size_t smem, cudaStream_t s)

@@ -12,7 +12,7 @@ constexpr int kMaxBitmapK = 8;     // deepest DFS the bitmap kernel is instantia
 constexpr int kChunkRows = 4096;   // row granule of work items (64 words of 64 bits)
 constexpr int kChunkWords = kChunkRows / 64;
 
-enum Strategy : int32_t { kBitmap = 0, kHist = 1, kGAtomic = 2, kSort = 3 };
+enum Strategy : int32_t { kBitmap = 0, kHist = 1, kGAtomic = 2, kSort = 3, kMarginal = 4 };
 enum ScoreKind : int32_t { kNoScore = -1, kLL = 0, kMDL = 1, kBDeu = 2, kMI = 3 };
 
 // Status word values written by kernels (0 = fine).
@@ -91,6 +91,7 @@ cudaError_t launch_mask_tail_bits(uint64_t *bits, int64_t rows, int64_t wstride,
 cudaError_t launch_count(const CountParams &p, int grid, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_bitmap(const CountParams &p, int grid, int threads, cudaStream_t s);
 size_t bitmap_smem_bytes(int threads, int stage_slots);
+int bitmap_ctas_per_sm(int threads, int stage_slots);
 const void *count_kernel_ptr();
 const void *bitmap_kernel_ptr();
 

@@ -9,18 +9,21 @@
 // dense contraction over the m instances, so it runs on the tensor cores:
 //
 //   * operands are built on the fly from the bitmaps: each bit becomes one
-//     e4m3 byte (1.0 = 0x38 or 0), written K-major into shared memory with the
-//     128-byte swizzle the MMA descriptors describe;
+//     e4m3 byte, 0x08 (= 2^-6, the smallest normal) or 0, written K-major into
+//     shared memory with the 128-byte swizzle the MMA descriptors describe;
 //   * tcgen05.mma.cta_group::1.kind::f8f6f4 (M = 128, N = 256, K = 32) issued
-//     by one thread accumulates in FP32 in tensor memory.  Products are 0 or
-//     1 and every partial sum is an integer no larger than the rows of one
-//     split, which the planner keeps far below 2^24, so the FP32 sums are
-//     exact; the result is read with tcgen05.ld, rounded to int32 and added
-//     to C (split-K over the rows);
-//   * only tiles that touch the upper triangle of C are computed.
+//     by one thread accumulates in FP32 in tensor memory.  Every product is 0
+//     or 2^-12 and every partial sum is 2^-12 times an integer no larger than
+//     the rows of one split, which the planner keeps far below 2^24, so the
+//     FP32 sums are exact; the result is read with tcgen05.ld, scaled by 2^12,
+//     converted to int32 and added to C (split-K over the rows);
+//   * only tiles that touch the upper triangle of C are computed; on tiles
+//     whose 128 A rows lie inside their 256 B rows, A is read from the B
+//     buffer instead of being built twice.
 //
-// Pipeline per CTA: 8 producer warps fill kStages shared-memory stages and
-// signal a "full" mbarrier; the MMA thread waits for it, issues four MMAs and
+// Pipeline per CTA: 16 producer warps fill kStages shared-memory stages
+// (loading the bitmap words three stages ahead of the one they expand)
+// and signal a "full" mbarrier; the MMA thread waits for it, issues four MMAs and
 // commits to the stage's "empty" mbarrier.  Every wait is bounded by
 // `wait_limit` polls; a wait that runs out sets the status word and the CTA
 // winds down (no trap, TMEM always released).
@@ -34,7 +37,7 @@ constexpr int kM = 128;
 constexpr int kN = 256;
 constexpr int kKStage = 128;                 // instances per stage = bytes per operand row
 constexpr int kStages = 4;
-constexpr int kProducerWarps = 8;
+constexpr int kProducerWarps = 16;
 constexpr int kProducers = kProducerWarps * 32;
 constexpr int kThreads = kProducers + 32;    // + the MMA / TMEM warp
 constexpr int kABytes = kM * kKStage;        // 16 KiB
@@ -107,12 +110,15 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar)
                  : "memory");
 }
 
-// Four bits -> four e4m3 bytes (1.0 = 0x38 where the bit is set).  The multiply
-// places bit i at bit 8i without carries (the shifted copies do not overlap).
+// Four bits -> four e4m3 bytes (0x08 = 2^-6 where the bit is set).  The
+// multiply places bit i at bit 8i + 3; its four shifted copies are 7 bits
+// apart, so no carries occur.
 __device__ __forceinline__ uint32_t expand4(uint32_t nib)
 {
-    return ((nib * 0x00204081u) & 0x01010101u) * 0x38u;
+    return (nib * 0x01020408u) & 0x08080808u;
 }
+
+constexpr float kOneHotScale = 4096.0f;  // 1 / (2^-6 * 2^-6)
 
 __device__ __forceinline__ void store_row_word(uint8_t *tile, int row, int half, uint64_t w)
 {
@@ -182,10 +188,40 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
+    // A tile inside the B tile's rows: A is a 16 KiB-aligned slice of B.
+    const int a_in_b = (ta * kM >= tb * kN && ta * kM + kM <= tb * kN + kN) ? ta * kM - tb * kN : -1;
     if (warp < kProducerWarps) {
         // ---------------------------------------------------------- producers
+        constexpr int kTasksMax = ((kM + kN) * 2 + kProducers - 1) / kProducers;
+        const int first = a_in_b >= 0 ? kM * 2 : 0;  // skip the A rows when A comes from B
+        const int ntask = (kM + kN) * 2 - first;
+        // words of stages st + 1, st + 2, st + 3 in flight while stage st is expanded
+        uint64_t p1[kTasksMax], p2[kTasksMax], p3[kTasksMax];
+        auto load = [&](int64_t st, uint64_t (&dst)[kTasksMax]) {
+            const int64_t kw = (st0 + st) * 2;  // first 64-bit word of that stage
+#pragma unroll
+            for (int j = 0; j < kTasksMax; ++j) {
+                const int u = first + threadIdx.x + j * kProducers;
+                const int i = u >> 1, half = u & 1;
+                const int grow = i < kM ? ta * kM + i : tb * kN + (i - kM);
+                dst[j] = (st < nst && u < first + ntask && grow < P.R)
+                             ? __ldg(P.bits + (int64_t)grow * P.wstride + kw + half)
+                             : 0ull;
+            }
+        };
+        load(0, p1);
+        load(1, p2);
+        load(2, p3);
         for (int64_t st = 0; st < nst; ++st) {
             const int slot = (int)(st % kStages);
+            uint64_t cur[kTasksMax];
+#pragma unroll
+            for (int j = 0; j < kTasksMax; ++j) {
+                cur[j] = p1[j];
+                p1[j] = p2[j];
+                p2[j] = p3[j];
+            }
+            load(st + 3, p3);
             if (st >= kStages) {
                 if (!mbar_wait(empty0 + 8 * slot, (uint32_t)((st / kStages - 1) & 1), P.wait_limit)) {
                     atomicExch(&s_abort, 1);
@@ -195,16 +231,16 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
             if (*(volatile int *)&s_abort) break;
             uint8_t *a_tile = smem + slot * kStageBytes;
             uint8_t *b_tile = a_tile + kABytes;
-            const int64_t kw = (st0 + st) * 2;  // first 64-bit word of this stage
-            for (int u = threadIdx.x; u < (kM + kN) * 2; u += kProducers) {
-                const int i = u >> 1, half = u & 1;
-                const int grow = i < kM ? ta * kM + i : tb * kN + (i - kM);
-                uint64_t w = 0ull;
-                if (grow < P.R) w = __ldg(P.bits + (int64_t)grow * P.wstride + kw + half);
-                if (i < kM)
-                    store_row_word(a_tile, i, half, w);
-                else
-                    store_row_word(b_tile, i - kM, half, w);
+#pragma unroll
+            for (int j = 0; j < kTasksMax; ++j) {
+                const int u = first + threadIdx.x + j * kProducers;
+                if (u < first + ntask) {
+                    const int i = u >> 1, half = u & 1;
+                    if (i < kM)
+                        store_row_word(a_tile, i, half, cur[j]);
+                    else
+                        store_row_word(b_tile, i - kM, half, cur[j]);
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(full0 + 8 * slot);
@@ -219,8 +255,8 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
                 break;
             }
             tc_fence_after();
-            const uint32_t a_addr = smem_u32(smem + slot * kStageBytes);
-            const uint32_t b_addr = a_addr + kABytes;
+            const uint32_t b_addr = smem_u32(smem + slot * kStageBytes) + kABytes;
+            const uint32_t a_addr = a_in_b >= 0 ? b_addr + (uint32_t)a_in_b * kKStage : b_addr - kABytes;
 #pragma unroll
             for (int kk = 0; kk < kKStage / 32; ++kk)
                 mma_f8(tmem, smem_desc(a_addr + 32 * kk), smem_desc(b_addr + 32 * kk),
@@ -257,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
                 if (row < P.R) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int v = __float2int_rn(__uint_as_float(r[j]));
+                        const int v = __float2int_rn(__uint_as_float(r[j]) * kOneHotScale);
                         if (v) atomicAdd(crow + c0 + j, v);
                     }
                 }
