@@ -107,20 +107,24 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ workloads
 
-def make_workload(name: str):
-    """Seeded inputs of one workload (host arrays)."""
-    c = CONFIGS[name]
-    if name in ("tiny", "random"):
-        db = config_database(name)
+def make_workload(name: str, m: int | None = None, nq: int | None = None):
+    """Seeded inputs of one workload (host arrays); m / nq shrink it (profiling)."""
+    c = dict(CONFIGS[name])
+    if m:
+        c["m"] = m
+    if nq:
+        c["nq"] = nq
+    if name in ("tiny", "random", "large"):
+        db = config_database(name, c["m"])
         queries = subset_queries(db.n, (1, 2, 3)) if name == "tiny" else \
             random_queries(db.n, c["nq"], c["k"][0], c["k"][1], c["seed"])
         return {"db": db, "queries": queries}
     if name == "scores":
-        db = config_database(name)
+        db = config_database(name, c["m"])
         child, parents = score_queries(db.n, c["nq"], c["pa"][0], c["pa"][1], c["seed"])
         return {"db": db, "child": child, "parents": parents}
     if name == "pairs":
-        return {"db": config_database(name)}
+        return {"db": config_database(name, c["m"])}
     if name == "support":
         bits = zipf_transaction_bitmaps(c["n_items"], c["m"], c["zipf_s"], c["mean_len"], c["seed"])
         probs = zipf_item_probs(c["n_items"], c["zipf_s"], c["mean_len"])
@@ -131,7 +135,7 @@ def make_workload(name: str):
 
 def describe(name: str, w) -> dict:
     c = CONFIGS[name]
-    if name in ("tiny", "random"):
+    if name in ("tiny", "random", "large"):
         ks = [len(q) for q in w["queries"]]
         return {"workload": f"{name}: n={w['db'].n} arity {c['arity'][0]}-{c['arity'][1]}, m={w['db'].m}, "
                             f"{len(ks)} count queries of {min(ks)}-{max(ks)} variables",
@@ -159,7 +163,7 @@ def oracle_rate(name: str, w, seconds: float, cores: int):
     sample = ""
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=cores) as ex:
-        if name in ("tiny", "random", "scores"):
+        if name in ("tiny", "random", "large", "scores"):
             orc = oracle.DB(w["db"].D, w["db"].arities)
             if name == "scores":
                 jobs = [(w["child"][q], w["parents"][q]) for q in range(len(w["child"]))]
@@ -210,14 +214,14 @@ def oracle_rate(name: str, w, seconds: float, cores: int):
 
 
 METRIC = "count queries/s (exact full contingency tables, batched persistent launch)"
-UNITS = {"tiny": "queries/s", "random": "queries/s", "scores": "queries/s", "pairs": "pairs/s",
-         "support": "itemsets/s"}
+UNITS = {"tiny": "queries/s", "random": "queries/s", "large": "queries/s", "scores": "queries/s",
+         "pairs": "pairs/s", "support": "itemsets/s"}
 
 
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, args.m, args.nq)
     cores = os.cpu_count() or 1
     rate, sample = oracle_rate(args.workload, w, args.ref_seconds, cores)
     steps = []
@@ -256,14 +260,14 @@ def run_gpu(args, rank: int, world: int):
         torch.cuda.synchronize()
 
     name = args.workload
-    w = make_workload(name)
+    w = make_workload(name, args.m, args.nq)
     stream = torch.cuda.Stream()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
     hbm, bf16, bf16_sus, peak_src = peaks()
 
     # ---- set up the plan (device-resident inputs) and the e2e call
     per_query = None
-    if name in ("tiny", "random"):
+    if name in ("tiny", "random", "large"):
         db, queries = w["db"], w["queries"]
         ctx = fc.fc_load(db.D, db.arities)
         if args.autotune:
@@ -466,6 +470,8 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip fc_autotune (strategy thresholds from the default cost model)")
     ap.add_argument("--strategy", type=int, default=-1, help="force one counting strategy (-1 = planner's choice)")
+    ap.add_argument("--m", type=int, default=None, help="instances (default: the workload's own)")
+    ap.add_argument("--nq", type=int, default=None, help="queries / itemsets (default: the workload's own)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -1152,9 +1152,10 @@ extern "C" int fc_plan_support(fc_ctx *c, int32_t nq, const int32_t *set_off, co
     P.n_items = c->n;
     p->sup_threads = std::max(1, std::min(32, o.support_warps)) * 32;
     P.sets_per_item = (p->sup_threads / 32) * std::max(1, o.support_sets_per_warp);
-    const int64_t part_words = std::max<int64_t>(64, round_up(o.support_part_words, 32));
+    // word ranges of whole 64-word steps (32 lanes x 2 words)
+    const int64_t part_words = std::max<int64_t>(64, round_up(o.support_part_words, 64));
     P.nparts = (int32_t)std::max<int64_t>(1, (c->words + part_words - 1) / part_words);
-    P.words_per_part = (int32_t)round_up((c->words + P.nparts - 1) / P.nparts, 32);
+    P.words_per_part = (int32_t)round_up((c->words + P.nparts - 1) / P.nparts, 64);
     P.m_tail = c->m;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, support_kernel_ptr(), p->sup_threads, 0);

@@ -353,43 +353,32 @@ __device__ __forceinline__ void key_rows_swar_bytes(const CountParams &P, const 
     const uint32_t base_bytes = (uint32_t)((threadIdx.x & ((1 << lshift) - 1)) << 2);
     const int sshift = 2 + lshift;
     const uint32_t init = base_bytes | (base_bytes << 16);
-    const int64_t ngroups = (r1 - r0) >> 4;
+    // 32 rows per thread and step: two 16-byte loads per column
+    const int64_t ngroups = (r1 - r0) >> 5;
     for (int64_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
-        const int64_t p = r0 + (g << 4);
-        uint32_t acc[8];
+        const int64_t p = r0 + (g << 5);
+        uint32_t acc[16];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j] = init;
-        int t = 0;
-        for (; t + 2 <= k; t += 2) {  // two columns in flight
-            const QVar v0 = vs[t], v1 = vs[t + 1];
-            const uint4 x0 = __ldg(reinterpret_cast<const uint4 *>(P.D + (int64_t)v0.var * P.m_pad + p));
-            const uint4 x1 = __ldg(reinterpret_cast<const uint4 *>(P.D + (int64_t)v1.var * P.m_pad + p));
-            const uint32_t s0 = (uint32_t)v0.stride << sshift, s1 = (uint32_t)v1.stride << sshift;
-            const uint32_t w0[4] = {x0.x, x0.y, x0.z, x0.w}, w1[4] = {x1.x, x1.y, x1.z, x1.w};
+        for (int j = 0; j < 16; ++j) acc[j] = init;
+        for (int t = 0; t < k; ++t) {
+            const QVar v = vs[t];
+            const uint4 *col = reinterpret_cast<const uint4 *>(P.D + (int64_t)v.var * P.m_pad + p);
+            const uint4 x0 = __ldg(col), x1 = __ldg(col + 1);
+            const uint32_t st = (uint32_t)v.stride << sshift;
+            const uint32_t w[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                acc[2 * i] += __byte_perm(w0[i], 0u, 0x4240) * s0 + __byte_perm(w1[i], 0u, 0x4240) * s1;
-                acc[2 * i + 1] += __byte_perm(w0[i], 0u, 0x4341) * s0 + __byte_perm(w1[i], 0u, 0x4341) * s1;
-            }
-        }
-        if (t < k) {
-            const QVar v0 = vs[t];
-            const uint4 x0 = __ldg(reinterpret_cast<const uint4 *>(P.D + (int64_t)v0.var * P.m_pad + p));
-            const uint32_t s0 = (uint32_t)v0.stride << sshift;
-            const uint32_t w0[4] = {x0.x, x0.y, x0.z, x0.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                acc[2 * i] += __byte_perm(w0[i], 0u, 0x4240) * s0;
-                acc[2 * i + 1] += __byte_perm(w0[i], 0u, 0x4341) * s0;
+            for (int i = 0; i < 8; ++i) {
+                acc[2 * i] += __byte_perm(w[i], 0u, 0x4240) * st;
+                acc[2 * i + 1] += __byte_perm(w[i], 0u, 0x4341) * st;
             }
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 16; ++j) {
             atomicAdd(reinterpret_cast<int *>(smem + (acc[j] & 0xFFFFu)), 1);
             atomicAdd(reinterpret_cast<int *>(smem + (acc[j] >> 16)), 1);
         }
     }
-    for (int64_t p = r0 + (ngroups << 4) + threadIdx.x; p < r1; p += blockDim.x) {
+    for (int64_t p = r0 + (ngroups << 5) + threadIdx.x; p < r1; p += blockDim.x) {
         uint32_t key = base_bytes;
         for (int t = 0; t < k; ++t)
             key += (uint32_t)P.D[(int64_t)vs[t].var * P.m_pad + p] * ((uint32_t)vs[t].stride << sshift);

@@ -7,9 +7,9 @@
 // suffix ANDs s_t = a_{t+1} & ... & a_{k-1}, the leave-one-out set of item t
 // is p_t & s_t, so one pass over the words yields all k + 1 counts.
 //
-// A warp owns one itemset at a time; its lanes read 32 consecutive 64-bit
-// words of every item row (coalesced 256-byte loads) and keep the k + 1
-// counts in registers.  Work items are (word range, group of itemsets),
+// A warp owns one itemset at a time; its lanes read 64 consecutive 64-bit
+// words of every item row (coalesced 16-byte loads per lane) and keep the
+// k + 1 counts in registers.  Work items are (word range, group of itemsets),
 // issued range-major, so all CTAs sweep the same slice of the item bitmaps at
 // the same time and the slice stays in L2 while every itemset passes over it.
 #include "fc_internal.h"
@@ -19,36 +19,48 @@ namespace {
 
 constexpr unsigned kFullMask = 0xffffffffu;
 
+// One itemset of K >= 2 items over words [w0, w1) (w0 even): each lane takes
+// two consecutive words per step (16-byte loads).  Item rows are zero past m
+// and padded with zero words, so reading one word past w1 at the array's end
+// adds nothing.  Prefix ANDs p_t = a_0 & .. & a_{t-1} and suffix ANDs
+// s_t = a_{t+1} & .. & a_{K-1} give every leave-one-out set as p_t & s_t
+// (3K - 5 ANDs per word) and the full set as p_K.
 template <int K>
 __device__ __forceinline__ void support_set(const SupportParams &P, const int32_t *items,
                                             int64_t w0, int64_t w1, int lane, int32_t *supp,
                                             int32_t *sub, bool atomic)
 {
-    const uint64_t *row[K > 0 ? K : 1];
+    static_assert(K >= 2, "two or more items");
+    const uint64_t *row[K];
 #pragma unroll
     for (int t = 0; t < K; ++t) row[t] = P.bits + (int64_t)items[t] * P.wstride;
     unsigned full = 0u;
-    unsigned loo[K > 0 ? K : 1];
+    unsigned loo[K];
 #pragma unroll
     for (int t = 0; t < K; ++t) loo[t] = 0u;
-    const int64_t last = P.words - 1;
-    const int rem = (int)(P.m_tail & 63);
-    const uint64_t tail = rem ? ((1ull << rem) - 1ull) : ~0ull;
-    for (int64_t w = w0 + lane; w < w1; w += 32) {
-        uint64_t a[K > 0 ? K : 1];
+    for (int64_t w = w0 + 2 * lane; w < w1; w += 64) {
+        ulonglong2 a[K];
 #pragma unroll
-        for (int t = 0; t < K; ++t) a[t] = __ldg(row[t] + w);
-        uint64_t pre[K + 1];
-        pre[0] = w == last ? tail : ~0ull;
+        for (int t = 0; t < K; ++t) a[t] = __ldg(reinterpret_cast<const ulonglong2 *>(row[t] + w));
 #pragma unroll
-        for (int t = 0; t < K; ++t) pre[t + 1] = pre[t] & a[t];
-        uint64_t suf = ~0ull;
+        for (int h = 0; h < 2; ++h) {
+            uint64_t x[K];
 #pragma unroll
-        for (int t = K - 1; t >= 0; --t) {
-            loo[t] += (unsigned)__popcll(pre[t] & suf);
-            suf &= a[t];
+            for (int t = 0; t < K; ++t) x[t] = h ? a[t].y : a[t].x;
+            uint64_t pre[K + 1];  // pre[t] = AND of x[0..t-1], pre[0] unused
+            pre[1] = x[0];
+#pragma unroll
+            for (int t = 2; t <= K; ++t) pre[t] = pre[t - 1] & x[t - 1];
+            uint64_t suf = x[K - 1];  // AND of x[t+1..K-1] for t = K-2
+            loo[K - 1] += (unsigned)__popcll(pre[K - 1]);
+#pragma unroll
+            for (int t = K - 2; t >= 1; --t) {
+                loo[t] += (unsigned)__popcll(pre[t] & suf);
+                suf &= x[t];
+            }
+            loo[0] += (unsigned)__popcll(suf);
+            full += (unsigned)__popcll(pre[K]);
         }
-        full += (unsigned)__popcll(pre[K]);
     }
     full = __reduce_add_sync(kFullMask, full);
 #pragma unroll
@@ -67,7 +79,8 @@ __device__ __forceinline__ void support_set(const SupportParams &P, const int32_
     }
 }
 
-// Itemsets larger than the unrolled sizes: the k + 1 ANDs recomputed per word.
+// Itemsets outside the unrolled sizes (0, 1 or more than 6 items): the k + 1
+// ANDs recomputed per word, the last word masked to the m transactions.
 __device__ void support_set_any(const SupportParams &P, const int32_t *items, int k, int64_t w0,
                                 int64_t w1, int lane, int32_t *supp, int32_t *sub, bool atomic)
 {
@@ -119,15 +132,11 @@ __global__ void __launch_bounds__(1024) support_kernel(const SupportParams P)
             int32_t *supp = P.support + q;
             int32_t *sub = P.sub_support + a;
             switch (k) {
-            case 0: support_set<0>(P, items, w0, w1, lane, supp, sub, atomic); break;
-            case 1: support_set<1>(P, items, w0, w1, lane, supp, sub, atomic); break;
             case 2: support_set<2>(P, items, w0, w1, lane, supp, sub, atomic); break;
             case 3: support_set<3>(P, items, w0, w1, lane, supp, sub, atomic); break;
             case 4: support_set<4>(P, items, w0, w1, lane, supp, sub, atomic); break;
             case 5: support_set<5>(P, items, w0, w1, lane, supp, sub, atomic); break;
             case 6: support_set<6>(P, items, w0, w1, lane, supp, sub, atomic); break;
-            case 7: support_set<7>(P, items, w0, w1, lane, supp, sub, atomic); break;
-            case 8: support_set<8>(P, items, w0, w1, lane, supp, sub, atomic); break;
             default: support_set_any(P, items, k, w0, w1, lane, supp, sub, atomic); break;
             }
         }
