@@ -81,15 +81,19 @@ struct DevGuard {
 
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
-// Device buffer owned by the runtime.
+// Device buffer owned by the runtime, or a view of a context pool buffer
+// (plans made by the synchronous entry points borrow them, so a call
+// allocates nothing once the pool has grown).
 struct DBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    bool owned = true;
     void release()
     {
-        if (p) cudaFree(p);
+        if (p && owned) cudaFree(p);
         p = nullptr;
         bytes = 0;
+        owned = true;
     }
     cudaError_t ensure(size_t want)
     {
@@ -150,6 +154,8 @@ struct fc_ctx {
     Options opt;
     // scratch of the host-buffer entry points
     DBuf io[3];
+    DBuf pool[6];        // buffers lent to one-shot plans (descriptors, counters, tables, sort, pairs)
+    bool borrow = false; // set while a synchronous entry point builds its plan
     std::vector<uint32_t> mark;
     uint32_t epoch = 0;
 };
@@ -214,6 +220,28 @@ struct fc_plan {
     size_t upload_bytes = 0;  // host-to-device bytes of the plan's descriptors
     std::vector<GraphEntry> graphs;
 };
+
+namespace {
+
+// A plan buffer: its own allocation, or a view of the context's pool slot.
+cudaError_t plan_buf(fc_ctx *c, DBuf &b, int slot, size_t bytes)
+{
+    if (!c->borrow) return b.ensure(bytes);
+    cudaError_t e = c->pool[slot].ensure(bytes);
+    if (e != cudaSuccess) return e;
+    b.p = c->pool[slot].p;
+    b.bytes = c->pool[slot].bytes;
+    b.owned = false;
+    return cudaSuccess;
+}
+
+struct BorrowScope {
+    fc_ctx *c;
+    explicit BorrowScope(fc_ctx *ctx) : c(ctx) { c->borrow = true; }
+    ~BorrowScope() { c->borrow = false; }
+};
+
+}  // namespace
 
 // ---------------------------------------------------------------- loading
 
@@ -381,6 +409,7 @@ extern "C" void fc_free(fc_ctx *c)
     DevGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto &b : c->io) b.release();
+    for (auto &b : c->pool) b.release();
     cudaFree(c->d_D);
     cudaFree(c->d_bits);
     cudaFree(c->d_marg);
@@ -469,11 +498,12 @@ void entropy_order(const fc_ctx *c, QVar *v, int k)
     std::stable_sort(v, v + k, [&](const QVar &a, const QVar &b) { return c->entropy[a.var] < c->entropy[b.var]; });
 }
 
-bool bitmap_ok(const fc_ctx *c, const QVar *v, int k)
+// Staged slots of the query in entropy order; the ordered copy goes to o.
+bool bitmap_ok(const fc_ctx *c, const QVar *v, int k, QVar *o)
 {
     if (k < 1 || k > kMaxBitmapK) return false;
-    std::vector<QVar> o(v, v + k);
-    entropy_order(c, o.data(), k);
+    std::copy(v, v + k, o);
+    entropy_order(c, o, k);
     int slots = 0;
     for (int t = 1; t < k; ++t) slots += o[t].arity;
     return slots <= c->opt.stage_slots;
@@ -486,13 +516,9 @@ QPlan choose(const fc_ctx *c, const QVar *v, int k, int64_t cells, int32_t smem_
     const double rows = (double)c->m;
     const double flush = (double)cells * o.flush_cost;
     const bool fits = cells <= smem_cells;
-    const bool bm = bitmap_ok(c, v, k);
-    double nodes = 0.0;
-    if (bm) {
-        std::vector<QVar> ord(v, v + k);
-        entropy_order(c, ord.data(), k);
-        nodes = dfs_nodes(ord.data(), k);
-    }
+    QVar ord[kMaxK];
+    const bool bm = bitmap_ok(c, v, k, ord);
+    const double nodes = bm ? dfs_nodes(ord, k) : 0.0;
     const double hist = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) + flush;
     const double bitmap = bm ? chunks * ((double)o.bitmap_chunk_cost + nodes * o.bitmap_cost) + flush : 1e300;
     const double gatomic = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) * 2.0 + (double)cells * 4.0;
@@ -680,17 +706,18 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     std::memcpy(host.data() + o_it, items.data(), sizeof(Item) * items.size());
     std::memcpy(host.data() + o_ql, qlist.data(), sizeof(int32_t) * qlist.size());
     std::memcpy(host.data() + o_bq, bq.data(), sizeof(int32_t) * bq.size());
-    cudaError_t e = p->desc.ensure(total);
+    cudaError_t e = plan_buf(c, p->desc, 0, total);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->desc.p, host.data(), total, cudaMemcpyHostToDevice, c->stream);
     p->upload_bytes = total;
     p->n_counters = 2 + nq;
-    if (e == cudaSuccess) e = p->counters.ensure(sizeof(int32_t) * p->n_counters);
-    if (e == cudaSuccess && score_kind != kNoScore) e = p->scratch_tables.ensure(sizeof(int32_t) * std::max<int64_t>(p->table_buf_cells, 1));
+    if (e == cudaSuccess) e = plan_buf(c, p->counters, 1, sizeof(int32_t) * p->n_counters);
+    if (e == cudaSuccess && score_kind != kNoScore)
+        e = plan_buf(c, p->scratch_tables, 2, sizeof(int32_t) * std::max<int64_t>(p->table_buf_cells, 1));
     if (e == cudaSuccess && !p->sort_jobs.empty()) {
         const int tile = sort_tile_rows();
         const int64_t nb = (c->m + tile - 1) / tile;
         const size_t kb = round_up(sizeof(uint32_t) * c->m, 256);
-        e = p->sort_mem.ensure(2 * kb + sizeof(uint32_t) * 256 * nb);
+        e = plan_buf(c, p->sort_mem, 3, 2 * kb + sizeof(uint32_t) * 256 * nb);
         if (e == cudaSuccess) {
             uint8_t *base = (uint8_t *)p->sort_mem.p;
             p->sort_sc.keys_a = (uint32_t *)base;
@@ -999,7 +1026,11 @@ extern "C" int fc_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, con
     if (!c || (nq > 0 && !tables)) return fail(FC_ERR_ARG, "fc_count_batch: null argument");
     DevGuard g(c->device);
     fc_plan *p = nullptr;
-    int rc = fc_plan_count(c, nq, var_off, vars, table_off, &p);
+    int rc;
+    {
+        BorrowScope b(c);
+        rc = fc_plan_count(c, nq, var_off, vars, table_off, &p);
+    }
     if (rc != FC_OK) return rc;
     rc = run_to_host(p, tables, sizeof(int32_t) * p->out_cells, nullptr, 0, nullptr, 0);
     fc_plan_free(p);
@@ -1012,7 +1043,11 @@ extern "C" int fc_score_batch(fc_ctx *c, int32_t nq, const int32_t *child, const
     if (!c || (nq > 0 && !scores)) return fail(FC_ERR_ARG, "fc_score_batch: null argument");
     DevGuard g(c->device);
     fc_plan *p = nullptr;
-    int rc = fc_plan_score(c, nq, child, par_off, parents, kind, ess, &p);
+    int rc;
+    {
+        BorrowScope b(c);
+        rc = fc_plan_score(c, nq, child, par_off, parents, kind, ess, &p);
+    }
     if (rc != FC_OK) return rc;
     rc = run_to_host(p, scores, sizeof(float) * nq, nullptr, 0, nullptr, 0);
     fc_plan_free(p);
@@ -1130,11 +1165,11 @@ extern "C" int fc_plan_support(fc_ctx *c, int32_t nq, const int32_t *set_off, co
         if (n_sub > 0) std::memcpy(host.data() + o_it, items, sizeof(int32_t) * n_sub);
         std::memcpy(host.data() + o_ord, order.data(), sizeof(int32_t) * nq);
     }
-    cudaError_t e = p->desc.ensure(total);
+    cudaError_t e = plan_buf(c, p->desc, 0, total);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->desc.p, host.data(), total, cudaMemcpyHostToDevice, c->stream);
     p->upload_bytes = total;
-    if (e == cudaSuccess) e = p->counters.ensure(16);
-    if (e == cudaSuccess) e = p->scratch_tables.ensure(sizeof(int32_t) * std::max<int64_t>(n_sub, 1));
+    if (e == cudaSuccess) e = plan_buf(c, p->counters, 1, 16);
+    if (e == cudaSuccess) e = plan_buf(c, p->scratch_tables, 2, sizeof(int32_t) * std::max<int64_t>(n_sub, 1));
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         fc_plan_free(p);
@@ -1170,7 +1205,11 @@ extern "C" int fc_support_batch(fc_ctx *c, int32_t nq, const int32_t *set_off, c
     if (!c || (nq > 0 && !support)) return fail(FC_ERR_ARG, "fc_support_batch: null argument");
     DevGuard g(c->device);
     fc_plan *p = nullptr;
-    int rc = fc_plan_support(c, nq, set_off, items, &p);
+    int rc;
+    {
+        BorrowScope b(c);
+        rc = fc_plan_support(c, nq, set_off, items, &p);
+    }
     if (rc != FC_OK) return rc;
     rc = run_to_host(p, support, sizeof(int32_t) * nq, sub_support, sizeof(int32_t) * p->n_sub,
                      confidence, sizeof(float) * p->n_sub);
@@ -1225,8 +1264,8 @@ extern "C" int fc_plan_pairs(fc_ctx *c, fc_plan **out)
     for (int a = 0; a < c->n; ++a)
         for (int b = a + 1; b < c->n; ++b, ++idx) off[idx + 1] = off[idx] + (int64_t)c->arity[a] * c->arity[b];
     p->pair_cells = off[npairs];
-    cudaError_t e = p->pairs_C.ensure(sizeof(int32_t) * (size_t)R_pad * R_pad);
-    if (e == cudaSuccess) e = p->pairs_meta.ensure(sizeof(int64_t) * (npairs + 1));
+    cudaError_t e = plan_buf(c, p->pairs_C, 4, sizeof(int32_t) * (size_t)R_pad * R_pad);
+    if (e == cudaSuccess) e = plan_buf(c, p->pairs_meta, 5, sizeof(int64_t) * (npairs + 1));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->pairs_meta.p, off.data(), sizeof(int64_t) * (npairs + 1), cudaMemcpyHostToDevice,
                             c->stream);
@@ -1271,7 +1310,11 @@ extern "C" int fc_pairs_all(fc_ctx *c, int32_t *pair_tables, float *mi)
     if (!c) return fail(FC_ERR_ARG, "fc_pairs_all: null context");
     DevGuard g(c->device);
     fc_plan *p = nullptr;
-    int rc = fc_plan_pairs(c, &p);
+    int rc;
+    {
+        BorrowScope b(c);
+        rc = fc_plan_pairs(c, &p);
+    }
     if (rc != FC_OK) return rc;
     rc = run_to_host(p, pair_tables, pair_tables ? sizeof(int32_t) * p->pair_cells : 0, mi,
                      mi ? sizeof(float) * p->n_pairs : 0, nullptr, 0);

@@ -353,17 +353,20 @@ __device__ __forceinline__ void key_rows_swar_bytes(const CountParams &P, const 
     const uint32_t base_bytes = (uint32_t)((threadIdx.x & ((1 << lshift) - 1)) << 2);
     const int sshift = 2 + lshift;
     const uint32_t init = base_bytes | (base_bytes << 16);
-    // 32 rows per thread and step: two 16-byte loads per column
-    const int64_t ngroups = (r1 - r0) >> 5;
-    for (int64_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
-        const int64_t p = r0 + (g << 5);
+    // Warp groups of 1024 rows: lane l of group G reads 16-byte vectors
+    // 64 G + l and 64 G + 32 + l, so each load instruction covers 512
+    // contiguous bytes of the column.
+    const int64_t nfull = (r1 - r0) >> 10;
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = threadIdx.x; u < (nfull << 5); u += blockDim.x) {
+        const int64_t vec = ((u >> 5) << 6) + lane;  // 16-byte vector index in the range
         uint32_t acc[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc[j] = init;
         for (int t = 0; t < k; ++t) {
             const QVar v = vs[t];
-            const uint4 *col = reinterpret_cast<const uint4 *>(P.D + (int64_t)v.var * P.m_pad + p);
-            const uint4 x0 = __ldg(col), x1 = __ldg(col + 1);
+            const uint4 *col = reinterpret_cast<const uint4 *>(P.D + (int64_t)v.var * P.m_pad + r0) + vec;
+            const uint4 x0 = __ldg(col), x1 = __ldg(col + 32);
             const uint32_t st = (uint32_t)v.stride << sshift;
             const uint32_t w[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
@@ -378,7 +381,7 @@ __device__ __forceinline__ void key_rows_swar_bytes(const CountParams &P, const 
             atomicAdd(reinterpret_cast<int *>(smem + (acc[j] >> 16)), 1);
         }
     }
-    for (int64_t p = r0 + (ngroups << 5) + threadIdx.x; p < r1; p += blockDim.x) {
+    for (int64_t p = r0 + (nfull << 10) + threadIdx.x; p < r1; p += blockDim.x) {
         uint32_t key = base_bytes;
         for (int t = 0; t < k; ++t)
             key += (uint32_t)P.D[(int64_t)vs[t].var * P.m_pad + p] * ((uint32_t)vs[t].stride << sshift);

@@ -70,7 +70,7 @@ def test_random_full_size_all_queries():
         check_batch(ctx, orc, sub, want[::25])
 
 
-@pytest.mark.parametrize("m", [1, 17, 63, 64, 65, 4095, 4096, 4097, 70_001, 131_072 + 13])
+@pytest.mark.parametrize("m", [1, 17, 63, 64, 65, 511, 513, 1023, 1025, 4095, 4096, 4097, 70_001, 131_072 + 13])
 def test_ragged_sizes_every_strategy(m):
     db = random_dag_database(9, m, 2, 5, 3, 0.5, seed=1000 + m % 97)
     ctx = fc.fc_load(db.D, db.arities)
@@ -80,6 +80,9 @@ def test_ragged_sizes_every_strategy(m):
     for s in [fc.FC_STRAT_AUTO] + STRATS:
         fc.fc_set_option(ctx, "strategy", s)
         check_batch(ctx, orc, queries, want)
+    fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_HIST)
+    fc.fc_set_option(ctx, "smem_cells", 40_000)        # interleaved table copies change
+    check_batch(ctx, orc, queries, want)
 
 
 def test_row_split_work_items():
