@@ -49,6 +49,27 @@ def peaks():
         return 6800.0, 1900.0, 1700.0, "fallback"
 
 
+def measured_traffic(workload: str):
+    """DRAM bytes per launch of the workload's dominant kernel from the committed
+    ncu summary, or None when the kernel source changed since the capture."""
+    import hashlib
+    try:
+        lines = open(os.path.join(ROOT, "profiles", "traffic.txt")).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        parts = ln.split()
+        if len(parts) != 5 or ln.startswith("#") or parts[0] != workload:
+            continue
+        src = os.path.join(ROOT, "paper_1804_04640_gb300", "csrc", parts[2])
+        try:
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        except OSError:
+            return None
+        return int(parts[4]) if sha == parts[3] else None
+    return None
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -270,10 +291,10 @@ def run_gpu(args, rank: int, world: int):
     if name in ("tiny", "random", "large"):
         db, queries = w["db"], w["queries"]
         ctx = fc.fc_load(db.D, db.arities)
-        if args.autotune:
-            fc.fc_autotune(ctx)
-        fc.fc_set_option(ctx, "strategy", args.strategy)
         off, flat = fc.pack_lists(queries)
+        if args.autotune:
+            fc.fc_autotune_batch(ctx, off, flat)
+        fc.fc_set_option(ctx, "strategy", args.strategy)
         plan = fc.fc_plan_count(ctx, off, flat)
         toff = fc.fc_plan_table_offsets(plan)
         outs = (torch.empty(int(toff[-1]), dtype=torch.int32, device="cuda"),)
@@ -300,10 +321,11 @@ def run_gpu(args, rank: int, world: int):
     elif name == "scores":
         db = w["db"]
         ctx = fc.fc_load(db.D, db.arities)
-        if args.autotune:
-            fc.fc_autotune(ctx)
-        fc.fc_set_option(ctx, "strategy", args.strategy)
         po, pa = fc.pack_lists(w["parents"])
+        if args.autotune:  # the counting work of a score query is the table over (parents..., child)
+            fo, ff = fc.pack_lists([list(p) + [c] for p, c in zip(w["parents"], w["child"])])
+            fc.fc_autotune_batch(ctx, fo, ff)
+        fc.fc_set_option(ctx, "strategy", args.strategy)
         plan = fc.fc_plan_score(ctx, w["child"], po, pa, "bdeu", 1.0)
         outs = (torch.empty(len(w["child"]), dtype=torch.float32, device="cuda"),)
         units = len(w["child"])
@@ -415,12 +437,12 @@ def run_gpu(args, rank: int, world: int):
         achieved = alg_flops / (ms / 1e3) / 1e12
         fp8_peak = bf16 * 2.0
         roof = {"bound": "tensor", "achieved": achieved, "peak": fp8_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp8_peak, "traffic": None,
+                "frac": achieved / fp8_peak, "traffic": measured_traffic(name),
                 "peak_source": f"{peak_src} bf16 burst x 2 (nominal fp8/bf16 ratio)"}
     else:
         achieved = alg_bytes / (ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "peak_source": f"{peak_src} hbm_gbs"}
+                "traffic": measured_traffic(name), "peak_source": f"{peak_src} hbm_gbs"}
 
     line = None
     if rank == 0:

@@ -255,6 +255,12 @@ int64_t fc_get_option(const fc_ctx *ctx, const char *key);
  * time spent (0 = default).  Results are kept in the context. */
 int fc_autotune(fc_ctx *ctx, int32_t budget_ms);
 
+/* Tune the strategy thresholds for one count batch (arguments as
+ * fc_count_batch): fc_autotune's fit, then the batch itself timed under a few
+ * scalings of the bitmap cost (and with the bitmap strategy off); the fastest
+ * setting stays in the context for later plans. */
+int fc_autotune_batch(fc_ctx *ctx, int32_t nq, const int32_t *var_off, const int32_t *vars);
+
 /* Message of the last error on this host thread ("" if none). */
 const char *fc_last_error(void);
 

@@ -30,7 +30,7 @@ EXPORTS = (
     "fc_support_batch", "fc_plan_count", "fc_plan_score", "fc_plan_support", "fc_plan_pairs",
     "fc_plan_size", "fc_plan_table_offsets", "fc_plan_strategies", "fc_plan_run", "fc_plan_free",
     "fc_sync", "fc_set_option", "fc_get_option", "fc_autotune", "fc_last_error",
-    "fc_selftest_wait_timeout", "fc_count_sorted_noalloc",
+    "fc_selftest_wait_timeout", "fc_count_sorted_noalloc", "fc_autotune_batch",
 )
 
 
@@ -92,6 +92,7 @@ def load_library(build_if_missing: bool = False):
         "fc_set_option": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_int64]),
         "fc_get_option": (ctypes.c_int64, [_vp, ctypes.c_char_p]),
         "fc_autotune": (ctypes.c_int, [_vp, ctypes.c_int32]),
+        "fc_autotune_batch": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p]),
         "fc_last_error": (ctypes.c_char_p, []),
         "fc_selftest_wait_timeout": (ctypes.c_int, [_vp, ctypes.c_int64]),
         "fc_count_sorted_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _i32p,
@@ -366,6 +367,11 @@ def fc_get_option(ctx: Handle, key: str) -> int:
 
 def fc_autotune(ctx: Handle, budget_ms: int = 0):
     _check(load_library().fc_autotune(ctx.ptr, int(budget_ms)))
+
+
+def fc_autotune_batch(ctx: Handle, var_off, vars_):
+    vo, vv = _host(var_off, np.int32), _host(vars_, np.int32)
+    _check(load_library().fc_autotune_batch(ctx.ptr, len(vo) - 1, _ptr(vo, _i32p), _ptr(vv, _i32p)))
 
 
 def fc_last_error() -> str:

@@ -1540,3 +1540,44 @@ extern "C" int fc_autotune(fc_ctx *c, int32_t budget_ms)
     }
     return FC_OK;
 }
+
+// Tunes the strategy thresholds for one batch: the per-size regression of
+// fc_autotune, then the batch itself timed with the bitmap cost scaled by
+// 1/4 .. 4 and with the bitmap strategy off; the fastest setting is kept.
+extern "C" int fc_autotune_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int32_t *vars)
+{
+    if (!c || (nq > 0 && (!var_off || !vars))) return fail(FC_ERR_ARG, "fc_autotune_batch: null argument");
+    if (c->transactions) return FC_OK;
+    int rc = fc_autotune(c, 0);
+    if (rc != FC_OK) return rc;
+    DevGuard g(c->device);
+    const Options base = c->opt;
+    const double scales[] = {0.25, 0.5, 1.0, 2.0, 4.0, -1.0};  // -1: bitmap never chosen
+    double best_t = 1e30;
+    Options best = base;
+    for (double sc : scales) {
+        c->opt = base;
+        c->opt.bitmap_cost = sc < 0 ? ((int64_t)1 << 50) : (int64_t)std::max(1.0, base.bitmap_cost * sc);
+        c->opt.bitmap_chunk_cost = sc < 0 ? ((int64_t)1 << 50) : (int64_t)(base.bitmap_chunk_cost * sc);
+        fc_plan *p = nullptr;
+        if ((rc = fc_plan_count(c, nq, var_off, vars, nullptr, &p)) != FC_OK) {
+            c->opt = base;
+            return rc;
+        }
+        DBuf out;
+        if (out.ensure(sizeof(int32_t) * std::max<int64_t>(p->out_cells, 1)) != cudaSuccess) {
+            fc_plan_free(p);
+            c->opt = base;
+            return fail(FC_ERR_OOM, "autotune buffer");
+        }
+        const double t = time_plan(p, out.p, 3);
+        out.release();
+        fc_plan_free(p);
+        if (t < best_t) {
+            best_t = t;
+            best = c->opt;
+        }
+    }
+    c->opt = best;
+    return FC_OK;
+}
