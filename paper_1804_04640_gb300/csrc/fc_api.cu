@@ -1285,12 +1285,12 @@ extern "C" int fc_plan_pairs(fc_ctx *c, fc_plan **out)
     const int64_t chunk_words = std::max<int64_t>(2, c->opt.pair_chunk_rows / 64 / 2 * 2);
     // row splits: enough CTAs to fill the GPU and at most chunk_words per split
     const int32_t tiles = pairs_tile_count(R_pad);
-    // one CTA per SM: pick the split count that fills whole waves, at least
-    // two waves and at least the splits the chunk bound asks for
+    // one CTA per SM: pick the split count that fills whole waves and gives
+    // at least the splits the chunk bound asks for
     const int64_t need = std::max<int64_t>(1, (c->words + chunk_words - 1) / chunk_words);
     const int64_t max_split = std::max<int64_t>(1, (c->words + 1) / 2);
     int64_t ksplit = need;
-    for (int64_t waves = 2; waves < 64; ++waves) {
+    for (int64_t waves = 1; waves < 64; ++waves) {
         const int64_t s = waves * c->num_sms / tiles;
         if (s >= need && s * tiles >= waves * c->num_sms - tiles / 2) {
             ksplit = s;

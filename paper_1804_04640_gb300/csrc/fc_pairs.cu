@@ -11,19 +11,20 @@
 //   * operands are built on the fly from the bitmaps: each bit becomes one
 //     e4m3 byte, 0x08 (= 2^-6, the smallest normal) or 0, written K-major into
 //     shared memory with the 128-byte swizzle the MMA descriptors describe;
-//   * tcgen05.mma.cta_group::1.kind::f8f6f4 (M = 128, N = 256, K = 32) issued
-//     by one thread accumulates in FP32 in tensor memory.  Every product is 0
-//     or 2^-12 and every partial sum is 2^-12 times an integer no larger than
-//     the rows of one split, which the planner keeps far below 2^24, so the
-//     FP32 sums are exact; the result is read with tcgen05.ld, scaled by 2^12,
-//     converted to int32 and added to C (split-K over the rows);
-//   * only tiles that touch the upper triangle of C are computed; on tiles
-//     whose 128 A rows lie inside their 256 B rows, A is read from the B
-//     buffer instead of being built twice.
+//   * a CTA owns a 256 x 256 region of C and one range of rows (split K):
+//     two tcgen05.mma.cta_group::1.kind::f8f6f4 accumulators (M = 128,
+//     N = 256, K = 32, FP32 in tensor memory, 512 columns) share one B
+//     operand of 256 rows; on diagonal regions both A halves are slices of B,
+//     so only B is built.  Every product is 0 or 2^-12 and every partial sum
+//     is 2^-12 times an integer no larger than the rows of one split, which
+//     the planner keeps far below 2^24, so the FP32 sums are exact; the
+//     result is read with tcgen05.ld, scaled by 2^12, converted to int32 and
+//     added to C;
+//   * only regions on or above the diagonal of C are computed.
 //
 // Pipeline per CTA: 16 producer warps fill kStages shared-memory stages
-// (loading the bitmap words three stages ahead of the one they expand)
-// and signal a "full" mbarrier; the MMA thread waits for it, issues four MMAs and
+// (loading the bitmap words three stages ahead of the one they expand) and
+// signal a "full" mbarrier; the MMA thread waits for it, issues eight MMAs and
 // commits to the stage's "empty" mbarrier.  Every wait is bounded by
 // `wait_limit` polls; a wait that runs out sets the status word and the CTA
 // winds down (no trap, TMEM always released).
@@ -33,18 +34,19 @@
 namespace fc {
 namespace {
 
-constexpr int kM = 128;
-constexpr int kN = 256;
+constexpr int kM = 128;                      // rows of one MMA
+constexpr int kN = 256;                      // columns of one MMA
+constexpr int kRegion = 256;                 // a CTA's region of C is kRegion x kRegion
 constexpr int kKStage = 128;                 // instances per stage = bytes per operand row
-constexpr int kStages = 4;
+constexpr int kStages = 3;
 constexpr int kProducerWarps = 16;
 constexpr int kProducers = kProducerWarps * 32;
 constexpr int kThreads = kProducers + 32;    // + the MMA / TMEM warp
-constexpr int kABytes = kM * kKStage;        // 16 KiB
+constexpr int kABytes = kRegion * kKStage;   // two A halves of 128 rows, 32 KiB
 constexpr int kBBytes = kN * kKStage;        // 32 KiB
 constexpr int kStageBytes = kABytes + kBBytes;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
-constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kTmemCols = 512;          // two 128 x 256 FP32 accumulators
 
 // Instruction descriptor of kind::f8f6f4: D = F32 (bits 4-5 = 1), A = B = E4M3
 // (format 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
@@ -135,20 +137,20 @@ __device__ __forceinline__ void store_row_word(uint8_t *tile, int row, int half,
     }
 }
 
-__device__ __forceinline__ void tile_of(int idx, int R_pad, int &ta, int &tb)
+// Region idx in the order (ra, rb), ra <= rb, rb-major.
+__device__ __forceinline__ void region_of(int idx, int R_pad, int &ra, int &rb)
 {
-    const int nta = R_pad / kM, ntb = R_pad / kN;
-    for (int b = 0; b < ntb; ++b)
-        for (int a = 0; a < nta; ++a)
-            if (a * kM <= b * kN + kN - 1) {
-                if (idx == 0) {
-                    ta = a;
-                    tb = b;
-                    return;
-                }
-                --idx;
+    const int nb = R_pad / kRegion;
+    for (int b = 0; b < nb; ++b)
+        for (int a = 0; a <= b; ++a) {
+            if (idx == 0) {
+                ra = a;
+                rb = b;
+                return;
             }
-    ta = tb = 0;
+            --idx;
+        }
+    ra = rb = 0;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsParams P)
@@ -159,9 +161,10 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x / P.ksplit, split = blockIdx.x % P.ksplit;
-    int ta, tb;
-    tile_of(tile, P.R_pad, ta, tb);
+    const int region = blockIdx.x / P.ksplit, split = blockIdx.x % P.ksplit;
+    int ra, rb;
+    region_of(region, P.R_pad, ra, rb);
+    const bool diag = ra == rb;  // both A halves are slices of B
     const int64_t total_stages = (P.words + 1) / 2;
     const int64_t st0 = total_stages * split / P.ksplit;
     const int64_t st1 = total_stages * (split + 1) / P.ksplit;
@@ -188,13 +191,13 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    // A tile inside the B tile's rows: A is a 16 KiB-aligned slice of B.
-    const int a_in_b = (ta * kM >= tb * kN && ta * kM + kM <= tb * kN + kN) ? ta * kM - tb * kN : -1;
     if (warp < kProducerWarps) {
         // ---------------------------------------------------------- producers
-        constexpr int kTasksMax = ((kM + kN) * 2 + kProducers - 1) / kProducers;
-        const int first = a_in_b >= 0 ? kM * 2 : 0;  // skip the A rows when A comes from B
-        const int ntask = (kM + kN) * 2 - first;
+        // tasks: (operand row, half of the stage's two 64-bit words); rows
+        // 0..255 are the A halves, 256..511 are B
+        constexpr int kTasksMax = ((kRegion + kN) * 2 + kProducers - 1) / kProducers;
+        const int first = diag ? kRegion * 2 : 0;  // skip the A rows when A comes from B
+        const int ntask = (kRegion + kN) * 2 - first;
         // words of stages st + 1, st + 2, st + 3 in flight while stage st is expanded
         uint64_t p1[kTasksMax], p2[kTasksMax], p3[kTasksMax];
         auto load = [&](int64_t st, uint64_t (&dst)[kTasksMax]) {
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
             for (int j = 0; j < kTasksMax; ++j) {
                 const int u = first + threadIdx.x + j * kProducers;
                 const int i = u >> 1, half = u & 1;
-                const int grow = i < kM ? ta * kM + i : tb * kN + (i - kM);
+                const int grow = i < kRegion ? ra * kRegion + i : rb * kRegion + (i - kRegion);
                 dst[j] = (st < nst && u < first + ntask && grow < P.R)
                              ? __ldg(P.bits + (int64_t)grow * P.wstride + kw + half)
                              : 0ull;
@@ -236,10 +239,10 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
                 const int u = first + threadIdx.x + j * kProducers;
                 if (u < first + ntask) {
                     const int i = u >> 1, half = u & 1;
-                    if (i < kM)
+                    if (i < kRegion)
                         store_row_word(a_tile, i, half, cur[j]);
                     else
-                        store_row_word(b_tile, i - kM, half, cur[j]);
+                        store_row_word(b_tile, i - kRegion, half, cur[j]);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -256,11 +259,14 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
             }
             tc_fence_after();
             const uint32_t b_addr = smem_u32(smem + slot * kStageBytes) + kABytes;
-            const uint32_t a_addr = a_in_b >= 0 ? b_addr + (uint32_t)a_in_b * kKStage : b_addr - kABytes;
+            const uint32_t a_addr = diag ? b_addr : b_addr - kABytes;
 #pragma unroll
-            for (int kk = 0; kk < kKStage / 32; ++kk)
-                mma_f8(tmem, smem_desc(a_addr + 32 * kk), smem_desc(b_addr + 32 * kk),
-                       (st > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < kKStage / 32; ++kk) {
+                const uint64_t bd = smem_desc(b_addr + 32 * kk);
+                const uint32_t acc = (st > 0 || kk > 0) ? 1u : 0u;
+                mma_f8(tmem, smem_desc(a_addr + 32 * kk), bd, acc);                          // rows 0..127
+                mma_f8(tmem + kN, smem_desc(a_addr + kM * kKStage + 32 * kk), bd, acc);     // rows 128..255
+            }
             mma_commit(empty0 + 8 * slot);
         }
         mma_commit(accb);  // fires when every MMA issued above has completed
@@ -273,12 +279,14 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
         tc_fence_after();
         // warp-uniform decision: tcgen05.ld below is a warp-wide instruction
         if (__all_sync(kFull, done && !*(volatile int *)&s_abort)) {
-            const int row = ta * kM + warp * 32 + lane;
-            int32_t *crow = P.C + (int64_t)row * P.R_pad + tb * kN;
+#pragma unroll 1
+          for (int half = 0; half < 2; ++half) {
+            const int row = ra * kRegion + half * kM + warp * 32 + lane;
+            int32_t *crow = P.C + (int64_t)row * P.R_pad + rb * kRegion;
 #pragma unroll 1
             for (int c0 = 0; c0 < kN; c0 += 32) {
                 uint32_t r[32];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(half * kN + c0);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -293,11 +301,13 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
                 if (row < P.R) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
+                        const int col = rb * kRegion + c0 + j;  // the lower triangle is never read
                         const int v = __float2int_rn(__uint_as_float(r[j]) * kOneHotScale);
-                        if (v) atomicAdd(crow + c0 + j, v);
+                        if (v && col < P.R && row <= col) atomicAdd(crow + c0 + j, v);
                     }
                 }
             }
+          }
         }
         tc_fence_before();
     }
@@ -364,16 +374,13 @@ __global__ void wait_selftest_kernel(int32_t *status, int64_t limit)
 
 int pairs_tile_count(int32_t R_pad)
 {
-    int count = 0;
-    for (int b = 0; b < R_pad / kN; ++b)
-        for (int a = 0; a < R_pad / kM; ++a)
-            if (a * kM <= b * kN + kN - 1) ++count;
-    return count;
+    const int nb = R_pad / kRegion;
+    return nb * (nb + 1) / 2;
 }
 
 cudaError_t launch_pairs_gemm(const PairsParams &p, cudaStream_t s)
 {
-    if (p.R_pad % kN != 0) return cudaErrorInvalidValue;
+    if (p.R_pad % kRegion != 0) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(pairs_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     const int grid = pairs_tile_count(p.R_pad) * p.ksplit;

@@ -200,3 +200,14 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     orc = oracle.DB(db.D, db.arities)
     assert np.array_equal(fc.fc_count(ctx, [0, 1]).astype(np.int64), orc.table([0, 1]))
     fc.fc_sync(ctx)                                            # status was cleared
+
+
+def test_batch_autotuner_keeps_counts_exact():
+    db = random_dag_database(20, 60_001, 2, 5, 3, 0.5, seed=61)
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    queries = random_queries(db.n, 1500, 1, 6, seed=62)
+    off, flat = fc.pack_lists(queries)
+    fc.fc_autotune_batch(ctx, off, flat)
+    assert fc.fc_get_option(ctx, "bitmap_cost") > 0
+    check_batch(ctx, orc, queries)
