@@ -389,6 +389,69 @@ __device__ __forceinline__ void key_rows_swar_bytes(const CountParams &P, const 
     }
 }
 
+// key_rows_swar_bytes with the number of variables fixed at compile time:
+// column pointers and scaled strides live in registers for the whole item and
+// the loop over variables is unrolled.
+template <int K>
+__device__ __forceinline__ void key_rows_swar_bytes_k(const CountParams &P, const QVar *vs, int64_t r0,
+                                                      int64_t r1, int lshift, int32_t *tab0)
+{
+    char *smem = reinterpret_cast<char *>(tab0);
+    const uint32_t base_bytes = (uint32_t)((threadIdx.x & ((1 << lshift) - 1)) << 2);
+    const int sshift = 2 + lshift;
+    const uint32_t init = base_bytes | (base_bytes << 16);
+    const uint4 *col[K];
+    uint32_t st[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        col[t] = reinterpret_cast<const uint4 *>(P.D + (int64_t)vs[t].var * P.m_pad + r0);
+        st[t] = (uint32_t)vs[t].stride << sshift;
+    }
+    const int64_t nfull = (r1 - r0) >> 10;
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = threadIdx.x; u < (nfull << 5); u += blockDim.x) {
+        const int64_t vec = ((u >> 5) << 6) + lane;
+        uint32_t acc[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] = init;
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            const uint4 x0 = __ldg(col[t] + vec), x1 = __ldg(col[t] + vec + 32);
+            const uint32_t w[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                acc[2 * i] += __byte_perm(w[i], 0u, 0x4240) * st[t];
+                acc[2 * i + 1] += __byte_perm(w[i], 0u, 0x4341) * st[t];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            atomicAdd(reinterpret_cast<int *>(smem + (acc[j] & 0xFFFFu)), 1);
+            atomicAdd(reinterpret_cast<int *>(smem + (acc[j] >> 16)), 1);
+        }
+    }
+    for (int64_t p = r0 + (nfull << 10) + threadIdx.x; p < r1; p += blockDim.x) {
+        uint32_t key = base_bytes;
+#pragma unroll
+        for (int t = 0; t < K; ++t) key += (uint32_t)P.D[(int64_t)vs[t].var * P.m_pad + p] * st[t];
+        atomicAdd(reinterpret_cast<int *>(smem + key), 1);
+    }
+}
+
+__device__ __forceinline__ void key_rows_swar_dispatch(const CountParams &P, const QVar *vs, int k, int64_t r0,
+                                                       int64_t r1, int lshift, int32_t *tab0)
+{
+    switch (k) {
+    case 1: key_rows_swar_bytes_k<1>(P, vs, r0, r1, lshift, tab0); break;
+    case 2: key_rows_swar_bytes_k<2>(P, vs, r0, r1, lshift, tab0); break;
+    case 3: key_rows_swar_bytes_k<3>(P, vs, r0, r1, lshift, tab0); break;
+    case 4: key_rows_swar_bytes_k<4>(P, vs, r0, r1, lshift, tab0); break;
+    case 5: key_rows_swar_bytes_k<5>(P, vs, r0, r1, lshift, tab0); break;
+    case 6: key_rows_swar_bytes_k<6>(P, vs, r0, r1, lshift, tab0); break;
+    default: key_rows_swar_bytes(P, vs, k, r0, r1, lshift, tab0); break;
+    }
+}
+
 // Scalar keys (any table size up to 2^31 cells), counted in global memory.
 __device__ __forceinline__ void key_rows_global(const CountParams &P, const QVar *vs, int k,
                                                 int64_t r0, int64_t r1, int32_t *tab)
@@ -473,7 +536,7 @@ __global__ void __launch_bounds__(512, 2) count_kernel(const CountParams P)
             for (int s = threadIdx.x; s < v.arity; s += blockDim.x)
                 smem_tab[s * v.stride] = (int32_t)P.marg[v.soff + s];
         } else if (lshift >= 0) {
-            key_rows_swar_bytes(P, s_vars, k, r0, r1, lshift, smem_tab);
+            key_rows_swar_dispatch(P, s_vars, k, r0, r1, lshift, smem_tab);
         } else if (in_smem) {
             key_rows_swar(P, s_vars, k, r0, r1, smem_tab + (warp % copies) * h.cells);
         } else {
