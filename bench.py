@@ -140,6 +140,15 @@ def make_workload(name: str, m: int | None = None, nq: int | None = None):
         queries = subset_queries(db.n, (1, 2, 3)) if name == "tiny" else \
             random_queries(db.n, c["nq"], c["k"][0], c["k"][1], c["seed"])
         return {"db": db, "queries": queries}
+    if name == "assign":
+        db = config_database("random", c["m"])
+        rng = np.random.default_rng(c["seed"])
+        qs = []
+        for _ in range(c["nq"]):
+            k = int(rng.integers(c["k"][0], c["k"][1] + 1))
+            vs = [int(x) for x in rng.choice(db.n, size=k, replace=False)]
+            qs.append((vs, [int(rng.integers(0, db.arities[v])) for v in vs]))
+        return {"db": db, "assign": qs}
     if name == "scores":
         db = config_database(name, c["m"])
         child, parents = score_queries(db.n, c["nq"], c["pa"][0], c["pa"][1], c["seed"])
@@ -161,6 +170,10 @@ def describe(name: str, w) -> dict:
         return {"workload": f"{name}: n={w['db'].n} arity {c['arity'][0]}-{c['arity'][1]}, m={w['db'].m}, "
                             f"{len(ks)} count queries of {min(ks)}-{max(ks)} variables",
                 "n": w["db"].n, "m": w["db"].m, "queries": len(ks)}
+    if name == "assign":
+        return {"workload": f"assign: n={w['db'].n}, m={w['db'].m}, {len(w['assign'])} specific assignments of "
+                            f"{c['k'][0]}-{c['k'][1]} conditions", "n": w["db"].n, "m": w["db"].m,
+                "queries": len(w["assign"])}
     if name == "scores":
         return {"workload": f"scores: n={w['db'].n}, m={w['db'].m}, {len(w['child'])} (child, parents) "
                             f"queries, |parents| {c['pa'][0]}-{c['pa'][1]}, MDL and BDeu(ess=1)",
@@ -202,6 +215,17 @@ def oracle_rate(name: str, w, seconds: float, cores: int):
                 units += len(chunk)
                 i += len(chunk)
             sample = f"{units} queries of the workload (in order, wrapping), {cores} threads"
+        elif name == "assign":
+            orc = oracle.DB(w["db"].D, w["db"].arities)
+            jobs = w["assign"]
+            t0 = time.perf_counter()
+            i = 0
+            while time.perf_counter() - t0 < seconds:
+                chunk = jobs[i % len(jobs): i % len(jobs) + 4 * cores] or jobs[: 4 * cores]
+                list(ex.map(lambda q: orc.count_assignment(*q), chunk))
+                units += len(chunk)
+                i += len(chunk)
+            sample = f"{units} assignments of the workload by row scan, {cores} threads"
         elif name == "pairs":
             orc = oracle.DB(w["db"].D, w["db"].arities)
             n = w["db"].n
@@ -236,7 +260,7 @@ def oracle_rate(name: str, w, seconds: float, cores: int):
 
 METRIC = "count queries/s (exact full contingency tables, batched persistent launch)"
 UNITS = {"tiny": "queries/s", "random": "queries/s", "large": "queries/s", "scores": "queries/s",
-         "pairs": "pairs/s", "support": "itemsets/s"}
+         "pairs": "pairs/s", "support": "itemsets/s", "assign": "assignments/s"}
 
 
 def run_reference(args, rank: int, world: int):
@@ -337,6 +361,22 @@ def run_gpu(args, rank: int, world: int):
         def e2e_call():
             fc.fc_score_batch(ctx, w["child"], po, pa, "bdeu", 1.0, out=pinned)
         strategies = np.bincount(fc.fc_plan_strategies(plan), minlength=5).tolist()
+    elif name == "assign":
+        db = w["db"]
+        ctx = fc.fc_load(db.D, db.arities)
+        vo, vv = fc.pack_lists([q[0] for q in w["assign"]])
+        _, ss = fc.pack_lists([q[1] for q in w["assign"]])
+        plan = fc.fc_plan_assignments(ctx, vo, vv, ss)
+        units = len(w["assign"])
+        outs = (torch.empty(units, dtype=torch.int32, device="cuda"),)
+        alg_bytes = int(len(vv)) * ((db.m + 7) // 8)  # one state bitmap per condition
+        pinned = torch.empty(units, dtype=torch.int64).pin_memory()
+        h2d = fc.fc_plan_size(plan, 5) + 4 * (len(vo) + 2 * len(vv))
+        d2h = 4 * units
+
+        def e2e_call():
+            fc.fc_count_assignment_batch(ctx, vo, vv, ss, out=pinned)
+        strategies = None
     elif name == "pairs":
         db = w["db"]
         ctx = fc.fc_load(db.D, db.arities)

@@ -136,6 +136,16 @@ int fc_count(fc_ctx *ctx, const int32_t *vars, int32_t k, int32_t *table);
 int fc_count_assignment(fc_ctx *ctx, const int32_t *vars, const int32_t *states, int32_t k,
                         int64_t *count);
 
+/* Counts of nq specific assignments in one launch (Sec. 2, Count of one
+ * assignment; the single root-to-leaf path of the bitmap DFS, end of
+ * Sec. 3.3: the AND of one state bitmap per condition, then a bit count).
+ * Assignment q is the conditions (vars[t] = states[t]) for t in
+ * var_off[q] .. var_off[q+1) (var_off[0] = 0).  counts: nq int64 (host).  A
+ * state outside its arity makes the count 0; no conditions give m; a variable
+ * listed twice with two states gives 0. */
+int fc_count_assignment_batch(fc_ctx *ctx, int32_t nq, const int32_t *var_off, const int32_t *vars,
+                              const int32_t *states, int64_t *counts);
+
 /* Batch of nq tables in one launch.  Query q has variables
  * vars[var_off[q] .. var_off[q+1]) and its table starts at cell table_off[q]
  * of `tables`; table_off is non-decreasing with
@@ -196,6 +206,11 @@ int fc_plan_score(fc_ctx *ctx, int32_t nq, const int32_t *child, const int32_t *
 int fc_plan_support(fc_ctx *ctx, int32_t nq, const int32_t *set_off, const int32_t *items,
                     fc_plan **out);
 
+/* Plan of an assignment-count batch (arguments as fc_count_assignment_batch);
+ * fc_plan_run writes nq int32 counts to out0. */
+int fc_plan_assignments(fc_ctx *ctx, int32_t nq, const int32_t *var_off, const int32_t *vars,
+                        const int32_t *states, fc_plan **out);
+
 /* Plan of the all-pairs computation (fc_pairs_all). */
 int fc_plan_pairs(fc_ctx *ctx, fc_plan **out);
 
@@ -217,7 +232,8 @@ int fc_plan_strategies(const fc_plan *plan, int32_t *strategy);
  *   score plan:   out0 = scores (float);
  *   pairs plan:   out0 = pair tables (int32, may be NULL), out1 = MI (float, may be NULL);
  *   support plan: out0 = support, out1 = sub_support (may be NULL),
- *                 out2 = confidence (float, may be NULL).
+ *                 out2 = confidence (float, may be NULL);
+ *   assignment plan: out0 = counts (int32).
  * The first run with a given (outputs, stream) captures a CUDA graph; later
  * runs replay it.  Runs of one plan must not overlap in time.  Device-side
  * errors (FC_ERR_TIMEOUT) are reported by fc_sync(). */

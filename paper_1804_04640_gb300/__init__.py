@@ -31,6 +31,7 @@ EXPORTS = (
     "fc_plan_size", "fc_plan_table_offsets", "fc_plan_strategies", "fc_plan_run", "fc_plan_free",
     "fc_sync", "fc_set_option", "fc_get_option", "fc_autotune", "fc_last_error",
     "fc_selftest_wait_timeout", "fc_count_sorted_noalloc", "fc_autotune_batch",
+    "fc_count_assignment_batch", "fc_plan_assignments",
 )
 
 
@@ -93,6 +94,8 @@ def load_library(build_if_missing: bool = False):
         "fc_get_option": (ctypes.c_int64, [_vp, ctypes.c_char_p]),
         "fc_autotune": (ctypes.c_int, [_vp, ctypes.c_int32]),
         "fc_autotune_batch": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p]),
+        "fc_count_assignment_batch": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p, _i32p, _i64p]),
+        "fc_plan_assignments": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p, _i32p, ctypes.POINTER(_vp)]),
         "fc_last_error": (ctypes.c_char_p, []),
         "fc_selftest_wait_timeout": (ctypes.c_int, [_vp, ctypes.c_int64]),
         "fc_count_sorted_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _i32p,
@@ -233,6 +236,27 @@ def fc_count_assignment(ctx: Handle, vars_, states) -> int:
     out = ctypes.c_int64(0)
     _check(lib.fc_count_assignment(ctx.ptr, _ptr(v, _i32p), _ptr(s, _i32p), len(v), ctypes.byref(out)))
     return int(out.value)
+
+
+def fc_count_assignment_batch(ctx: Handle, var_off, vars_, states, out=None):
+    """int64 count of each assignment (vars[t] = states[t] over each query's span)."""
+    lib = load_library()
+    vo, vv, st = _host(var_off, np.int32), _host(vars_, np.int32), _host(states, np.int32)
+    nq = len(vo) - 1
+    if out is None:
+        out = np.zeros(max(nq, 1), dtype=np.int64)
+    _check(lib.fc_count_assignment_batch(ctx.ptr, nq, _ptr(vo, _i32p), _ptr(vv, _i32p), _ptr(st, _i32p),
+                                         _ptr(out, _i64p)))
+    return out[:nq] if len(out) > nq else out
+
+
+def fc_plan_assignments(ctx: Handle, var_off, vars_, states) -> Handle:
+    lib = load_library()
+    vo, vv, st = _host(var_off, np.int32), _host(vars_, np.int32), _host(states, np.int32)
+    out = _vp()
+    _check(lib.fc_plan_assignments(ctx.ptr, len(vo) - 1, _ptr(vo, _i32p), _ptr(vv, _i32p), _ptr(st, _i32p),
+                                   ctypes.byref(out)))
+    return Handle(out, lib.fc_plan_free, ctx)
 
 
 def fc_count_batch(ctx: Handle, var_off, vars_, table_off=None, out=None):

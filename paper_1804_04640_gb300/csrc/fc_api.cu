@@ -345,7 +345,8 @@ extern "C" int fc_load(fc_ctx **out, const uint8_t *D, int32_t n, int64_t m,
     if ((e = cudaMalloc(&c->d_soff, sizeof(int32_t) * n)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
     cudaMemcpyAsync(c->d_arity, c->arity.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(c->d_soff, c->soff.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream);
-    const size_t bits_bytes = sizeof(uint64_t) * (size_t)c->R * c->wstride;
+    // one row per (variable, state) plus an all-zero row R (states outside an arity)
+    const size_t bits_bytes = sizeof(uint64_t) * (size_t)(c->R + 1) * c->wstride;
     if ((e = cudaMalloc(&c->d_bits, bits_bytes)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc bitmaps"));
     if ((e = cudaMemsetAsync(c->d_bits, 0, bits_bytes, c->stream)) != cudaSuccess) return bail(cuda_fail(e, "memset bitmaps"));
     int32_t *bad = c->d_status + 1;
@@ -1099,7 +1100,8 @@ cudaError_t enqueue_support(fc_plan *p, int32_t *support, int32_t *sub, float *c
     SupportParams P = p->sp;
     P.support = support;
     P.sub_support = sub ? sub : (int32_t *)p->scratch_tables.p;
-    P.confidence = conf;
+    P.confidence = P.full_only ? nullptr : conf;
+    if (P.full_only) conf = nullptr;
     P.next_item = (int32_t *)p->counters.p;
     cudaError_t e = cudaMemsetAsync(p->counters.p, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
@@ -1115,6 +1117,11 @@ cudaError_t enqueue_support(fc_plan *p, int32_t *support, int32_t *sub, float *c
     return e;
 }
 
+}  // namespace
+
+namespace {
+int build_set_plan(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *items, int full_only,
+                   fc_plan **out);
 }  // namespace
 
 extern "C" int fc_plan_support(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *items,
@@ -1142,13 +1149,24 @@ extern "C" int fc_plan_support(fc_ctx *c, int32_t nq, const int32_t *set_off, co
             c->mark[it] = c->epoch;
         }
     }
+    return build_set_plan(c, nq, set_off, items, 0, out);
+}
+
+namespace {
+
+// A plan over sets of bitmap rows: itemset supports with their leave-one-out
+// supports (full_only = 0), or the support of each set alone (full_only = 1,
+// specific-assignment counts).  set_off[0] == 0 and the rows are valid.
+int build_set_plan(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *items, int full_only,
+                   fc_plan **out)
+{
     fc_plan *p = new (std::nothrow) fc_plan();
     if (!p) return fail(FC_ERR_OOM, "host allocation failed");
     p->ctx = c;
     p->kind = kPlanSupport;
     p->nq = nq;
     const int64_t n_sub = nq > 0 ? set_off[nq] : 0;
-    p->n_sub = n_sub;
+    p->n_sub = full_only ? 0 : n_sub;
     const Options &o = c->opt;
     // itemsets in decreasing size so that the heavy ones start first
     std::vector<int32_t> order(nq);
@@ -1192,11 +1210,60 @@ extern "C" int fc_plan_support(fc_ctx *c, int32_t nq, const int32_t *set_off, co
     P.nparts = (int32_t)std::max<int64_t>(1, (c->words + part_words - 1) / part_words);
     P.words_per_part = (int32_t)round_up((c->words + P.nparts - 1) / P.nparts, 64);
     P.m_tail = c->m;
+    P.full_only = full_only;
+    if (full_only) p->sup_threads = std::min(p->sup_threads, 512);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, support_kernel_ptr(), p->sup_threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, support_kernel_ptr(full_only), p->sup_threads, 0);
     p->sup_grid = c->num_sms * std::max(1, per_sm);
     *out = p;
     return FC_OK;
+}
+
+}  // namespace
+
+extern "C" int fc_plan_assignments(fc_ctx *c, int32_t nq, const int32_t *var_off, const int32_t *vars,
+                                   const int32_t *states, fc_plan **out)
+{
+    if (!c || !out || (nq > 0 && !var_off)) return fail(FC_ERR_ARG, "fc_plan_assignments: null argument");
+    *out = nullptr;
+    if (c->transactions) return fail(FC_ERR_STATE, "assignment counts need a categorical context");
+    if (nq < 0) return fail(FC_ERR_ARG, "nq < 0");
+    DevGuard g(c->device);
+    if (nq > 0 && var_off[0] != 0) return fail(FC_ERR_ARG, "var_off[0] must be 0");
+    std::vector<int32_t> rows;
+    for (int32_t q = 0; q < nq; ++q) {
+        const int32_t a = var_off[q], b = var_off[q + 1];
+        if (b < a) return fail(FC_ERR_ARG, "var_off must be non-decreasing");
+        if (b - a > kMaxK) return fail(FC_ERR_SIZE, "assignment %d has %d conditions, at most %d supported", q, b - a, kMaxK);
+        if (b > a && (!vars || !states)) return fail(FC_ERR_ARG, "null vars or states");
+        for (int32_t t = a; t < b; ++t) {
+            const int32_t v = vars[t];
+            if (v < 0 || v >= c->n) return fail(FC_ERR_ARG, "variable %d out of range", v);
+            // a state outside the arity matches nothing: the all-zero row R
+            rows.push_back(states[t] >= 0 && states[t] < c->arity[v] ? c->soff[v] + states[t] : c->R);
+        }
+    }
+    return build_set_plan(c, nq, var_off, rows.data(), 1, out);
+}
+
+extern "C" int fc_count_assignment_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int32_t *vars,
+                                         const int32_t *states, int64_t *counts)
+{
+    if (!c || (nq > 0 && !counts)) return fail(FC_ERR_ARG, "fc_count_assignment_batch: null argument");
+    DevGuard g(c->device);
+    fc_plan *p = nullptr;
+    int rc;
+    {
+        BorrowScope b(c);
+        rc = fc_plan_assignments(c, nq, var_off, vars, states, &p);
+    }
+    if (rc != FC_OK) return rc;
+    std::vector<int32_t> tmp(std::max(nq, 1));
+    rc = run_to_host(p, tmp.data(), sizeof(int32_t) * nq, nullptr, 0, nullptr, 0);
+    fc_plan_free(p);
+    if (rc == FC_OK)
+        for (int32_t q = 0; q < nq; ++q) counts[q] = tmp[q];
+    return rc;
 }
 
 extern "C" int fc_support_batch(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *items,

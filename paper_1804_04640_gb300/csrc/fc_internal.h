@@ -135,13 +135,13 @@ struct SupportParams {
     int32_t words_per_part;  // word range of one work item
     int32_t nparts;
     int32_t sets_per_item;   // itemsets one CTA takes per work item
-    int32_t pad;
+    int32_t full_only;       // 1: only supp(S) (assignment counts), no leave-one-out sets
     int64_t m_tail;          // m: bits at positions >= m are not transactions
 };
 cudaError_t launch_support(const SupportParams &p, int grid, int threads, size_t smem,
                            cudaStream_t s);
 cudaError_t launch_support_confidence(const SupportParams &p, cudaStream_t s);
-const void *support_kernel_ptr();
+const void *support_kernel_ptr(int full_only);
 
 // All-pairs one-hot co-occurrence on tcgen05 tensor cores.
 struct PairsParams {

@@ -79,6 +79,56 @@ __device__ __forceinline__ void support_set(const SupportParams &P, const int32_
     }
 }
 
+// supp(S) alone: the AND of K rows and a popcount (specific-assignment
+// counts, where no rule confidences are wanted).  Rows are zero past m.
+template <int K>
+__device__ __forceinline__ void full_set(const SupportParams &P, const int32_t *items, int64_t w0, int64_t w1,
+                                         int lane, int32_t *supp, bool atomic)
+{
+    const uint64_t *row[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) row[t] = P.bits + (int64_t)items[t] * P.wstride;
+    unsigned full = 0u;
+#pragma unroll 1
+    for (int64_t w = w0 + 2 * lane; w < w1; w += 64) {
+        ulonglong2 x = __ldg(reinterpret_cast<const ulonglong2 *>(row[0] + w));
+#pragma unroll
+        for (int t = 1; t < K; ++t) {
+            const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2 *>(row[t] + w));
+            x.x &= a.x;
+            x.y &= a.y;
+        }
+        full += (unsigned)(__popcll(x.x) + __popcll(x.y));
+    }
+    full = __reduce_add_sync(kFullMask, full);
+    if (lane == 0) {
+        if (atomic) {
+            if (full) atomicAdd(supp, (int)full);
+        } else {
+            *supp = (int)full;
+        }
+    }
+}
+
+__device__ void full_set_any(const SupportParams &P, const int32_t *items, int k, int64_t w0, int64_t w1,
+                             int lane, int32_t *supp, bool atomic)
+{
+    unsigned full = 0u;
+    for (int64_t w = w0 + lane; w < w1; w += 32) {
+        uint64_t x = __ldg(P.bits + (int64_t)items[0] * P.wstride + w);
+        for (int t = 1; t < k; ++t) x &= __ldg(P.bits + (int64_t)items[t] * P.wstride + w);
+        full += (unsigned)__popcll(x);
+    }
+    full = __reduce_add_sync(kFullMask, full);
+    if (lane == 0) {
+        if (atomic) {
+            if (full) atomicAdd(supp, (int)full);
+        } else {
+            *supp = (int)full;
+        }
+    }
+}
+
 // Itemsets outside the unrolled sizes (0, 1 or more than 6 items): the k + 1
 // ANDs recomputed per word, the last word masked to the m transactions.
 __device__ void support_set_any(const SupportParams &P, const int32_t *items, int k, int64_t w0,
@@ -143,6 +193,50 @@ __global__ void __launch_bounds__(1024) support_kernel(const SupportParams P)
     }
 }
 
+// Counts of specific assignments (end of Sec. 3.3): the support-kernel loop
+// with supp(S) alone per set of bitmap rows.
+__global__ void __launch_bounds__(512, 2) assign_kernel(const SupportParams P)
+{
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t ngroups = ((int64_t)P.nq + P.sets_per_item - 1) / P.sets_per_item;
+    const int64_t n_work = ngroups * P.nparts;
+    const bool atomic = P.nparts > 1;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(P.next_item, 1);
+        __syncthreads();
+        const int64_t it = s_item;
+        __syncthreads();
+        if (it >= n_work) break;
+        const int64_t part = it / ngroups, group = it % ngroups;
+        const int64_t w0 = part * P.words_per_part;
+        const int64_t w1 = min(P.words, w0 + P.words_per_part);
+        const int64_t g0 = group * P.sets_per_item;
+        const int64_t g1 = min((int64_t)P.nq, g0 + P.sets_per_item);
+        for (int64_t i = g0 + warp; i < g1; i += nwarps) {
+            const int32_t q = P.order[i];
+            const int32_t a = P.set_off[q], k = P.set_off[q + 1] - a;
+            const int32_t *items = P.items + a;
+            int32_t *supp = P.support + q;
+            switch (k) {
+            case 0:  // the empty assignment matches every instance
+                if (lane == 0 && (!atomic || part == 0)) {
+                    if (atomic)
+                        atomicAdd(supp, (int)P.m_tail);
+                    else
+                        *supp = (int)P.m_tail;
+                }
+                break;
+            case 1: full_set<1>(P, items, w0, w1, lane, supp, atomic); break;
+            case 2: full_set<2>(P, items, w0, w1, lane, supp, atomic); break;
+            case 3: full_set<3>(P, items, w0, w1, lane, supp, atomic); break;
+            case 4: full_set<4>(P, items, w0, w1, lane, supp, atomic); break;
+            default: full_set_any(P, items, k, w0, w1, lane, supp, atomic); break;
+            }
+        }
+    }
+}
+
 // conf((S without item t) => item t) = supp(S) / supp(S without item t), 0 when
 // the denominator is 0 (then supp(S) is 0 as well).
 __global__ void confidence_kernel(const SupportParams P)
@@ -160,11 +254,17 @@ __global__ void confidence_kernel(const SupportParams P)
 
 }  // namespace
 
-const void *support_kernel_ptr() { return (const void *)support_kernel; }
+const void *support_kernel_ptr(int full_only)
+{
+    return full_only ? (const void *)assign_kernel : (const void *)support_kernel;
+}
 
 cudaError_t launch_support(const SupportParams &p, int grid, int threads, size_t smem, cudaStream_t s)
 {
-    support_kernel<<<grid, threads, smem, s>>>(p);
+    if (p.full_only)
+        assign_kernel<<<grid, threads > 512 ? 512 : threads, smem, s>>>(p);
+    else
+        support_kernel<<<grid, threads, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,124 @@
+"""Parity in the launch configuration bench.py times, at the full workload sizes.
+
+Each test builds its workload with bench.make_workload, plans it the way the
+benchmark does (batch autotuner, device-resident plan, CUDA-graph replay on a
+side stream, twice) and compares with the oracle: every table of the
+10,000-query batch, and seeded samples (plus properties that hold at any size)
+for the larger workloads.
+"""
+import concurrent.futures as cf
+import os
+
+import numpy as np
+import pytest
+
+import bench
+import oracle
+import paper_1804_04640_gb300 as fc
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    fc.load_library(build_if_missing=True)
+
+
+def _pool_map(fn, xs):
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        return list(ex.map(fn, xs))
+
+
+def _replay(plan, outs, torch):
+    s = torch.cuda.Stream()
+    results = []
+    for _ in range(2):
+        for o in outs:
+            o.fill_(-1) if o.dtype != torch.float32 else o.fill_(float("nan"))
+        s.wait_stream(torch.cuda.current_stream())
+        fc.fc_plan_run(plan, *outs, stream=s)
+        s.synchronize()
+        results.append([o.cpu().numpy().copy() for o in outs])
+    for a, b in zip(results[0], results[1]):
+        assert np.array_equal(a, b, equal_nan=True)
+    return results[1]
+
+
+def test_random_batch_as_benchmarked():
+    torch = pytest.importorskip("torch")
+    w = bench.make_workload("random")
+    db, queries = w["db"], w["queries"]
+    ctx = fc.fc_load(db.D, db.arities)
+    off, flat = fc.pack_lists(queries)
+    fc.fc_autotune_batch(ctx, off, flat)
+    plan = fc.fc_plan_count(ctx, off, flat)
+    toff = fc.fc_plan_table_offsets(plan)
+    (tables,) = _replay(plan, [torch.empty(int(toff[-1]), dtype=torch.int32, device="cuda")], torch)
+    orc = oracle.DB(db.D, db.arities)
+    want = _pool_map(orc.table, queries)
+    for q, t in enumerate(want):
+        assert np.array_equal(tables[toff[q]:toff[q + 1]].astype(np.int64), t), q
+
+
+def test_scores_batch_as_benchmarked():
+    torch = pytest.importorskip("torch")
+    w = bench.make_workload("scores")
+    db = w["db"]
+    ctx = fc.fc_load(db.D, db.arities)
+    fo, ff = fc.pack_lists([list(p) + [c] for p, c in zip(w["parents"], w["child"])])
+    fc.fc_autotune_batch(ctx, fo, ff)
+    po, pa = fc.pack_lists(w["parents"])
+    plan = fc.fc_plan_score(ctx, w["child"], po, pa, "bdeu", 1.0)
+    (scores,) = _replay(plan, [torch.empty(len(w["child"]), dtype=torch.float32, device="cuda")], torch)
+    orc = oracle.DB(db.D, db.arities)
+    idx = np.random.default_rng(17).choice(len(w["child"]), size=800, replace=False)
+    want = np.array(_pool_map(lambda q: orc.score(w["child"][q], w["parents"][q], "bdeu", 1.0), idx))
+    got = scores[idx].astype(np.float64)
+    assert np.all(np.abs(got - want) <= 1e-5 * np.abs(want) + 1e-12)
+
+
+def test_pairs_as_benchmarked():
+    torch = pytest.importorskip("torch")
+    w = bench.make_workload("pairs")
+    db = w["db"]
+    ctx = fc.fc_load(db.D, db.arities)
+    plan = fc.fc_plan_pairs(ctx)
+    outs = [torch.empty(fc.fc_plan_size(plan, 0), dtype=torch.int32, device="cuda"),
+            torch.empty(fc.fc_plan_size(plan, 1), dtype=torch.float32, device="cuda")]
+    tables, mi = _replay(plan, outs, torch)
+    orc = oracle.DB(db.D, db.arities)
+    pairs = [(a, b) for a in range(db.n) for b in range(a + 1, db.n)]
+    off = np.zeros(len(pairs) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([int(db.arities[a]) * int(db.arities[b]) for a, b in pairs])
+    sums = np.add.reduceat(tables.astype(np.int64), off[:-1])
+    assert np.all(sums == db.m)                                  # every pair table sums to m
+    idx = np.random.default_rng(5).choice(len(pairs), size=200, replace=False)
+
+    def one(p):
+        a, b = pairs[p]
+        t = orc.table([a, b])
+        return t, oracle.score_table(t, int(db.arities[a]), int(db.arities[b]), "mi")
+
+    for p, (t, m) in zip(idx, _pool_map(one, idx)):
+        assert np.array_equal(tables[off[p]:off[p + 1]].astype(np.int64), t)
+        assert abs(float(mi[p]) - m) <= 1e-5 * abs(m) + 1e-12
+
+
+def test_support_as_benchmarked():
+    torch = pytest.importorskip("torch")
+    w = bench.make_workload("support")
+    bits, m, sets = w["bits"], w["m"], w["sets"]
+    ctx = fc.fc_load_bits(bits, m)
+    so, it = fc.pack_lists(sets)
+    plan = fc.fc_plan_support(ctx, so, it)
+    outs = [torch.empty(len(sets), dtype=torch.int32, device="cuda"),
+            torch.empty(len(it), dtype=torch.int32, device="cuda"),
+            torch.empty(len(it), dtype=torch.float32, device="cuda")]
+    supp, sub, conf = _replay(plan, outs, torch)
+    owner = np.repeat(np.arange(len(sets)), np.diff(so))
+    assert np.all(supp[owner] <= sub)
+    idx = np.random.default_rng(9).choice(len(sets), size=32, replace=False)
+    for q, (s, sb, c) in zip(idx, _pool_map(lambda q: oracle.support_rules(bits, m, sets[q]), idx)):
+        a, b = so[q], so[q + 1]
+        assert supp[q] == s and np.array_equal(sub[a:b].astype(np.int64), sb)
+        assert np.allclose(conf[a:b], c, rtol=1e-6, atol=0)

@@ -211,3 +211,27 @@ def test_batch_autotuner_keeps_counts_exact():
     fc.fc_autotune_batch(ctx, off, flat)
     assert fc.fc_get_option(ctx, "bitmap_cost") > 0
     check_batch(ctx, orc, queries)
+
+
+@pytest.mark.parametrize("m", [1, 100, 70_001, 1_000_003])
+def test_assignment_batch(m):
+    """Batched specific assignments (end of Sec. 3.3) against the oracle's
+    row-by-row Count, with out-of-range states, repeated variables and empty
+    assignments."""
+    db = random_dag_database(12, m, 2, 5, 3, 0.5, seed=71)
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    rng = np.random.default_rng(m)
+    qs = []
+    for _ in range(3000):
+        k = int(rng.integers(0, 9))
+        vs = [int(x) for x in rng.choice(db.n, size=k, replace=False)]
+        st = [int(rng.integers(0, db.arities[v])) for v in vs]
+        qs.append((vs, st))
+    qs += [([3], [7]), ([2, 2], [0, 0]), ([2, 2], [0, 1]), ([], []), ([5, 1], [0, 200])]
+    vo, vv = fc.pack_lists([q[0] for q in qs])
+    _, ss = fc.pack_lists([q[1] for q in qs])
+    got = fc.fc_count_assignment_batch(ctx, vo, vv, ss)
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        want = list(ex.map(lambda q: orc.count_assignment(*q), qs))
+    assert got.tolist() == want

@@ -216,6 +216,8 @@ CONFIGS = {
                    nq=50_000, pa=(0, 4), ess=1.0),
     "support": dict(n_items=1000, m=10_000_000, zipf_s=1.1, mean_len=10.0, seed=5,
                     nq=1_000_000, k=(2, 5)),
+    # specific assignments over the batched-random database (end of Sec. 3.3)
+    "assign": dict(m=100_000, seed=7, nq=100_000, k=(1, 6)),
     # tables beyond shared memory (up to 16^5 cells): the global-atomic and
     # sort + run-length paths
     "large": dict(n=8, m=1_000_000, arity=(12, 16), max_indeg=2, alpha=0.3, seed=6,
