@@ -140,6 +140,9 @@ def make_workload(name: str, m: int | None = None, nq: int | None = None):
         queries = subset_queries(db.n, (1, 2, 3)) if name == "tiny" else \
             random_queries(db.n, c["nq"], c["k"][0], c["k"][1], c["seed"])
         return {"db": db, "queries": queries}
+    if name == "families":
+        db = config_database("scores", c["m"])
+        return {"db": db, "vars": list(range(c["nv"])), "max_parents": c["max_parents"]}
     if name == "assign":
         db = config_database("random", c["m"])
         rng = np.random.default_rng(c["seed"])
@@ -170,6 +173,11 @@ def describe(name: str, w) -> dict:
         return {"workload": f"{name}: n={w['db'].n} arity {c['arity'][0]}-{c['arity'][1]}, m={w['db'].m}, "
                             f"{len(ks)} count queries of {min(ks)}-{max(ks)} variables",
                 "n": w["db"].n, "m": w["db"].m, "queries": len(ks)}
+    if name == "families":
+        nf = len(w["vars"])
+        return {"workload": f"families: BN-score database (n={w['db'].n}, m={w['db'].m}), every child of the "
+                            f"first {nf} variables with every parent set of <= {w['max_parents']} of the others, BDeu",
+                "n": w["db"].n, "m": w["db"].m, "variables": nf, "max_parents": w["max_parents"]}
     if name == "assign":
         return {"workload": f"assign: n={w['db'].n}, m={w['db'].m}, {len(w['assign'])} specific assignments of "
                             f"{c['k'][0]}-{c['k'][1]} conditions", "n": w["db"].n, "m": w["db"].m,
@@ -215,6 +223,18 @@ def oracle_rate(name: str, w, seconds: float, cores: int):
                 units += len(chunk)
                 i += len(chunk)
             sample = f"{units} queries of the workload (in order, wrapping), {cores} threads"
+        elif name == "families":
+            import paper_1804_04640_gb300 as fcm
+            orc = oracle.DB(w["db"].D, w["db"].arities)
+            jobs = fcm.family_list(w["vars"], w["max_parents"])
+            t0 = time.perf_counter()
+            i = 0
+            while time.perf_counter() - t0 < seconds:
+                chunk = jobs[i % len(jobs): i % len(jobs) + 4 * cores] or jobs[: 4 * cores]
+                list(ex.map(lambda f: orc.score(f[0], f[1], "bdeu"), chunk))
+                units += len(chunk)
+                i += len(chunk)
+            sample = f"{units} families scored one by one from row scans, {cores} threads"
         elif name == "assign":
             orc = oracle.DB(w["db"].D, w["db"].arities)
             jobs = w["assign"]
@@ -260,7 +280,7 @@ def oracle_rate(name: str, w, seconds: float, cores: int):
 
 METRIC = "count queries/s (exact full contingency tables, batched persistent launch)"
 UNITS = {"tiny": "queries/s", "random": "queries/s", "large": "queries/s", "scores": "queries/s",
-         "pairs": "pairs/s", "support": "itemsets/s", "assign": "assignments/s"}
+         "pairs": "pairs/s", "support": "itemsets/s", "assign": "assignments/s", "families": "families/s"}
 
 
 def run_reference(args, rank: int, world: int):
@@ -361,6 +381,30 @@ def run_gpu(args, rank: int, world: int):
         def e2e_call():
             fc.fc_score_batch(ctx, w["child"], po, pa, "bdeu", 1.0, out=pinned)
         strategies = np.bincount(fc.fc_plan_strategies(plan), minlength=5).tolist()
+    elif name == "families":
+        db = w["db"]
+        ctx = fc.fc_load(db.D, db.arities)
+        fams = fc.family_list(w["vars"], w["max_parents"])
+        po, pa = fc.pack_lists([f[1] for f in fams])
+        if args.autotune:
+            fo, ff = fc.pack_lists([list(f[1]) + [f[0]] for f in fams])
+            fc.fc_autotune_batch(ctx, fo, ff)
+        plan = fc.fc_plan_families(ctx, w["vars"], w["max_parents"], "bdeu", 1.0)
+        units = fc.fc_plan_size(plan, 1)
+        outs = (torch.empty(units, dtype=torch.float32, device="cuda"),)
+        nv, dmax = len(w["vars"]), min(w["max_parents"], len(w["vars"]) - 1)
+        import math
+        alg_bytes = sum(math.comb(nv, sz) * sz for sz in range(1, dmax + 2)) * db.m
+        pinned = torch.empty(units, dtype=torch.float32).pin_memory()
+        h2d = fc.fc_plan_size(plan, 5)
+        d2h = 4 * units
+        # the same families with one table per family (no sharing of variable sets)
+        per_family_plan = fc.fc_plan_score(ctx, [f[0] for f in fams], po, pa, "bdeu", 1.0)
+        per_family_out = torch.empty(units, dtype=torch.float32, device="cuda")
+
+        def e2e_call():
+            fc.fc_score_families(ctx, w["vars"], w["max_parents"], "bdeu", 1.0, out=pinned)
+        strategies = None
     elif name == "assign":
         db = w["db"]
         ctx = fc.fc_load(db.D, db.arities)
@@ -410,6 +454,14 @@ def run_gpu(args, rank: int, world: int):
         def e2e_call():
             fc.fc_support_batch(ctx, so, it, out=pins)
         strategies = None
+
+    # bytes the step's kernels read from the database (columns or state bitmaps)
+    if name == "support":
+        resident_bytes = int(np.asarray(w["bits"]).nbytes)
+    elif name == "assign":
+        resident_bytes = int(w["db"].arities.sum()) * ((w["db"].m + 63) // 64) * 8
+    else:
+        resident_bytes = w["db"].n * w["db"].m
 
     def step():
         fc.fc_plan_run(plan, *outs, stream=stream)
@@ -461,6 +513,23 @@ def run_gpu(args, rank: int, world: int):
         pq = {"value": len(plans) / (pq_ms / 1e3), "unit": "queries/s", "queries": len(plans),
               "launches": len(plans)}
 
+    # ---- families: the same families with one counted table each
+    pf = None
+    if name == "families":
+        for _ in range(2):
+            fc.fc_plan_run(per_family_plan, per_family_out, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(3, min(args.steps, 10))
+        e0.record(stream)
+        for _ in range(reps):
+            fc.fc_plan_run(per_family_plan, per_family_out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pf_ms = e0.elapsed_time(e1) / reps
+        pf = {"value": units / (pf_ms / 1e3), "unit": "families/s", "ms_per_step": pf_ms,
+              "note": "one counted table per family (fc_plan_score)"}
+
     # ---- end to end through the host-buffer entry point
     for _ in range(2):
         e2e_call()
@@ -483,6 +552,11 @@ def run_gpu(args, rank: int, world: int):
         achieved = alg_bytes / (ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": measured_traffic(name), "peak_source": f"{peak_src} hbm_gbs"}
+        if resident_bytes < L2_BYTES:
+            roof["note"] = (f"effective bytes/s: the {resident_bytes / 2**20:.0f} MiB the kernels read stay in "
+                            "L2 after the first touch, so this is not an HBM fraction")
+    roof["duration"] = (f"whole step ({fc.fc_plan_size(plan, 6)} kernels per step); the dominant kernel's "
+                        "own share is in the committed launch list")
 
     line = None
     if rank == 0:
@@ -505,12 +579,14 @@ def run_gpu(args, rank: int, world: int):
             "data": "synthetic (seeded random-DAG samples)", "config": cfg,
             "e2e": {"value": units / e2e_s, "unit": UNITS[name], "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": args.steps * (2 if name == "pairs" else 1),
+            "gpu_launches": args.steps * fc.fc_plan_size(plan, 6),
             "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
         }
         if pq is not None:
             line["per_query"] = pq
             line["batched_over_per_query"] = value / world / pq["value"]
+        if pf is not None:
+            line["per_family_tables"] = pf
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

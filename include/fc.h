@@ -162,6 +162,22 @@ int fc_count_batch(fc_ctx *ctx, int32_t nq, const int32_t *var_off, const int32_
 int fc_score_batch(fc_ctx *ctx, int32_t nq, const int32_t *child, const int32_t *par_off,
                    const int32_t *parents, int32_t kind, double ess, float *scores);
 
+/* Scores of every family of the parent-set lattice over a variable list
+ * (Sec. 4.2: for each child X, every parent set Pa of at most max_parents of
+ * the other listed variables).  Each variable set V = Pa + {X} is counted
+ * once as a joint table and serves all |V| families that split it, so the
+ * counting work is that of the distinct variable sets.
+ *   vars    nv distinct variable ids; d = min(max_parents, nv - 1) <= 7.
+ *   scores  nv * F floats, F = sum_{s=0..d} C(nv-1, s).  The score of child
+ *           vars[c] with parents P is at c * F + (number of parent sets
+ *           smaller than |P|) + the lexicographic rank of P's positions among
+ *           the other nv - 1 variables (in list order).
+ * kind and ess as in fc_score_batch.  fc_families_count(nv, max_parents)
+ * returns nv * F (or -1 for bad arguments). */
+int64_t fc_families_count(int32_t nv, int32_t max_parents);
+int fc_score_families(fc_ctx *ctx, int32_t nv, const int32_t *vars, int32_t max_parents, int32_t kind,
+                      double ess, float *scores);
+
 /* All pairwise tables and their mutual information (the one-hot
  * co-occurrence product: for variables a < b the table over (a, b) is one
  * block of A^T A, A the m x sum(r) one-hot matrix of D; each table is the
@@ -211,13 +227,19 @@ int fc_plan_support(fc_ctx *ctx, int32_t nq, const int32_t *set_off, const int32
 int fc_plan_assignments(fc_ctx *ctx, int32_t nq, const int32_t *var_off, const int32_t *vars,
                         const int32_t *states, fc_plan **out);
 
+/* Plan of the family scores (arguments as fc_score_families); fc_plan_run
+ * writes the nv * F scores to out0 (float, device). */
+int fc_plan_families(fc_ctx *ctx, int32_t nv, const int32_t *vars, int32_t max_parents, int32_t kind,
+                     double ess, fc_plan **out);
+
 /* Plan of the all-pairs computation (fc_pairs_all). */
 int fc_plan_pairs(fc_ctx *ctx, fc_plan **out);
 
 /* Sizes of a plan's outputs: key 0 = int32 cells of the table output (count and
- * pairs plans), 1 = float scores / MI values, 2 = int32 supports, 3 = entries of
+ * pairs plans), 1 = float scores / MI values / family scores, 2 = int32 supports, 3 = entries of
  * sub_support / confidence, 4 = number of queries, 5 = bytes of descriptors the
- * plan copied to the device.  Returns -1 for a bad key. */
+ * plan copied to the device, 6 = kernels one fc_plan_run launches with every
+ * output given.  Returns -1 for a bad key. */
 int64_t fc_plan_size(const fc_plan *plan, int32_t key);
 
 /* Table offsets chosen by a count plan (nq + 1 int64, host buffer). */
@@ -233,7 +255,8 @@ int fc_plan_strategies(const fc_plan *plan, int32_t *strategy);
  *   pairs plan:   out0 = pair tables (int32, may be NULL), out1 = MI (float, may be NULL);
  *   support plan: out0 = support, out1 = sub_support (may be NULL),
  *                 out2 = confidence (float, may be NULL);
- *   assignment plan: out0 = counts (int32).
+ *   assignment plan: out0 = counts (int32);
+ *   families plan: out0 = scores (float).
  * The first run with a given (outputs, stream) captures a CUDA graph; later
  * runs replay it.  Runs of one plan must not overlap in time.  Device-side
  * errors (FC_ERR_TIMEOUT) are reported by fc_sync(). */

@@ -31,7 +31,8 @@ EXPORTS = (
     "fc_plan_size", "fc_plan_table_offsets", "fc_plan_strategies", "fc_plan_run", "fc_plan_free",
     "fc_sync", "fc_set_option", "fc_get_option", "fc_autotune", "fc_last_error",
     "fc_selftest_wait_timeout", "fc_count_sorted_noalloc", "fc_autotune_batch",
-    "fc_count_assignment_batch", "fc_plan_assignments",
+    "fc_count_assignment_batch", "fc_plan_assignments", "fc_families_count", "fc_score_families",
+    "fc_plan_families",
 )
 
 
@@ -94,6 +95,11 @@ def load_library(build_if_missing: bool = False):
         "fc_get_option": (ctypes.c_int64, [_vp, ctypes.c_char_p]),
         "fc_autotune": (ctypes.c_int, [_vp, ctypes.c_int32]),
         "fc_autotune_batch": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p]),
+        "fc_families_count": (ctypes.c_int64, [ctypes.c_int32, ctypes.c_int32]),
+        "fc_score_families": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_double, _vp]),
+        "fc_plan_families": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_double, ctypes.POINTER(_vp)]),
         "fc_count_assignment_batch": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p, _i32p, _i64p]),
         "fc_plan_assignments": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p, _i32p, ctypes.POINTER(_vp)]),
         "fc_last_error": (ctypes.c_char_p, []),
@@ -285,6 +291,47 @@ def fc_score_batch(ctx: Handle, child, par_off, parents, kind, ess: float = 1.0,
         out = np.zeros(max(len(ch), 1), dtype=np.float32)
     _check(lib.fc_score_batch(ctx.ptr, len(ch), _ptr(ch, _i32p), _ptr(po, _i32p), _ptr(pa, _i32p),
                               int(kind), float(ess), _ptr(out)))
+    return out
+
+
+def fc_families_count(nv: int, max_parents: int) -> int:
+    return int(load_library().fc_families_count(int(nv), int(max_parents)))
+
+
+def fc_score_families(ctx: Handle, vars_, max_parents: int, kind, ess: float = 1.0, out=None):
+    """Scores of every (child, parent set) family over vars (layout in include/fc.h)."""
+    lib = load_library()
+    v = _host(vars_, np.int32)
+    kind = SCORE_KINDS.get(kind, kind)
+    if out is None:
+        out = np.zeros(max(fc_families_count(len(v), max_parents), 1), dtype=np.float32)
+    _check(lib.fc_score_families(ctx.ptr, len(v), _ptr(v, _i32p), int(max_parents), int(kind), float(ess),
+                                 _ptr(out)))
+    return out
+
+
+def fc_plan_families(ctx: Handle, vars_, max_parents: int, kind, ess: float = 1.0) -> Handle:
+    lib = load_library()
+    v = _host(vars_, np.int32)
+    kind = SCORE_KINDS.get(kind, kind)
+    out = _vp()
+    _check(lib.fc_plan_families(ctx.ptr, len(v), _ptr(v, _i32p), int(max_parents), int(kind), float(ess),
+                                ctypes.byref(out)))
+    return Handle(out, lib.fc_plan_free, ctx)
+
+
+def family_list(vars_, max_parents: int):
+    """(child, parents) of every family in the order fc_score_families writes them."""
+    import itertools
+    vs = [int(x) for x in vars_]
+    nv = len(vs)
+    d = min(max_parents, nv - 1)
+    out = []
+    for c in range(nv):
+        others = [vs[i] for i in range(nv) if i != c]
+        for s in range(d + 1):
+            for comb in itertools.combinations(range(nv - 1), s):
+                out.append((vs[c], [others[i] for i in comb]))
     return out
 
 

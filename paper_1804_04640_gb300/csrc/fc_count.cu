@@ -49,8 +49,17 @@ struct ScoreAcc {
     double d;
 };
 
-// Per-thread part of a score over rows j0, j0 + step, ... of a complete table
-// (parents-major, child-last, r child states).
+// Parent configuration j of a table laid out parents-major, child-last:
+// its r cells start at j * r, one apart.
+struct DenseRows {
+    int32_t r;
+    __device__ __forceinline__ int64_t base(int64_t j) const { return j * r; }
+    __device__ __forceinline__ int64_t step() const { return 1; }
+};
+
+// Per-thread part of a score over parent configurations j0, j0 + step, ... of
+// a complete table; rows.base(j) is the first cell of configuration j and
+// rows.step() the distance between its r child cells.
 //   LL  = sum N_ijk log2(N_ijk / N_ij) = -(1/ln2) sum N_ijk log1p((N_ij - N_ijk) / N_ijk):
 //         every term has the same sign and the integer difference is exact.
 //   MDL = -LL + (log2 m / 2)(r - 1) q.
@@ -59,29 +68,29 @@ struct ScoreAcc {
 //         with p_j, p_k > 0, x_jk = (N_jk m - N_j N_k) / (N_j N_k) with an exact
 //         int64 numerator; this equals the usual sum because sum p_j p_k x_jk = 0,
 //         and every term is >= 0.
-template <bool kGlobal>
-__device__ ScoreAcc score_part(const int32_t *tab, int32_t cells, int32_t r, int kind,
-                               const int64_t *marg_child, int64_t m, double ess, int64_t j0,
-                               int64_t step)
+template <bool kGlobal, class Rows>
+__device__ ScoreAcc score_rows(const int32_t *tab, const Rows &rows, int64_t q, int32_t r, int kind,
+                               const int64_t *marg_child, int64_t m, double ess, int64_t j0, int64_t jstep)
 {
-    const int64_t q = cells / r;
     ScoreAcc acc{{0.0f, 0.0f}, 0.0};
     const double aj = ess / (double)q, ajk = ess / ((double)r * (double)q);
     const double lg_aj = kind == kBDeu ? lgamma(aj) : 0.0;
     const double lg_ajk = kind == kBDeu ? lgamma(ajk) : 0.0;
-    for (int64_t j = j0; j < q; j += step) {
+    const int64_t cs = rows.step();
+    for (int64_t j = j0; j < q; j += jstep) {
+        const int64_t b = rows.base(j);
         int64_t nij = 0;
-        for (int k = 0; k < r; ++k) nij += tab_ld<kGlobal>(tab, j * r + k);
+        for (int k = 0; k < r; ++k) nij += tab_ld<kGlobal>(tab, b + k * cs);
         if (nij == 0) continue;
         if (kind == kLL || kind == kMDL) {
             for (int k = 0; k < r; ++k) {
-                const int32_t n = tab_ld<kGlobal>(tab, j * r + k);
+                const int32_t n = tab_ld<kGlobal>(tab, b + k * cs);
                 if (n > 0) kahan_add(acc.k, (float)n * log1pf((float)(nij - n) / (float)n));
             }
         } else if (kind == kBDeu) {
             acc.d += lg_aj - lgamma(aj + (double)nij);
             for (int k = 0; k < r; ++k) {
-                const int32_t n = tab_ld<kGlobal>(tab, j * r + k);
+                const int32_t n = tab_ld<kGlobal>(tab, b + k * cs);
                 if (n > 0) acc.d += lgamma(ajk + (double)n) - lg_ajk;
             }
         } else {  // kMI
@@ -89,7 +98,7 @@ __device__ ScoreAcc score_part(const int32_t *tab, int32_t cells, int32_t r, int
             for (int k = 0; k < r; ++k) {
                 const int64_t nk = marg_child[k];
                 if (nk == 0) continue;
-                const int32_t n = tab_ld<kGlobal>(tab, j * r + k);
+                const int32_t n = tab_ld<kGlobal>(tab, b + k * cs);
                 const long long num = (long long)n * m - (long long)nij * nk;
                 const float x = (float)num / ((float)nij * (float)nk);
                 kahan_add(acc.k, pj * ((float)nk / (float)m) * mi_term(x));
@@ -97,6 +106,14 @@ __device__ ScoreAcc score_part(const int32_t *tab, int32_t cells, int32_t r, int
         }
     }
     return acc;
+}
+
+template <bool kGlobal>
+__device__ ScoreAcc score_part(const int32_t *tab, int32_t cells, int32_t r, int kind,
+                               const int64_t *marg_child, int64_t m, double ess, int64_t j0,
+                               int64_t step)
+{
+    return score_rows<kGlobal>(tab, DenseRows{r}, cells / r, r, kind, marg_child, m, ess, j0, step);
 }
 
 __device__ __forceinline__ void warp_merge(ScoreAcc &acc)
@@ -593,6 +610,77 @@ __global__ void __launch_bounds__(512, 2) count_kernel(const CountParams P)
     }
 }
 
+// The parent configurations of one family inside the joint table of its
+// variable set: the parents are every axis but the child's; configuration j
+// is decoded over them (last fastest) into a cell offset.
+struct FamilyRows {
+    int32_t np;
+    int32_t ar[kMaxFamily];
+    int64_t st[kMaxFamily];
+    int64_t cstep;
+    __device__ __forceinline__ int64_t base(int64_t j) const
+    {
+        int64_t b = 0;
+        for (int t = np - 1; t >= 0; --t) {
+            const int64_t d = j % ar[t];
+            j /= ar[t];
+            b += d * st[t];
+        }
+        return b;
+    }
+    __device__ __forceinline__ int64_t step() const { return cstep; }
+};
+
+// One block per family (child, parents): the score of the child given the
+// other variables of a joint table counted once for the whole variable set
+// (Sec. 4.2: every family of the parent-set lattice is a (child, rest) split
+// of some variable set).
+__global__ void family_score_kernel(const FamilyJob *__restrict__ jobs, int64_t njobs,
+                                    const int32_t *__restrict__ tables, const int32_t *__restrict__ arity,
+                                    const int32_t *__restrict__ soff, const int64_t *__restrict__ marg,
+                                    int64_t m, int kind, double ess, float *scores)
+{
+    __shared__ ScoreAcc s_red[32];
+    for (int64_t jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
+        const FamilyJob job = jobs[jb];
+        int32_t ar[kMaxFamily];
+        int64_t st[kMaxFamily];
+        int64_t stride = 1;
+        for (int t = job.k - 1; t >= 0; --t) {
+            ar[t] = arity[job.vars[t]];
+            st[t] = stride;
+            stride *= ar[t];
+        }
+        FamilyRows rows;
+        rows.np = 0;
+        int64_t q = 1;
+        for (int t = 0; t < job.k; ++t) {
+            if (t == job.child_pos) continue;
+            rows.ar[rows.np] = ar[t];
+            rows.st[rows.np] = st[t];
+            ++rows.np;
+            q *= ar[t];
+        }
+        const int32_t rc = ar[job.child_pos];
+        rows.cstep = st[job.child_pos];
+        ScoreAcc acc = score_rows<true>(tables + job.table_off, rows, q, rc, kind,
+                                        marg + soff[job.vars[job.child_pos]], m, ess, threadIdx.x, blockDim.x);
+        warp_merge(acc);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) s_red[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ScoreAcc t{{0.0f, 0.0f}, 0.0};
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                kahan_merge(t.k, s_red[w].k);
+                t.d += s_red[w].d;
+            }
+            scores[job.slot] = score_finish(t, kind, m, rc, q);
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void score_global_kernel(const QHead *__restrict__ qh, const int32_t *__restrict__ q_list,
                                     const int32_t *__restrict__ tables, float *scores,
                                     const int64_t *__restrict__ marg, int64_t m, double ess)
@@ -642,6 +730,15 @@ cudaError_t launch_bitmap(const CountParams &p, int grid, int threads, cudaStrea
     cudaError_t e = cudaFuncSetAttribute(bitmap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     bitmap_kernel<<<grid, threads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_family_scores(const FamilyJob *jobs, int64_t njobs, const int32_t *tables, const int32_t *arity,
+                                 const int32_t *soff, const int64_t *marg, int64_t m, int kind, double ess,
+                                 float *scores, int grid, cudaStream_t s)
+{
+    if (njobs <= 0) return cudaSuccess;
+    family_score_kernel<<<grid, 128, 0, s>>>(jobs, njobs, tables, arity, soff, marg, m, kind, ess, scores);
     return cudaGetLastError();
 }
 

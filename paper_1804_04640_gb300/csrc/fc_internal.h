@@ -108,6 +108,20 @@ cudaError_t launch_sort_count(const uint8_t *D, int64_t m_pad, int64_t m, const 
                               int32_t k, int32_t key_bits, int32_t *table, int32_t cells,
                               int32_t zero_table, SortScratch sc, cudaStream_t s);
 
+// One family (child, parents) scored from the joint table of its variable
+// set: vars in the table's order (last fastest), child at child_pos.
+constexpr int kMaxFamily = 8;
+struct FamilyJob {
+    int64_t table_off;
+    int32_t slot;
+    int16_t k;
+    int16_t child_pos;
+    int32_t vars[kMaxFamily];
+};
+cudaError_t launch_family_scores(const FamilyJob *jobs, int64_t njobs, const int32_t *tables, const int32_t *arity,
+                                 const int32_t *soff, const int64_t *marg, int64_t m, int kind, double ess,
+                                 float *scores, int grid, cudaStream_t s);
+
 // Scores of queries whose tables are complete in global memory.
 cudaError_t launch_score_global(const QHead *qh, const int32_t *q_list, int32_t nlist,
                                 const int32_t *tables, float *scores, const int64_t *marg,

@@ -122,3 +122,22 @@ def test_support_as_benchmarked():
         a, b = so[q], so[q + 1]
         assert supp[q] == s and np.array_equal(sub[a:b].astype(np.int64), sb)
         assert np.allclose(conf[a:b], c, rtol=1e-6, atol=0)
+
+
+def test_families_as_benchmarked():
+    torch = pytest.importorskip("torch")
+    w = bench.make_workload("families")
+    db = w["db"]
+    ctx = fc.fc_load(db.D, db.arities)
+    fams = fc.family_list(w["vars"], w["max_parents"])
+    fo, ff = fc.pack_lists([list(f[1]) + [f[0]] for f in fams])
+    fc.fc_autotune_batch(ctx, fo, ff)
+    plan = fc.fc_plan_families(ctx, w["vars"], w["max_parents"], "bdeu", 1.0)
+    assert fc.fc_plan_size(plan, 1) == len(fams)
+    (scores,) = _replay(plan, [torch.empty(len(fams), dtype=torch.float32, device="cuda")], torch)
+    assert np.all(np.isfinite(scores)) and np.all(scores < 0)
+    orc = oracle.DB(db.D, db.arities)
+    idx = np.random.default_rng(23).choice(len(fams), size=600, replace=False)
+    want = np.array(_pool_map(lambda q: orc.score(fams[q][0], fams[q][1], "bdeu", 1.0), idx))
+    got = scores[idx].astype(np.float64)
+    assert np.all(np.abs(got - want) <= 1e-5 * np.abs(want) + 1e-12)

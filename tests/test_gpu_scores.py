@@ -95,3 +95,22 @@ def test_score_plan_matches_host_call():
         fc.fc_plan_run(plan, out, stream=cur)
         fc.fc_sync(ctx, cur)
         assert np.array_equal(out.cpu().numpy(), host)
+
+
+@pytest.mark.parametrize("kind", ["mdl", "bdeu", "mi", "ll"])
+def test_family_lattice_scores(kind):
+    """Every (child, parent set) family of a variable list (Sec. 4.2 query
+    stream), each joint table counted once: against the oracle."""
+    db = random_dag_database(14, 40_003, 2, 4, 3, 1.0, seed=81)
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    vars_ = [3, 0, 11, 7, 5, 9, 12, 1, 4]
+    fams = fc.family_list(vars_, 3)
+    assert len(fams) == fc.fc_families_count(len(vars_), 3)
+    got = fc.fc_score_families(ctx, vars_, 3, kind, 1.0)
+    want = oracle_scores(orc, [f[0] for f in fams], [f[1] for f in fams], kind, 1.0, range(len(fams)))
+    assert_close(got, want, kind)
+    # the same families through the per-query score batch
+    po, pa = fc.pack_lists([f[1] for f in fams])
+    direct = fc.fc_score_batch(ctx, [f[0] for f in fams], po, pa, kind, 1.0)
+    assert_close(direct, want, kind)
