@@ -143,6 +143,9 @@ def make_workload(name: str, m: int | None = None, nq: int | None = None):
     if name == "families":
         db = config_database("scores", c["m"])
         return {"db": db, "vars": list(range(c["nv"])), "max_parents": c["max_parents"]}
+    if name == "rules":
+        return {"db": config_database("scores", c["m"]), "args": (c["min_support"], c["min_confidence"],
+                                                                  c["max_size"], False)}
     if name == "assign":
         db = config_database("random", c["m"])
         rng = np.random.default_rng(c["seed"])
@@ -178,6 +181,12 @@ def describe(name: str, w) -> dict:
         return {"workload": f"families: BN-score database (n={w['db'].n}, m={w['db'].m}), every child of the "
                             f"first {nf} variables with every parent set of <= {w['max_parents']} of the others, BDeu",
                 "n": w["db"].n, "m": w["db"].m, "variables": nf, "max_parents": w["max_parents"]}
+    if name == "rules":
+        a = w["args"]
+        return {"workload": f"rules: bottom-up mining over the {int(w['db'].arities.sum())} (variable, state) items "
+                            f"of the BN-score database (n={w['db'].n}, m={w['db'].m}), support > {a[0]}, "
+                            f"confidence > {a[1]}, itemsets of <= {a[2]} items, single-item consequents",
+                "n": w["db"].n, "m": w["db"].m, "min_support": a[0], "min_confidence": a[1], "max_size": a[2]}
     if name == "assign":
         return {"workload": f"assign: n={w['db'].n}, m={w['db'].m}, {len(w['assign'])} specific assignments of "
                             f"{c['k'][0]}-{c['k'][1]} conditions", "n": w["db"].n, "m": w["db"].m,
@@ -235,6 +244,20 @@ def oracle_rate(name: str, w, seconds: float, cores: int):
                 units += len(chunk)
                 i += len(chunk)
             sample = f"{units} families scored one by one from row scans, {cores} threads"
+        elif name == "rules":
+            from oracle import miner
+            db = w["db"]
+            ms = max(1000, min(db.m, 20_000))
+            X = miner.item_matrix_from_db(db.D[:, :ms], db.arities)
+            st = {}
+            t0 = time.perf_counter()
+            miner.mine_rules(X, *w["args"], stats=st)
+            dt_s = time.perf_counter() - t0
+            # the row scans dominate and grow linearly in m: scale to the full rows
+            units = st.get("candidates", 0) * ms / db.m
+            sample = (f"the whole mining run on the first {ms} of {db.m} rows ({st.get('candidates', 0)} candidates "
+                      f"scanned in {dt_s:.1f} s, 1 thread), rate scaled by {ms}/{db.m}")
+            return units / dt_s, sample
         elif name == "assign":
             orc = oracle.DB(w["db"].D, w["db"].arities)
             jobs = w["assign"]
@@ -280,7 +303,8 @@ def oracle_rate(name: str, w, seconds: float, cores: int):
 
 METRIC = "count queries/s (exact full contingency tables, batched persistent launch)"
 UNITS = {"tiny": "queries/s", "random": "queries/s", "large": "queries/s", "scores": "queries/s",
-         "pairs": "pairs/s", "support": "itemsets/s", "assign": "assignments/s", "families": "families/s"}
+         "pairs": "pairs/s", "support": "itemsets/s", "assign": "assignments/s", "families": "families/s",
+         "rules": "candidate itemsets/s"}
 
 
 def run_reference(args, rank: int, world: int):
@@ -289,6 +313,8 @@ def run_reference(args, rank: int, world: int):
     w = make_workload(args.workload, args.m, args.nq)
     cores = os.cpu_count() or 1
     rate, sample = oracle_rate(args.workload, w, args.ref_seconds, cores)
+    if args.workload == "rules":
+        cores = 1  # the oracle's level-wise search runs on one thread
     steps = []
     for _ in range(args.warmup + args.steps):
         steps.append(oracle_rate(args.workload, w, max(0.5, args.ref_seconds / 4), cores)[0])
@@ -325,6 +351,8 @@ def run_gpu(args, rank: int, world: int):
         torch.cuda.synchronize()
 
     name = args.workload
+    if name == "rules":
+        return run_rules_gpu(args, rank, world, fc, torch, barrier, dist, dev)
     w = make_workload(name, args.m, args.nq)
     stream = torch.cuda.Stream()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
@@ -587,6 +615,99 @@ def run_gpu(args, rank: int, world: int):
             line["batched_over_per_query"] = value / world / pq["value"]
         if pf is not None:
             line["per_family_tables"] = pf
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+def run_rules_gpu(args, rank, world, fc, torch, barrier, dist, dev):
+    """One step = one whole fc_mine_rules call (host candidate generation,
+    one counting launch per level, counts read back), timed with CUDA events
+    around the synchronous call on an idle device."""
+    name = "rules"
+    w = make_workload(name, args.m, args.nq)
+    db = w["db"]
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    hbm, _, _, peak_src = peaks()
+    ctx = fc.fc_load(db.D, db.arities)
+    for _ in range(args.warmup):
+        r = fc.fc_mine_rules(ctx, *w["args"])
+    torch.cuda.synchronize()
+    units = r["candidates"]
+    steps = min(args.steps, 50)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    dev_ns = []
+    barrier()
+    with ClockSampler(dev) as clk:
+        for i in range(steps):
+            flush.fill_(i)
+            torch.cuda.synchronize()
+            starts[i].record()
+            r = fc.fc_mine_rules(ctx, *w["args"])
+            ends[i].record()
+            dev_ns.append(r["device_ns"])
+        barrier()
+        times = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    ms = float(np.mean(times))
+    total_ms = float(np.sum(times))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = units * world * steps / (total_ms / 1e3)
+
+    # end to end: load the database from host memory, mine, results on the host
+    e2e_t = []
+    for _ in range(max(3, min(steps, 10))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2 = fc.fc_load(db.D, db.arities)
+        r2 = fc.fc_mine_rules(c2, *w["args"])
+        del c2
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = float(np.median(e2e_t))
+
+    # dominant kernel: the per-level itemset count; algorithmic bytes = one
+    # bitmap row of ceil(m/64) words per item of every candidate
+    sizes = np.diff(r["set_off"])
+    row_bytes = (db.m + 63) // 64 * 8
+    dev_ms = float(np.median(dev_ns)) / 1e6
+    line = None
+    if rank == 0:
+        cores = os.cpu_count() or 1
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            rate, sample = oracle_rate(name, w, args.cpu_seconds, cores)
+            cpu = {"value": rate, "unit": UNITS[name], "cores": 1, "kind": "oracle", "sample": sample}
+        alg_bytes = r["candidate_items"] * row_bytes
+        line = {
+            "metric": f"{name}: {UNITS[name]}", "value": value, "unit": UNITS[name], "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8/int32",
+            "data": "synthetic (seeded random-DAG samples)",
+            "config": dict(describe(name, w), l2="flushed between timed steps (256 MiB write)",
+                           frequent_itemsets=int(len(sizes)), rules=int(len(r["rule_set"])),
+                           candidates=int(units), levels=int(r["levels"]),
+                           max_itemset=int(sizes.max()) if len(sizes) else 0),
+            "e2e": {"value": units / e2e_s, "unit": UNITS[name],
+                    "h2d_bytes_per_step": int(db.n * db.m + r2["h2d_bytes"]),
+                    "d2h_bytes_per_step": int(r2["d2h_bytes"])},
+            "gpu_launches": steps * int(r["levels"]),
+            "device_ms_per_step": dev_ms,
+            "cpu_baseline": cpu, "clocks": clk.summary(),
+        }
+        if dev_ms > 0:
+            achieved = alg_bytes / (dev_ms / 1e3) / 1e9
+            line["roofline"] = {
+                "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
+                "note": (f"effective bytes/s of the counting launches (device time of the levels, "
+                         f"{dev_ms:.3f} ms of {ms:.3f} ms per step); the {db.arities.sum() * row_bytes / 2**20:.0f} "
+                         "MiB of item bitmaps stay in L2, so this is not an HBM fraction"),
+                "duration": "sum of the per-level counting launches (CUDA events inside the library)"}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

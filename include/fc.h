@@ -203,6 +203,58 @@ int64_t fc_pairs_cells(const fc_ctx *ctx);
 int fc_support_batch(fc_ctx *ctx, int32_t nq, const int32_t *set_off, const int32_t *items,
                      int32_t *support, int32_t *sub_support, float *confidence);
 
+/* ----------------------------------------------- association-rule mining
+ *
+ * Bottom-up search of the itemset lattice (Sec. 4.3): level 1 is every item,
+ * level k every k-itemset whose (k-1)-subsets are all frequent; each level's
+ * candidates are counted in one batched device launch (specific-assignment
+ * counts, end of Sec. 3.3), the frequent ones kept, and the search stops at
+ * max_size items or at an empty level.
+ *
+ * Items: for a context from fc_load_bits, item i is transaction bitmap i; for
+ * a categorical context, item soff(v) + s is the event D[v] == s, where soff(v)
+ * is the sum of the arities of variables 0..v-1 (two states of one variable
+ * never form an itemset).
+ *
+ * Thresholds (strict, as the paper states them, decided in double precision):
+ *   S is frequent     when supp(S) > min_support * m;
+ *   rule A => S \ A   is kept when supp(S) > min_confidence * supp(A),
+ * for frequent S of at least 2 items and A a non-empty proper subset of S:
+ * every such A when all_splits = 1 (2^k - 2 rules per k-itemset), else only
+ * the A that leave one item as consequent (rules Pa(X) => X).
+ * min_support in [0, 1], min_confidence >= 0, max_size in [1, 32] (at most 16
+ * with all_splits).
+ *
+ * The result is host memory owned by the returned handle: read it with
+ * fc_rules_size / fc_rules_itemsets / fc_rules_list, release it with
+ * fc_rules_free.  Errors: FC_ERR_ARG (bad threshold or size), FC_ERR_SIZE
+ * (more than 2^31 - 1 candidates on one level), FC_ERR_CUDA, FC_ERR_OOM. */
+typedef struct fc_rules fc_rules;
+int fc_mine_rules(fc_ctx *ctx, double min_support, double min_confidence, int32_t max_size,
+                  int32_t all_splits, fc_rules **out);
+
+/* key 0 = frequent itemsets, 1 = items over all of them, 2 = rules,
+ * 3 = candidate itemsets counted on the device, 4 = levels counted on the
+ * device, 5 = descriptor bytes copied host to device, 6 = count bytes copied
+ * device to host, 7 = nanoseconds of device time in the counting launches
+ * (CUDA events around each level's launch), 8 = items over the candidates
+ * (bitmap rows the counting launches read).  -1 for a bad key. */
+int64_t fc_rules_size(const fc_rules *rules, int32_t key);
+
+/* Frequent itemsets, size by size and lexicographic within a size, each in
+ * increasing item order: set_off (count + 1 int32, CSR offsets into items),
+ * items (int32) and support (int64).  Host buffers sized by fc_rules_size;
+ * any may be NULL. */
+int fc_rules_itemsets(const fc_rules *rules, int32_t *set_off, int32_t *items, int64_t *support);
+
+/* Rules in itemset order, then by antecedent mask: itemset (int64 index into
+ * the itemset list), antecedent (bit t set when item t of the itemset is in
+ * A; the consequent is the rest) and confidence supp(S) / supp(A) (float,
+ * the double quotient rounded once).  Host buffers; any may be NULL. */
+int fc_rules_list(const fc_rules *rules, int64_t *itemset, uint32_t *antecedent, float *confidence);
+
+void fc_rules_free(fc_rules *rules);
+
 /* ------------------------------------------- plans: device-resident batches
  *
  * A plan validates a batch once, picks a strategy per query, uploads the

@@ -32,7 +32,8 @@ EXPORTS = (
     "fc_sync", "fc_set_option", "fc_get_option", "fc_autotune", "fc_last_error",
     "fc_selftest_wait_timeout", "fc_count_sorted_noalloc", "fc_autotune_batch",
     "fc_count_assignment_batch", "fc_plan_assignments", "fc_families_count", "fc_score_families",
-    "fc_plan_families",
+    "fc_plan_families", "fc_mine_rules", "fc_rules_size", "fc_rules_itemsets", "fc_rules_list",
+    "fc_rules_free",
 )
 
 
@@ -102,6 +103,12 @@ def load_library(build_if_missing: bool = False):
                                             ctypes.c_double, ctypes.POINTER(_vp)]),
         "fc_count_assignment_batch": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p, _i32p, _i64p]),
         "fc_plan_assignments": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p, _i32p, ctypes.POINTER(_vp)]),
+        "fc_mine_rules": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(_vp)]),
+        "fc_rules_size": (ctypes.c_int64, [_vp, ctypes.c_int32]),
+        "fc_rules_itemsets": (ctypes.c_int, [_vp, _i32p, _i32p, _i64p]),
+        "fc_rules_list": (ctypes.c_int, [_vp, _i64p, ctypes.POINTER(ctypes.c_uint32), _f32p]),
+        "fc_rules_free": (None, [_vp]),
         "fc_last_error": (ctypes.c_char_p, []),
         "fc_selftest_wait_timeout": (ctypes.c_int, [_vp, ctypes.c_int64]),
         "fc_count_sorted_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _i32p,
@@ -333,6 +340,38 @@ def family_list(vars_, max_parents: int):
             for comb in itertools.combinations(range(nv - 1), s):
                 out.append((vs[c], [others[i] for i in comb]))
     return out
+
+
+def fc_mine_rules(ctx: Handle, min_support: float, min_confidence: float, max_size: int,
+                  all_splits: bool = False):
+    """Bottom-up rule mining (layout in include/fc.h).
+
+    Returns a dict: ``set_off``/``items``/``support`` (frequent itemsets, CSR),
+    ``rule_set``/``antecedent``/``confidence`` (rules), and the number of
+    ``candidates`` and ``levels`` counted on the device.
+    """
+    lib = load_library()
+    h = _vp()
+    _check(lib.fc_mine_rules(ctx.ptr, float(min_support), float(min_confidence), int(max_size),
+                             int(bool(all_splits)), ctypes.byref(h)))
+    try:
+        ns, ni, nr = (int(lib.fc_rules_size(h, k)) for k in range(3))
+        so = np.zeros(ns + 1, dtype=np.int32)
+        it = np.zeros(max(ni, 1), dtype=np.int32)
+        sp = np.zeros(max(ns, 1), dtype=np.int64)
+        _check(lib.fc_rules_itemsets(h, _ptr(so, _i32p), _ptr(it, _i32p), _ptr(sp, _i64p)))
+        rs = np.zeros(max(nr, 1), dtype=np.int64)
+        ra = np.zeros(max(nr, 1), dtype=np.uint32)
+        rc = np.zeros(max(nr, 1), dtype=np.float32)
+        _check(lib.fc_rules_list(h, _ptr(rs, _i64p), ra.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                 _ptr(rc, _f32p)))
+        return {"set_off": so, "items": it[:ni], "support": sp[:ns], "rule_set": rs[:nr],
+                "antecedent": ra[:nr], "confidence": rc[:nr],
+                "candidates": int(lib.fc_rules_size(h, 3)), "levels": int(lib.fc_rules_size(h, 4)),
+                "h2d_bytes": int(lib.fc_rules_size(h, 5)), "d2h_bytes": int(lib.fc_rules_size(h, 6)),
+                "device_ns": int(lib.fc_rules_size(h, 7)), "candidate_items": int(lib.fc_rules_size(h, 8))}
+    finally:
+        lib.fc_rules_free(h)
 
 
 def fc_pairs_cells(ctx: Handle) -> int:

@@ -1287,6 +1287,54 @@ extern "C" int fc_plan_assignments(fc_ctx *c, int32_t nq, const int32_t *var_off
     return build_set_plan(c, nq, var_off, rows.data(), 1, out);
 }
 
+void fc::itemset_universe(const fc_ctx *c, int32_t *n_items, int64_t *m)
+{
+    *n_items = c->R;
+    *m = c->m;
+}
+
+void fc::item_groups(const fc_ctx *c, int32_t *group, int64_t *support)
+{
+    for (int32_t v = 0; v < c->n; ++v)
+        for (int32_t s = 0; s < c->arity[v]; ++s) group[c->soff[v] + s] = v;
+    std::copy(c->marg.begin(), c->marg.end(), support);
+}
+
+int fc::count_itemsets(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *rows, int32_t *counts,
+                       ItemsetCountStats *st)
+{
+    if (nq == 0) return FC_OK;
+    DevGuard g(c->device);
+    fc_plan *p = nullptr;
+    int rc;
+    {
+        BorrowScope b(c);
+        rc = build_set_plan(c, nq, set_off, rows, 1, &p);
+    }
+    if (rc != FC_OK) return rc;
+    const size_t bytes = sizeof(int32_t) * nq;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = c->io[0].ensure(bytes);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->stream);
+    rc = e != cudaSuccess ? cuda_fail(e, "itemset counts") : run_plan(p, c->io[0].p, nullptr, nullptr, c->stream, false);
+    if (rc == FC_OK && (e = cudaEventRecord(ev[1], c->stream)) == cudaSuccess)
+        e = cudaMemcpyAsync(counts, c->io[0].p, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (rc == FC_OK && e != cudaSuccess) rc = cuda_fail(e, "itemset counts");
+    if (rc == FC_OK) rc = read_status(c, c->stream);
+    if (rc == FC_OK && st) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) st->device_ms += ms;
+        st->h2d_bytes += (int64_t)p->upload_bytes;
+        st->d2h_bytes += (int64_t)bytes;
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    fc_plan_free(p);
+    return rc;
+}
+
 extern "C" int fc_count_assignment_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int32_t *vars,
                                          const int32_t *states, int64_t *counts)
 {

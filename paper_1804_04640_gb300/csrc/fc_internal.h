@@ -182,3 +182,25 @@ cudaError_t launch_wait_selftest(int32_t *status, int64_t wait_limit, cudaStream
 int set_error(int code, const char *fmt, ...);
 
 }  // namespace fc
+
+// ---- items of a context, for the rule miner (fc_rules.cu)
+struct fc_ctx;
+namespace fc {
+// Number of items (bitmap rows) of a context and its instance count m.
+void itemset_universe(const fc_ctx *c, int32_t *n_items, int64_t *m);
+// For each item: the variable it belongs to (an item of a categorical context
+// is one state of a variable; a transaction item is its own group) and its
+// support (the popcount of its bitmap).  Arrays of n_items entries.
+void item_groups(const fc_ctx *c, int32_t *group, int64_t *support);
+// Totals of count_itemsets calls: descriptor bytes uploaded, count bytes read
+// back, and device time of the counting launches (CUDA events around them).
+struct ItemsetCountStats {
+    int64_t h2d_bytes = 0, d2h_bytes = 0;
+    double device_ms = 0.0;
+};
+// Support of each of nq itemsets (lists of item ids in `rows`, CSR offsets
+// `set_off` with set_off[0] == 0, ids already validated), counted on the
+// device; int32 results in the host array `counts`.  `st` may be NULL.
+int count_itemsets(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *rows, int32_t *counts,
+                   ItemsetCountStats *st);
+}  // namespace fc

@@ -141,3 +141,49 @@ def test_families_as_benchmarked():
     want = np.array(_pool_map(lambda q: orc.score(fams[q][0], fams[q][1], "bdeu", 1.0), idx))
     got = scores[idx].astype(np.float64)
     assert np.all(np.abs(got - want) <= 1e-5 * np.abs(want) + 1e-12)
+
+
+def test_rules_as_benchmarked():
+    """Full-size mining run: every pair of frequent items is checked against a
+    complete pair-count matrix, a sample of larger itemsets against the
+    oracle's row scan, and every rule against the reported supports."""
+    from oracle import miner
+    w = bench.make_workload("rules")
+    db = w["db"]
+    min_support, min_conf, max_size, _ = w["args"]
+    ctx = fc.fc_load(db.D, db.arities)
+    r = fc.fc_mine_rules(ctx, *w["args"])
+    r2 = fc.fc_mine_rules(ctx, *w["args"])
+    for k in ("set_off", "items", "support", "rule_set", "antecedent", "confidence"):
+        assert np.array_equal(r[k], r2[k])
+    so, it, sp = r["set_off"], r["items"], r["support"]
+    sets = [tuple(int(x) for x in it[so[i]:so[i + 1]]) for i in range(len(so) - 1)]
+    assert sets == sorted(sets, key=lambda S: (len(S), S)) and max(map(len, sets)) <= max_size
+    thr = min_support * db.m
+    assert all(float(s) > thr for s in sp)
+    X = miner.item_matrix_from_db(db.D, db.arities)
+    single = X.sum(axis=1)
+    freq1 = [i for i in range(X.shape[0]) if float(single[i]) > thr]
+    assert [S for S in sets if len(S) == 1] == [(i,) for i in freq1]
+    Xf = X[freq1].astype(np.float32)
+    pair = (Xf @ Xf.T).astype(np.int64)  # counts <= 1e6 are exact in float32
+    want2 = {(freq1[a], freq1[b]): int(pair[a, b]) for a in range(len(freq1)) for b in range(a + 1, len(freq1))
+             if float(pair[a, b]) > thr}
+    got2 = {S: int(s) for S, s in zip(sets, sp) if len(S) == 2}
+    assert got2 == want2
+    big = [i for i, S in enumerate(sets) if len(S) >= 3]
+    idx = np.random.default_rng(31).choice(big, size=min(300, len(big)), replace=False)
+    want = _pool_map(lambda i: miner.itemset_support(X, sets[i]), idx)
+    assert [int(sp[i]) for i in idx] == want
+    index = {S: i for i, S in enumerate(sets)}
+    rules = {(int(a), int(b)): float(c) for a, b, c in zip(r["rule_set"], r["antecedent"], r["confidence"])}
+    for i, S in enumerate(sets):
+        k = len(S)
+        for t in range(k - 1, -1, -1) if k >= 2 else ():
+            mk = ((1 << k) - 1) ^ (1 << t)
+            sa = int(sp[index[tuple(S[u] for u in range(k) if mk >> u & 1)]])
+            keep = float(sp[i]) > min_conf * float(sa)
+            assert ((i, mk) in rules) == keep
+            if keep:
+                assert rules[(i, mk)] == np.float32(float(sp[i]) / float(sa))
+    assert len(rules) == len(r["rule_set"])

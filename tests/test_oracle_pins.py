@@ -226,3 +226,106 @@ def test_support_rules_brute_force():
     assert oracle.support_rules(bits, m, [])[0] == m
     for i in range(12):
         assert oracle.support_rules(bits, m, [i])[0] == int(holds[i].sum())
+
+
+# ---- association-rule miner (Sec. 4.3) -------------------------------------
+
+def _rules_cases():
+    txs, cases, cur = [], [], None
+    for line in open(os.path.join(GOLDEN, "rules_example.txt")):
+        tok = line.split()
+        if not tok or tok[0].startswith("#"):
+            continue
+        if tok[0] == "tx":
+            txs.append([int(x) for x in tok[1:]])
+        elif tok[0] == "case":
+            cur = {"args": (float(tok[1]), float(tok[2]), int(tok[3]), bool(int(tok[4]))),
+                   "sets": [], "rules": []}
+        elif tok[0] == "set":
+            i = tok.index(":")
+            cur["sets"].append((tuple(int(x) for x in tok[1:i]), int(tok[i + 1])))
+        elif tok[0] == "rule":
+            a, b = tok[3].split("/")
+            cur["rules"].append((int(tok[1]), int(tok[2]), int(a) / int(b)))
+        elif tok[0] == "end":
+            cases.append(cur)
+    X = np.zeros((4, len(txs)), dtype=bool)
+    for p, t in enumerate(txs):
+        X[t, p] = True
+    return X, cases
+
+
+def test_rules_hand_worked():
+    """Frequent itemsets and rules of a hand-worked six-transaction database,
+    including the strict thresholds and the size limit."""
+    from oracle import miner
+    X, cases = _rules_cases()
+    assert len(cases) == 5
+    for c in cases:
+        sets, supp, rules = miner.mine_rules(X, *c["args"])
+        assert list(zip(sets, supp)) == c["sets"], c["args"]
+        assert [(i, mk) for i, mk, _ in rules] == [(i, mk) for i, mk, _ in c["rules"]], c["args"]
+        for (_, _, got), (_, _, want) in zip(rules, c["rules"]):
+            assert got == pytest.approx(want, rel=1e-15)
+
+
+def _brute_rules(X, min_support, min_confidence, max_size, all_splits):
+    """Every subset of at most max_size items, counted with a row loop."""
+    n, m = X.shape
+    rows = [set(np.flatnonzero(X[:, p]).tolist()) for p in range(m)]
+
+    def supp(S):
+        return sum(1 for r in rows if all(i in r for i in S))
+
+    sets = []
+    for k in range(1, max_size + 1):
+        for S in itertools.combinations(range(n), k):
+            s = supp(S)
+            if s > min_support * m:
+                sets.append((S, s))
+    rules = []
+    for idx, (S, s) in enumerate(sets):
+        k = len(S)
+        for mask in range(1, (1 << k) - 1):
+            if not all_splits and bin(mask).count("1") != k - 1:
+                continue
+            a = supp([S[t] for t in range(k) if mask >> t & 1])
+            if s > min_confidence * a:
+                rules.append((idx, mask, s / a))
+    return sets, rules
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_rules_brute_force(seed):
+    """The level-wise search equals counting every subset of at most max_size
+    items directly (correlated items so that sets of 4-5 items are frequent)."""
+    from oracle import miner
+    rng = np.random.default_rng(seed)
+    n, m = 10, 120
+    base = rng.random(m) < 0.7
+    X = np.array([(base & (rng.random(m) < 0.9)) | (rng.random(m) < 0.2) for _ in range(n)])
+    for args in [(0.25, 0.5, 5, False), (0.3, 0.7, 4, True), (0.05, 0.0, 3, True), (0.9, 0.3, 6, False)]:
+        sets, supp, rules = miner.mine_rules(X, *args)
+        bsets, brules = _brute_rules(X, *args)
+        assert sorted(zip(sets, supp)) == sorted(bsets)
+        # order: size by size, lexicographic within a size
+        assert sets == sorted(sets, key=lambda S: (len(S), S))
+        got = {(sets[i], mk): c for i, mk, c in rules}
+        want = {(bsets[i][0], mk): c for i, mk, c in brules}
+        assert got.keys() == want.keys() and all(got[k] == pytest.approx(want[k], rel=1e-15) for k in got)
+    assert max(len(S) for S in miner.mine_rules(X, 0.25, 0.5, 6)[0]) >= 4
+
+
+def test_rules_item_matrices():
+    """Item ids of a categorical database are (variable, state) pairs in
+    arity order; bitmaps unpack least significant bit first."""
+    from oracle import miner
+    D = np.array([[0, 1, 2, 1], [1, 1, 0, 0]], dtype=np.uint8)
+    X = miner.item_matrix_from_db(D, [3, 2])
+    assert X.shape == (5, 4)
+    assert X[2].tolist() == [False, False, True, False] and X[3].tolist() == [False, False, True, True]
+    bits = np.array([[0b1011], [1 << 63 | 1]], dtype=np.uint64)
+    Y = miner.item_matrix_from_bits(bits, 64)
+    assert Y[0, :4].tolist() == [True, True, False, True] and Y[0].sum() == 3
+    assert Y[1, 0] and Y[1, 63] and Y[1].sum() == 2
+    assert miner.itemset_support(X, []) == 4 and miner.itemset_support(X, [1, 3]) == 1

@@ -13,6 +13,7 @@ from .synth import (  # noqa: F401
     score_queries,
     zipf_item_probs,
     zipf_transaction_bitmaps,
+    basket_transaction_bitmaps,
     weighted_itemsets,
     config_database,
     CONFIGS,

@@ -157,6 +157,30 @@ def zipf_transaction_bitmaps(n_items: int, m: int, s: float, mean_len: float,
     return out
 
 
+def basket_transaction_bitmaps(n_items: int, m: int, n_groups: int, seed: int) -> np.ndarray:
+    """Correlated transactions: item i belongs to group i % n_groups; each
+    transaction switches group g on with probability a_g ~ U(0.3, 0.8); an
+    item is present with probability p_i ~ U(0.6, 0.95) when its group is on
+    and e_i ~ U(0, 0.15) otherwise.  Items of one group therefore co-occur and
+    form frequent itemsets of several items.  Packed like
+    zipf_transaction_bitmaps: shape (n_items, ceil(m/64)), uint64, bit p of
+    word w is transaction 64 w + p."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.3, 0.8, size=n_groups)
+    p_on = rng.uniform(0.6, 0.95, size=n_items)
+    p_off = rng.uniform(0.0, 0.15, size=n_items)
+    words = (m + 63) // 64
+    out = np.zeros((n_items, words), dtype=np.uint64)
+    on = rng.random((n_groups, m)) < a[:, None]
+    row = np.zeros(words * 64, dtype=bool)
+    for it in range(n_items):
+        g = it % n_groups
+        u = rng.random(m)
+        row[:m] = np.where(on[g], u < p_on[it], u < p_off[it])
+        out[it] = np.packbits(row, bitorder="little").view(np.uint64)
+    return out
+
+
 def weighted_itemsets(n_items: int, nq: int, k_lo: int, k_hi: int,
                       probs: np.ndarray, seed: int) -> list:
     """``nq`` distinct itemsets, size uniform in {k_lo..k_hi}; items within a
@@ -219,6 +243,10 @@ CONFIGS = {
     # the parent-set lattice over the first 20 variables of the BN-score
     # database, parent sets of at most 4 (Sec. 4.2 query stream)
     "families": dict(m=1_000_000, nv=20, max_parents=4, seed=4),
+    # bottom-up rule mining over the (variable, state) items of the BN-score
+    # database: support > 0.2, confidence > 0.3, itemsets of at most 6 items
+    # (Sec. 4.3 thresholds), single-item consequents
+    "rules": dict(m=1_000_000, min_support=0.2, min_confidence=0.3, max_size=6),
     # specific assignments over the batched-random database (end of Sec. 3.3)
     "assign": dict(m=100_000, seed=7, nq=100_000, k=(1, 6)),
     # tables beyond shared memory (up to 16^5 cells): the global-atomic and
