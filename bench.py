@@ -146,6 +146,8 @@ def make_workload(name: str, m: int | None = None, nq: int | None = None):
     if name == "rules":
         return {"db": config_database("scores", c["m"]), "args": (c["min_support"], c["min_confidence"],
                                                                   c["max_size"], False)}
+    if name == "append":
+        return {"db": config_database("scores", c["m"] + c["block"]), "m0": c["m"], "block": c["block"]}
     if name == "assign":
         db = config_database("random", c["m"])
         rng = np.random.default_rng(c["seed"])
@@ -181,6 +183,10 @@ def describe(name: str, w) -> dict:
         return {"workload": f"families: BN-score database (n={w['db'].n}, m={w['db'].m}), every child of the "
                             f"first {nf} variables with every parent set of <= {w['max_parents']} of the others, BDeu",
                 "n": w["db"].n, "m": w["db"].m, "variables": nf, "max_parents": w["max_parents"]}
+    if name == "append":
+        return {"workload": f"append: BN-score database (n={w['db'].n}) loaded with {w['m0']} instances, "
+                            f"each step appends a block of {w['block']} instances from device memory",
+                "n": w["db"].n, "m0": w["m0"], "block": w["block"]}
     if name == "rules":
         a = w["args"]
         return {"workload": f"rules: bottom-up mining over the {int(w['db'].arities.sum())} (variable, state) items "
@@ -244,6 +250,21 @@ def oracle_rate(name: str, w, seconds: float, cores: int):
                 units += len(chunk)
                 i += len(chunk)
             sample = f"{units} families scored one by one from row scans, {cores} threads"
+        elif name == "append":
+            # the oracle has no incremental state: a grown database is scanned
+            # again, so its append rate is the rate of re-deriving the
+            # marginals (one pass over every instance) per appended block
+            db = w["db"]
+            orc = oracle.DB(db.D[:, : w["m0"] + w["block"]], db.arities)
+            t0 = time.perf_counter()
+            rows = 0
+            while rows == 0 or time.perf_counter() - t0 < seconds:
+                for v in range(db.n):
+                    orc.table([v])
+                rows += w["block"]
+            dt_s = time.perf_counter() - t0
+            return rows / dt_s, (f"one-variable tables of all {db.n} variables over the "
+                                 f"{w['m0'] + w['block']} instances after an append, repeated, 1 thread")
         elif name == "rules":
             from oracle import miner
             db = w["db"]
@@ -304,7 +325,7 @@ def oracle_rate(name: str, w, seconds: float, cores: int):
 METRIC = "count queries/s (exact full contingency tables, batched persistent launch)"
 UNITS = {"tiny": "queries/s", "random": "queries/s", "large": "queries/s", "scores": "queries/s",
          "pairs": "pairs/s", "support": "itemsets/s", "assign": "assignments/s", "families": "families/s",
-         "rules": "candidate itemsets/s"}
+         "rules": "candidate itemsets/s", "append": "instances/s"}
 
 
 def run_reference(args, rank: int, world: int):
@@ -313,8 +334,8 @@ def run_reference(args, rank: int, world: int):
     w = make_workload(args.workload, args.m, args.nq)
     cores = os.cpu_count() or 1
     rate, sample = oracle_rate(args.workload, w, args.ref_seconds, cores)
-    if args.workload == "rules":
-        cores = 1  # the oracle's level-wise search runs on one thread
+    if args.workload in ("rules", "append"):
+        cores = 1  # these oracle legs run on one thread
     steps = []
     for _ in range(args.warmup + args.steps):
         steps.append(oracle_rate(args.workload, w, max(0.5, args.ref_seconds / 4), cores)[0])
@@ -353,6 +374,8 @@ def run_gpu(args, rank: int, world: int):
     name = args.workload
     if name == "rules":
         return run_rules_gpu(args, rank, world, fc, torch, barrier, dist, dev)
+    if name == "append":
+        return run_append_gpu(args, rank, world, fc, torch, barrier, dist, dev)
     w = make_workload(name, args.m, args.nq)
     stream = torch.cuda.Stream()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
@@ -708,6 +731,93 @@ def run_rules_gpu(args, rank, world, fc, torch, barrier, dist, dev):
                          f"{dev_ms:.3f} ms of {ms:.3f} ms per step); the {db.arities.sum() * row_bytes / 2**20:.0f} "
                          "MiB of item bitmaps stay in L2, so this is not an HBM fraction"),
                 "duration": "sum of the per-level counting launches (CUDA events inside the library)"}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+def run_append_gpu(args, rank, world, fc, torch, barrier, dist, dev):
+    """One step = one fc_append of a block of instances that already sits in
+    device memory (copy behind the old instances, state check, bitmap repack
+    from the old m / 64, marginal update), timed with CUDA events around the
+    synchronous call on an idle device; the context was reserved up front."""
+    name = "append"
+    w = make_workload(name, args.m, args.nq)
+    db, m0, B = w["db"], w["m0"], w["block"]
+    D = np.ascontiguousarray(db.D)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    hbm, _, _, peak_src = peaks()
+    steps = min(args.steps, 50)
+    ctx = fc.fc_load(D[:, :m0], db.arities)
+    fc.fc_reserve(ctx, m0 + B * (args.warmup + steps + 1))
+    block = torch.from_numpy(np.ascontiguousarray(D[:, m0:m0 + B])).cuda()
+    for _ in range(args.warmup):
+        fc.fc_append(ctx, block)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    barrier()
+    with ClockSampler(dev) as clk:
+        for i in range(steps):
+            flush.fill_(i)
+            torch.cuda.synchronize()
+            starts[i].record()
+            fc.fc_append(ctx, block)
+            ends[i].record()
+        barrier()
+        times = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    ms = float(np.mean(times))
+    total_ms = float(np.sum(times))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = B * world * steps / (total_ms / 1e3)
+    # the grown context still answers like a single load (spot check)
+    assert fc.fc_info(ctx, 1) == m0 + B * (args.warmup + steps)
+
+    # end to end: the block comes from host memory (pinned) each step
+    host_block = torch.from_numpy(np.ascontiguousarray(D[:, m0:m0 + B])).pin_memory()
+    e2e_ctx = fc.fc_load(D[:, :m0], db.arities)
+    fc.fc_reserve(e2e_ctx, m0 + B * 12)
+    e2e_t = []
+    for _ in range(10):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fc.fc_append(e2e_ctx, host_block.numpy())
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = float(np.median(e2e_t[2:]))
+
+    R = int(db.arities.sum())
+    # algorithmic bytes per appended instance: read the new states and write
+    # them behind D (2 n), read them again for the state check and the
+    # marginals (2 n) and once more to pack (n), write R bits
+    per_row = 5 * db.n + R / 8
+    line = None
+    if rank == 0:
+        cores = os.cpu_count() or 1
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            rate, sample = oracle_rate(name, w, args.cpu_seconds, cores)
+            cpu = {"value": rate, "unit": UNITS[name], "cores": 1, "kind": "oracle", "sample": sample}
+        achieved = per_row * B / (ms / 1e3) / 1e9
+        line = {
+            "metric": f"{name}: {UNITS[name]}", "value": value, "unit": UNITS[name], "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded random-DAG samples)",
+            "config": dict(describe(name, w), l2="flushed between timed steps (256 MiB write)"),
+            "e2e": {"value": B / e2e_s, "unit": UNITS[name], "h2d_bytes_per_step": int(db.n * B),
+                    "d2h_bytes_per_step": int(8 * R + 4)},
+            "gpu_launches": steps * 3,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
+                         "duration": "whole append call (copy, check, pack, marginals, two host syncs)",
+                         "note": f"algorithmic {per_row:.0f} B per appended instance"},
+            "cpu_baseline": cpu, "clocks": clk.summary(),
+        }
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

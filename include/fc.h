@@ -101,18 +101,50 @@ int fc_load(fc_ctx **out, const uint8_t *D, int32_t n, int64_t m, const int32_t 
 /* Load binary transaction data for association-rule queries (Sec. 4.3).
  *   bitmaps n_items rows of ceil(m / 64) uint64 words; bit p % 64 of word
  *           p / 64 of row i is set when transaction p holds item i.
- * Bits at positions >= m are ignored.  Only fc_support_batch and
- * fc_plan_support apply to such a context.
+ * Bits at positions >= m are ignored.  Only fc_support_batch,
+ * fc_plan_support, fc_mine_rules and fc_append_bits apply to such a context.
  * Errors: FC_ERR_ARG, FC_ERR_RANGE (m >= 2^31), FC_ERR_OOM, FC_ERR_CUDA. */
 int fc_load_bits(fc_ctx **out, const uint64_t *bitmaps, int32_t n_items, int64_t m, int32_t where);
 
-/* Release a context and all device memory it owns.  Plans made from it must
- * be freed first.  Null is ignored. */
+/* Release a context and all device memory it owns.  Plans made from it and
+ * not yet freed lose their device memory and can then only be passed to
+ * fc_plan_free (fc_plan_run returns FC_ERR_STATE).  Null is ignored. */
 void fc_free(fc_ctx *ctx);
 
 /* Basic facts about a context: key 0 = n (variables or items), 1 = m,
- * 2 = sum of arities, 3 = device ordinal.  Returns -1 for a bad key. */
+ * 2 = sum of arities, 3 = device ordinal, 4 = instances that fit without
+ * reallocating (see fc_reserve), 5 = appends so far.  -1 for a bad key. */
 int64_t fc_info(const fc_ctx *ctx, int32_t key);
+
+/* ---------------------------------------------------- growing a database
+ *
+ * Sec. 5: when the database grows by new instances, the bitmaps take a
+ * simple update and the radix/histogram strategies read D as it stands.  An
+ * append copies the new instances behind the old ones, repacks only the
+ * bitmap words from the old m / 64 on, adds the new instances' state counts
+ * to the marginals and refreshes the entropies, so every later query, score
+ * and plan sees the m + m_new instances, with results identical to loading
+ * the concatenated database at once.
+ *
+ * Plans built before an append refuse to run (FC_ERR_STATE): build new ones.
+ * Storage keeps spare rows and grows by at least half when full (the old
+ * contents are copied; the call then synchronises the context's stream);
+ * fc_reserve sets the room up front.  The appended instances must not make
+ * m reach 2^31 (FC_ERR_RANGE).  Calls on one context must not overlap. */
+
+/* Append m_new instances of a categorical context: D as for fc_load (layout
+ * FC_COL_MAJOR = n x m_new, FC_ROW_MAJOR = m_new x n; where FC_HOST or
+ * FC_DEVICE; the caller keeps ownership).  A state >= its variable's arity
+ * appends nothing and returns FC_ERR_RANGE.  m_new = 0 is a no-op. */
+int fc_append(fc_ctx *ctx, const uint8_t *D, int64_t m_new, int32_t layout, int32_t where);
+
+/* Append m_new transactions to a context from fc_load_bits: bitmaps are
+ * n_items rows of ceil(m_new / 64) uint64 words, bit p of word w of row i set
+ * when new transaction 64 w + p holds item i; bits past m_new are ignored. */
+int fc_append_bits(fc_ctx *ctx, const uint64_t *bitmaps, int64_t m_new, int32_t where);
+
+/* Make room for m_total instances (no effect when there is room already). */
+int fc_reserve(fc_ctx *ctx, int64_t m_total);
 
 /* Per-state marginal counts: out[state_offset(i) + s] = Count(X_i = s), with
  * state_offset(i) = sum of the arities of X_0..X_{i-1} (host buffer of

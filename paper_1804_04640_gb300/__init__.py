@@ -33,7 +33,7 @@ EXPORTS = (
     "fc_selftest_wait_timeout", "fc_count_sorted_noalloc", "fc_autotune_batch",
     "fc_count_assignment_batch", "fc_plan_assignments", "fc_families_count", "fc_score_families",
     "fc_plan_families", "fc_mine_rules", "fc_rules_size", "fc_rules_itemsets", "fc_rules_list",
-    "fc_rules_free",
+    "fc_rules_free", "fc_append", "fc_append_bits", "fc_reserve",
 )
 
 
@@ -109,6 +109,9 @@ def load_library(build_if_missing: bool = False):
         "fc_rules_itemsets": (ctypes.c_int, [_vp, _i32p, _i32p, _i64p]),
         "fc_rules_list": (ctypes.c_int, [_vp, _i64p, ctypes.POINTER(ctypes.c_uint32), _f32p]),
         "fc_rules_free": (None, [_vp]),
+        "fc_append": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]),
+        "fc_append_bits": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32]),
+        "fc_reserve": (ctypes.c_int, [_vp, ctypes.c_int64]),
         "fc_last_error": (ctypes.c_char_p, []),
         "fc_selftest_wait_timeout": (ctypes.c_int, [_vp, ctypes.c_int64]),
         "fc_count_sorted_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _i32p,
@@ -214,6 +217,31 @@ def fc_load_bits(bitmaps, m: int) -> Handle:
     h = Handle(out, lib.fc_free)
     h.arities = np.ones(int(b.shape[0]), dtype=np.int64)
     return h
+
+
+def fc_append(ctx: Handle, D, layout: int = FC_COL_MAJOR):
+    """Append instances (same forms as fc_load's D) to a categorical context."""
+    lib = load_library()
+    if _is_cuda(D):
+        where, d = FC_DEVICE, D
+    else:
+        where, d = FC_HOST, _host(D, np.uint8)
+    m_new = d.shape[1] if layout == FC_COL_MAJOR else d.shape[0]
+    _check(lib.fc_append(ctx.ptr, _ptr(d), int(m_new), layout, where))
+
+
+def fc_append_bits(ctx: Handle, bitmaps, m_new: int):
+    """Append m_new transactions (n_items x ceil(m_new/64) uint64 bitmaps)."""
+    lib = load_library()
+    if _is_cuda(bitmaps):
+        where, b = FC_DEVICE, bitmaps
+    else:
+        where, b = FC_HOST, _host(bitmaps, np.uint64)
+    _check(lib.fc_append_bits(ctx.ptr, _ptr(b), int(m_new), where))
+
+
+def fc_reserve(ctx: Handle, m_total: int):
+    _check(load_library().fc_reserve(ctx.ptr, int(m_total)))
 
 
 def fc_free(ctx: Handle):

@@ -158,6 +158,8 @@ struct fc_ctx {
     bool borrow = false; // set while a synchronous entry point builds its plan
     std::vector<uint32_t> mark;
     uint32_t epoch = 0;
+    uint64_t generation = 0;  // bumped by every append; plans of older generations refuse to run
+    std::vector<fc_plan *> live_plans;  // orphaned (device memory released) if the context goes first
 };
 
 namespace {
@@ -223,6 +225,7 @@ struct fc_plan {
     DBuf fam_tables, fam_jobs;
     int64_t n_jobs = 0;
     int fam_kind = 0;
+    uint64_t generation = 0;  // the context's generation when the plan was built
     size_t upload_bytes = 0;  // host-to-device bytes of the plan's descriptors
     std::vector<GraphEntry> graphs;
 };
@@ -410,11 +413,22 @@ extern "C" int fc_load_bits(fc_ctx **out, const uint64_t *bitmaps, int32_t n_ite
     return FC_OK;
 }
 
+namespace {
+void release_plan(fc_plan *p);
+}  // namespace
+
 extern "C" void fc_free(fc_ctx *c)
 {
     if (!c) return;
     DevGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    // plans still alive keep their host struct for fc_plan_free but lose
+    // their device memory and their context
+    for (fc_plan *p : c->live_plans) {
+        release_plan(p);
+        p->ctx = nullptr;
+    }
+    c->live_plans.clear();
     for (auto &b : c->io) b.release();
     for (auto &b : c->pool) b.release();
     cudaFree(c->d_D);
@@ -427,6 +441,170 @@ extern "C" void fc_free(fc_ctx *c)
     delete c;
 }
 
+// ---------------------------------------------------------------- appends
+//
+// Sec. 5: a database that grows by new instances needs only an update of the
+// bitmaps (and the histogram/radix strategies read D as it stands).  Storage
+// keeps spare rows: D columns are m_pad bytes apart and bitmap rows wstride
+// words apart, both sized for a capacity that grows geometrically, with every
+// byte and bit past m zero.
+
+namespace {
+
+int64_t capacity_rows(const fc_ctx *c)
+{
+    const int64_t bit_rows = c->wstride * 64;
+    return c->transactions ? bit_rows : std::min(c->m_pad, bit_rows);
+}
+
+// Make room for m_need instances (reallocating and copying when needed).
+int grow_storage(fc_ctx *c, int64_t m_need)
+{
+    if (m_need <= capacity_rows(c)) return FC_OK;
+    if (m_need >= ((int64_t)1 << 31)) return fail(FC_ERR_RANGE, "m would reach %lld, must stay < 2^31", (long long)m_need);
+    int64_t cap = std::max<int64_t>(m_need, capacity_rows(c) + capacity_rows(c) / 2);
+    cap = std::min<int64_t>(round_up(cap, kChunkRows), ((int64_t)1 << 31) - 1);
+    cap = std::max(cap, m_need);
+    const int64_t new_pad = round_up(cap, kChunkRows);
+    const int64_t new_wstride = round_up((new_pad + 63) / 64, kChunkWords);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "append");
+    const int64_t rows = c->transactions ? c->R : c->R + 1;
+    uint64_t *nb = nullptr;
+    const size_t bbytes = sizeof(uint64_t) * (size_t)rows * new_wstride;
+    if ((e = cudaMalloc(&nb, bbytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc bitmaps");
+    e = cudaMemsetAsync(nb, 0, bbytes, c->stream);
+    if (e == cudaSuccess && c->words > 0)
+        e = cudaMemcpy2DAsync(nb, sizeof(uint64_t) * new_wstride, c->d_bits, sizeof(uint64_t) * c->wstride,
+                              sizeof(uint64_t) * c->words, rows, cudaMemcpyDeviceToDevice, c->stream);
+    uint8_t *nd = nullptr;
+    if (e == cudaSuccess && !c->transactions) {
+        const size_t dbytes = (size_t)c->n * new_pad;
+        e = cudaMalloc(&nd, dbytes);
+        if (e == cudaSuccess) e = cudaMemsetAsync(nd, 0, dbytes, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(nd, new_pad, c->d_D, c->m_pad, c->m, c->n, cudaMemcpyDeviceToDevice, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(nb);
+        cudaFree(nd);
+        return cuda_fail(e, "grow storage");
+    }
+    cudaFree(c->d_bits);
+    c->d_bits = nb;
+    c->wstride = new_wstride;
+    if (!c->transactions) {
+        cudaFree(c->d_D);
+        c->d_D = nd;
+        c->m_pad = new_pad;
+    }
+    return FC_OK;
+}
+
+// New instance count, marginals and entropies after an append.
+int finish_append(fc_ctx *c, int64_t m_total)
+{
+    c->m = m_total;
+    c->words = (m_total + 63) / 64;
+    c->generation += 1;
+    cudaError_t e = cudaMemcpyAsync(c->marg.data(), c->d_marg, sizeof(int64_t) * c->R, cudaMemcpyDeviceToHost,
+                                    c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "append marginals");
+    if (!c->transactions)
+        for (int i = 0; i < c->n; ++i) {
+            double h = 0.0;
+            for (int s = 0; s < c->arity[i]; ++s) {
+                const double p = (double)c->marg[c->soff[i] + s] / (double)c->m;
+                if (p > 0.0) h -= p * std::log2(p);
+            }
+            c->entropy[i] = h;
+        }
+    return FC_OK;
+}
+
+}  // namespace
+
+extern "C" int fc_reserve(fc_ctx *c, int64_t m_total)
+{
+    if (!c) return fail(FC_ERR_ARG, "fc_reserve: null context");
+    if (m_total < 0) return fail(FC_ERR_ARG, "fc_reserve: m_total < 0");
+    DevGuard g(c->device);
+    return grow_storage(c, m_total);
+}
+
+extern "C" int fc_append(fc_ctx *c, const uint8_t *D, int64_t m_new, int32_t layout, int32_t where)
+{
+    if (!c) return fail(FC_ERR_ARG, "fc_append: null context");
+    if (c->transactions) return fail(FC_ERR_STATE, "fc_append: a context from fc_load_bits takes fc_append_bits");
+    if (m_new < 0) return fail(FC_ERR_ARG, "fc_append: m_new < 0");
+    if (m_new == 0) return FC_OK;
+    if (!D) return fail(FC_ERR_ARG, "fc_append: null D");
+    if (layout != FC_COL_MAJOR && layout != FC_ROW_MAJOR) return fail(FC_ERR_ARG, "fc_append: bad layout");
+    if (where != FC_HOST && where != FC_DEVICE) return fail(FC_ERR_ARG, "fc_append: bad pointer location");
+    DevGuard g(c->device);
+    const int64_t m0 = c->m, m1 = m0 + m_new;
+    int rc = grow_storage(c, m1);
+    if (rc != FC_OK) return rc;
+    const cudaMemcpyKind kind = where == FC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaError_t e;
+    if (layout == FC_COL_MAJOR) {
+        e = cudaMemcpy2DAsync(c->d_D + m0, c->m_pad, D, m_new, m_new, c->n, kind, c->stream);
+    } else {
+        const size_t bytes = (size_t)c->n * m_new;
+        e = c->io[2].ensure(bytes);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->io[2].p, D, bytes, kind, c->stream);
+        if (e == cudaSuccess)
+            e = launch_transpose_rows((const uint8_t *)c->io[2].p, m_new, c->n, c->d_D + m0, c->m_pad, c->stream);
+    }
+    // states are checked before anything visible changes
+    int32_t *bad = c->d_status + 1;
+    int32_t bad_h = 0;
+    if (e == cudaSuccess) e = launch_check_states(c->d_D, c->m_pad, m0, m1, c->n, c->d_arity, bad, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_h, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fc_append");
+    if (bad_h) {
+        cudaMemsetAsync(bad, 0, sizeof(int32_t), c->stream);
+        cudaMemset2DAsync(c->d_D + m0, c->m_pad, 0, m_new, c->n, c->stream);
+        cudaStreamSynchronize(c->stream);
+        return fail(FC_ERR_RANGE, "fc_append: a state is >= its variable's arity; nothing was appended");
+    }
+    e = launch_pack_bits(c->d_D, c->m_pad, m1, c->n, c->d_arity, c->d_soff, c->d_bits, c->wstride, 255, bad,
+                         c->stream, m0 / 64);
+    if (e == cudaSuccess)
+        e = launch_state_counts(c->d_D, c->m_pad, m0, m1, c->n, c->d_arity, c->d_soff, c->d_marg, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fc_append bitmaps");
+    return finish_append(c, m1);
+}
+
+extern "C" int fc_append_bits(fc_ctx *c, const uint64_t *bitmaps, int64_t m_new, int32_t where)
+{
+    if (!c) return fail(FC_ERR_ARG, "fc_append_bits: null context");
+    if (!c->transactions) return fail(FC_ERR_STATE, "fc_append_bits: a categorical context takes fc_append");
+    if (m_new < 0) return fail(FC_ERR_ARG, "fc_append_bits: m_new < 0");
+    if (m_new == 0) return FC_OK;
+    if (!bitmaps) return fail(FC_ERR_ARG, "fc_append_bits: null bitmaps");
+    if (where != FC_HOST && where != FC_DEVICE) return fail(FC_ERR_ARG, "fc_append_bits: bad pointer location");
+    DevGuard g(c->device);
+    const int64_t m0 = c->m, m1 = m0 + m_new;
+    int rc = grow_storage(c, m1);
+    if (rc != FC_OK) return rc;
+    const int64_t n_in = (m_new + 63) / 64;
+    const uint64_t *src = bitmaps;
+    cudaError_t e = cudaSuccess;
+    if (where == FC_HOST) {
+        const size_t bytes = sizeof(uint64_t) * (size_t)c->R * n_in;
+        e = c->io[2].ensure(bytes);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->io[2].p, bitmaps, bytes, cudaMemcpyHostToDevice, c->stream);
+        src = (const uint64_t *)c->io[2].p;
+    }
+    if (e == cudaSuccess) e = launch_append_bits(c->d_bits, c->wstride, c->R, m0, src, n_in, m_new, c->d_marg, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fc_append_bits");
+    return finish_append(c, m1);
+}
+
 extern "C" int64_t fc_info(const fc_ctx *c, int32_t key)
 {
     if (!c) return -1;
@@ -435,6 +613,8 @@ extern "C" int64_t fc_info(const fc_ctx *c, int32_t key)
     case 1: return c->m;
     case 2: return c->R;
     case 3: return c->device;
+    case 4: return capacity_rows(c);
+    case 5: return (int64_t)c->generation;
     default: return -1;
     }
 }
@@ -554,6 +734,8 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     fc_plan *p = new (std::nothrow) fc_plan();
     if (!p) return fail(FC_ERR_OOM, "host allocation failed");
     p->ctx = c;
+    p->generation = c->generation;
+    c->live_plans.push_back(p);
     p->kind = score_kind == kNoScore ? kPlanCount : kPlanScore;
     p->nq = nq;
     p->score_kind = score_kind;
@@ -574,14 +756,14 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
         int32_t k;
         int32_t child;
         if (!get(q, vars, k, child)) {
-            delete p;
+            fc_plan_free(p);
             return FC_ERR_ARG;
         }
         const size_t first = qv.size();
         int32_t k_eff = 0;
         const int64_t cells = describe(c, vars, k, qv, k_eff);
         if (cells < 0) {
-            delete p;
+            fc_plan_free(p);
             return (int)cells;
         }
         QPlan ch = choose(c, qv.data() + first, k_eff, cells, max_cells);
@@ -601,7 +783,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
         if (score_kind == kNoScore) {
             if (user_off) {
                 if (user_off[q + 1] - user_off[q] < cells || user_off[q] < 0) {
-                    delete p;
+                    fc_plan_free(p);
                     return fail(FC_ERR_ARG, "table_off of query %d leaves %lld cells, it needs %lld", q,
                                 (long long)(user_off[q + 1] - user_off[q]), (long long)cells);
                 }
@@ -1013,6 +1195,9 @@ extern "C" int fc_plan_strategies(const fc_plan *p, int32_t *s)
 extern "C" int fc_plan_run(fc_plan *p, void *o0, void *o1, void *o2, void *stream)
 {
     if (!p) return fail(FC_ERR_ARG, "fc_plan_run: null plan");
+    if (!p->ctx) return fail(FC_ERR_STATE, "fc_plan_run: the plan's context was freed");
+    if (p->generation != p->ctx->generation)
+        return fail(FC_ERR_STATE, "fc_plan_run: instances were appended since the plan was built; build a new plan");
     DevGuard g(p->ctx->device);
     if ((p->kind == kPlanCount && p->out_cells > 0 && !o0) || (p->kind == kPlanScore && p->nq > 0 && !o0) ||
         (p->kind == kPlanFamilies && p->n_jobs > 0 && !o0) ||
@@ -1021,15 +1206,17 @@ extern "C" int fc_plan_run(fc_plan *p, void *o0, void *o1, void *o2, void *strea
     return run_plan(p, o0, o1, o2, (cudaStream_t)stream, true);
 }
 
-extern "C" void fc_plan_free(fc_plan *p)
+namespace {
+// Device resources of a plan (its graphs and buffers); the caller has made
+// the plan's device current.
+void release_plan(fc_plan *p)
 {
-    if (!p) return;
-    DevGuard g(p->ctx->device);
     cudaStreamSynchronize(p->ctx->stream);
     for (auto &gr : p->graphs) {
         cudaStreamSynchronize(gr.s);
         cudaGraphExecDestroy(gr.exec);
     }
+    p->graphs.clear();
     p->desc.release();
     p->counters.release();
     p->scratch_tables.release();
@@ -1038,6 +1225,19 @@ extern "C" void fc_plan_free(fc_plan *p)
     p->pairs_meta.release();
     p->fam_tables.release();
     p->fam_jobs.release();
+}
+}  // namespace
+
+extern "C" void fc_plan_free(fc_plan *p)
+{
+    if (!p) return;
+    if (p->ctx) {  // still attached: release here (an orphan was released by fc_free)
+        fc_ctx *c = p->ctx;
+        DevGuard g(c->device);
+        release_plan(p);
+        auto &lp = c->live_plans;
+        lp.erase(std::remove(lp.begin(), lp.end(), p), lp.end());
+    }
     if (p->inner) fc_plan_free(p->inner);
     delete p;
 }
@@ -1204,6 +1404,8 @@ int build_set_plan(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t 
     fc_plan *p = new (std::nothrow) fc_plan();
     if (!p) return fail(FC_ERR_OOM, "host allocation failed");
     p->ctx = c;
+    p->generation = c->generation;
+    c->live_plans.push_back(p);
     p->kind = kPlanSupport;
     p->nq = nq;
     const int64_t n_sub = nq > 0 ? set_off[nq] : 0;
@@ -1410,6 +1612,8 @@ extern "C" int fc_plan_pairs(fc_ctx *c, fc_plan **out)
     fc_plan *p = new (std::nothrow) fc_plan();
     if (!p) return fail(FC_ERR_OOM, "host allocation failed");
     p->ctx = c;
+    p->generation = c->generation;
+    c->live_plans.push_back(p);
     p->kind = kPlanPairs;
     p->nq = 0;
     const int32_t R_pad = (int32_t)round_up(c->R, 256);
@@ -1825,6 +2029,8 @@ extern "C" int fc_plan_families(fc_ctx *c, int32_t nv, const int32_t *vars, int3
     fc_plan *p = new (std::nothrow) fc_plan();
     if (!p) return fail(FC_ERR_OOM, "host allocation failed");
     p->ctx = c;
+    p->generation = c->generation;
+    c->live_plans.push_back(p);
     p->kind = kPlanFamilies;
     p->nq = nv;
     p->fam_kind = kind;
@@ -1836,7 +2042,7 @@ extern "C" int fc_plan_families(fc_ctx *c, int32_t nv, const int32_t *vars, int3
         int rc = fc_plan_count(c, (int32_t)nsets, set_off.data(), set_vars.data(), nullptr, &p->inner);
         c->borrow = saved;
         if (rc != FC_OK) {
-            delete p;
+            fc_plan_free(p);
             return rc;
         }
     }

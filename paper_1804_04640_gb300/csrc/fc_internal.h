@@ -77,10 +77,19 @@ struct CountParams {
 };
 
 // Launchers (each defined in the translation unit holding its kernel).
+// Bitmap words [first_word, ceil(m / 64)) of every (variable, state) row,
+// from the column-major D.
 cudaError_t launch_pack_bits(const uint8_t *D, int64_t m_pad, int64_t m, int32_t n,
                              const int32_t *d_arity, const int32_t *d_soff, uint64_t *bits,
                              int64_t wstride, int32_t max_arity, int32_t *bad_state,
-                             cudaStream_t s);
+                             cudaStream_t s, int64_t first_word = 0);
+// Appends (Sec. 5: a growing database updates the bitmaps in place).
+cudaError_t launch_check_states(const uint8_t *D, int64_t m_pad, int64_t p0, int64_t p1, int32_t n,
+                                const int32_t *d_arity, int32_t *bad_state, cudaStream_t s);
+cudaError_t launch_state_counts(const uint8_t *D, int64_t m_pad, int64_t p0, int64_t p1, int32_t n,
+                                const int32_t *d_arity, const int32_t *d_soff, int64_t *marg, cudaStream_t s);
+cudaError_t launch_append_bits(uint64_t *bits, int64_t wstride, int32_t n_items, int64_t m_old,
+                               const uint64_t *nb, int64_t n_in, int64_t m_new, int64_t *marg, cudaStream_t s);
 cudaError_t launch_bit_popcounts(const uint64_t *bits, int64_t rows, int64_t wstride,
                                  int64_t *counts, cudaStream_t s);
 cudaError_t launch_transpose_rows(const uint8_t *Drow, int64_t m, int32_t n, uint8_t *Dcol,

@@ -4,20 +4,22 @@
 // single root-to-leaf path of Alg. 1, end of Sec. 3.3).
 #include "fc_internal.h"
 
+#include <algorithm>
+
 namespace fc {
 namespace {
 
 // One warp packs 64 consecutive instances of one variable: for every state s
 // the two ballots over (D_i[p] == s) are the low and high halves of word
 // p / 64 of bitmap (i, s).  A state >= r_i sets *bad_state.
-__global__ void pack_bits_kernel(const uint8_t *__restrict__ D, int64_t m_pad, int64_t m,
+__global__ void pack_bits_kernel(const uint8_t *__restrict__ D, int64_t m_pad, int64_t m, int64_t w0,
                                  const int32_t *__restrict__ arity,
                                  const int32_t *__restrict__ soff, uint64_t *__restrict__ bits,
                                  int64_t wstride, int32_t *bad_state)
 {
     const int i = blockIdx.y;
     const int lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t w = w0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w * 64 >= m) return;  // whole warp leaves together
     const int64_t p0 = w * 64 + lane, p1 = p0 + 32;
     const uint8_t *col = D + (int64_t)i * m_pad;
@@ -97,18 +99,136 @@ __global__ void assignment_count_kernel(const uint64_t *__restrict__ bits, int64
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+// Appended instances [p0, p1) of every variable (blockIdx.y strides over the
+// n variables): any state >= its arity sets *bad_state.
+__global__ void check_states_kernel(const uint8_t *__restrict__ D, int64_t m_pad, int64_t p0, int64_t p1,
+                                    int32_t n, const int32_t *__restrict__ arity, int32_t *bad_state)
+{
+    bool bad = false;
+    for (int i = blockIdx.y; i < n; i += gridDim.y) {
+        const uint8_t *col = D + (int64_t)i * m_pad;
+        const int r = arity[i];
+        for (int64_t p = p0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < p1;
+             p += (int64_t)gridDim.x * blockDim.x)
+            bad |= col[p] >= r;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(bad_state, 1);
+}
+
+// Marginal counts of the appended instances [p0, p1) of every variable
+// (blockIdx.y strides over them), added to marg[soff + state] through a
+// shared-memory histogram per block.
+__global__ void state_counts_kernel(const uint8_t *__restrict__ D, int64_t m_pad, int64_t p0, int64_t p1,
+                                    int32_t n, const int32_t *__restrict__ arity, const int32_t *__restrict__ soff,
+                                    unsigned long long *marg)
+{
+    __shared__ unsigned int hist[256];
+    for (int i = blockIdx.y; i < n; i += gridDim.y) {
+        for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0u;
+        __syncthreads();
+        const uint8_t *col = D + (int64_t)i * m_pad;
+        for (int64_t p = p0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < p1;
+             p += (int64_t)gridDim.x * blockDim.x)
+            atomicAdd(&hist[col[p]], 1u);
+        __syncthreads();
+        for (int t = threadIdx.x; t < arity[i]; t += blockDim.x)
+            if (hist[t]) atomicAdd(marg + soff[i] + t, (unsigned long long)hist[t]);
+        __syncthreads();
+    }
+}
+
+// Transactions [m_old, m_old + m_new) of each item (blockIdx.y strides over
+// the items) from `nb` (n_in
+// words per item, bit p of word j = new transaction 64 j + p) merged into the
+// item's bitmap: output word o >= m_old / 64 takes the new bits shifted by
+// m_old % 64, the first one keeps the old bits below that shift.  Bits of the
+// input past m_new are ignored.  The popcount of the new bits is added to
+// marg[item].
+__global__ void append_bits_kernel(uint64_t *__restrict__ bits, int64_t wstride, int32_t n_items, int64_t m_old,
+                                   const uint64_t *__restrict__ nb, int64_t n_in, int64_t m_new,
+                                   unsigned long long *marg)
+{
+    const int64_t w0 = m_old >> 6;
+    const int sh = (int)(m_old & 63);
+    const int64_t n_out = ((m_old + m_new + 63) >> 6) - w0;
+    const int64_t last = (m_new + 63) >> 6;  // input words that hold new bits
+    for (int it = blockIdx.y; it < n_items; it += gridDim.y) {
+        const uint64_t *src = nb + (int64_t)it * n_in;
+        auto word = [&](int64_t j) -> uint64_t {
+            if (j < 0 || j >= last) return 0ull;
+            uint64_t x = src[j];
+            if (j == last - 1 && (m_new & 63)) x &= (~0ull) >> (64 - (m_new & 63));
+            return x;
+        };
+        unsigned long long c = 0;
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_out;
+             j += (int64_t)gridDim.x * blockDim.x) {
+            const uint64_t cur = word(j);
+            c += __popcll(cur);
+            uint64_t v;
+            if (sh == 0) {
+                v = cur;
+            } else {
+                v = (cur << sh) | (word(j - 1) >> (64 - sh));
+                if (j == 0) v |= bits[(int64_t)it * wstride + w0] & ((1ull << sh) - 1ull);
+            }
+            bits[(int64_t)it * wstride + w0 + j] = v;
+        }
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd(marg + it, c);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_pack_bits(const uint8_t *D, int64_t m_pad, int64_t m, int32_t n,
                              const int32_t *d_arity, const int32_t *d_soff, uint64_t *bits,
                              int64_t wstride, int32_t /*max_arity*/, int32_t *bad_state,
-                             cudaStream_t s)
+                             cudaStream_t s, int64_t first_word)
 {
     const int warps = 8;
-    const int64_t words = (m + 63) / 64;
+    const int64_t words = (m + 63) / 64 - first_word;
+    if (words <= 0) return cudaSuccess;
     dim3 grid((unsigned)((words + warps - 1) / warps), (unsigned)n);
-    pack_bits_kernel<<<grid, warps * 32, 0, s>>>(D, m_pad, m, d_arity, d_soff, bits, wstride,
+    pack_bits_kernel<<<grid, warps * 32, 0, s>>>(D, m_pad, m, first_word, d_arity, d_soff, bits, wstride,
                                                  bad_state);
+    return cudaGetLastError();
+}
+
+namespace {
+unsigned append_grid(int64_t units, int threads)
+{
+    const int64_t b = (units + threads - 1) / threads;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 1024));
+}
+unsigned append_rows(int32_t n) { return (unsigned)std::max(1, std::min(n, 65535)); }
+}  // namespace
+
+cudaError_t launch_check_states(const uint8_t *D, int64_t m_pad, int64_t p0, int64_t p1, int32_t n,
+                                const int32_t *d_arity, int32_t *bad_state, cudaStream_t s)
+{
+    if (p1 <= p0) return cudaSuccess;
+    check_states_kernel<<<dim3(append_grid(p1 - p0, 256), append_rows(n)), 256, 0, s>>>(D, m_pad, p0, p1, n,
+                                                                                         d_arity, bad_state);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_counts(const uint8_t *D, int64_t m_pad, int64_t p0, int64_t p1, int32_t n,
+                                const int32_t *d_arity, const int32_t *d_soff, int64_t *marg, cudaStream_t s)
+{
+    if (p1 <= p0) return cudaSuccess;
+    state_counts_kernel<<<dim3(append_grid(p1 - p0, 256), append_rows(n)), 256, 0, s>>>(
+        D, m_pad, p0, p1, n, d_arity, d_soff, reinterpret_cast<unsigned long long *>(marg));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_append_bits(uint64_t *bits, int64_t wstride, int32_t n_items, int64_t m_old,
+                               const uint64_t *nb, int64_t n_in, int64_t m_new, int64_t *marg, cudaStream_t s)
+{
+    if (m_new <= 0) return cudaSuccess;
+    const int64_t n_out = ((m_old + m_new + 63) >> 6) - (m_old >> 6);
+    append_bits_kernel<<<dim3(append_grid(n_out, 256), append_rows(n_items)), 256, 0, s>>>(
+        bits, wstride, n_items, m_old, nb, n_in, m_new, reinterpret_cast<unsigned long long *>(marg));
     return cudaGetLastError();
 }
 
