@@ -118,7 +118,7 @@ int64_t fc_info(const fc_ctx *ctx, int32_t key);
 
 /* ---------------------------------------------------- growing a database
  *
- * Sec. 5: when the database grows by new instances, the bitmaps take a
+ * Sec. 6: when the database grows by new instances, the bitmaps take a
  * simple update and the radix/histogram strategies read D as it stands.  An
  * append copies the new instances behind the old ones, repacks only the
  * bitmap words from the old m / 64 on, adds the new instances' state counts

@@ -443,7 +443,7 @@ extern "C" void fc_free(fc_ctx *c)
 
 // ---------------------------------------------------------------- appends
 //
-// Sec. 5: a database that grows by new instances needs only an update of the
+// Sec. 6: a database that grows by new instances needs only an update of the
 // bitmaps (and the histogram/radix strategies read D as it stands).  Storage
 // keeps spare rows: D columns are m_pad bytes apart and bitmap rows wstride
 // words apart, both sized for a capacity that grows geometrically, with every

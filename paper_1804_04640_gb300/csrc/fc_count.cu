@@ -45,9 +45,63 @@ __device__ __forceinline__ int32_t tab_ld(const int32_t *t, int64_t i)
 }
 
 struct ScoreAcc {
-    Kahan k;
-    double d;
+    Kahan k;         // LL / MDL / MI terms; the N ln(N/N_j) part of BDeu (nats)
+    Kahan r;         // BDeu: remainder terms R'' (see below)
+    double d;        // BDeu: whole remainder terms of large prior counts (a >= 1)
+    int32_t nk, nj;  // BDeu: cells and configurations whose R'' omits -lnGamma(a)
 };
+
+__device__ __forceinline__ ScoreAcc score_zero() { return ScoreAcc{{0.0f, 0.0f}, {0.0f, 0.0f}, 0.0, 0, 0}; }
+
+// Per-query constants of BDeu (Sec. 3.1/4.2 reading: prior a_j = ess/q per
+// parent configuration, a_jk = ess/(r q) per cell).
+struct BdeuK {
+    float ak, aj;      // a_jk, a_j rounded to float (per-term arithmetic)
+    float g1k, g1j;    // lnGamma(1 + a) (small-count branch)
+    double akd, ajd;   // exact a (FP64 branch)
+    double lgk, lgj;   // lnGamma(a): subtracted once per FP32-branch term, by count
+};
+
+// One thread computes the constants; callers broadcast them.
+__device__ BdeuK bdeu_consts(int64_t q, int32_t r, double ess)
+{
+    BdeuK b;
+    b.ajd = ess / (double)q;
+    b.akd = b.ajd / (double)r;
+    b.ak = (float)b.akd;
+    b.aj = (float)b.ajd;
+    b.g1k = (float)lgamma(1.0 + b.akd);
+    b.g1j = (float)lgamma(1.0 + b.ajd);
+    b.lgk = lgamma(b.akd);
+    b.lgj = lgamma(b.ajd);
+    return b;
+}
+
+// c_n = lnGamma(n) - n ln n + n for n = 1..7 (index 0 unused).
+__constant__ float kBdeuSmall[8] = {0.0f, 1.0f, 0.6137056388801094f, 0.39731031455561583f, 0.2465820247484931f,
+                                    0.13086426817744368f, 0.03693492741371607f, -0.0421198313770903f};
+
+// R''(a, n) = lnGamma(a + n) - n ln n + n for a count n >= 1 and a prior a < 1,
+// in FP32 without cancellation:
+//   n < 8:  lnGamma(1 + a) + c_n + sum_{i=1}^{n-1} log1p(a / i)
+//           (Gamma(n + a) = Gamma(1 + a) prod_{i=1}^{n-1} (i + a));
+//   n >= 8: n log1p(a/n) + (a - 1/2) ln(n + a) - a + ln(2 pi)/2
+//           + 1/(12 z) - 1/(360 z^3), z = n + a (Stirling's series; the next
+//           term is below 2.5e-8 for z >= 8).
+__device__ __forceinline__ float bdeu_rem(float a, float g1, int64_t n)
+{
+    if (n < 8) {
+        float t = g1 + kBdeuSmall[n];
+        for (int i = 1; i < (int)n; ++i) t += log1pf(a / (float)i);
+        return t;
+    }
+    const float nf = (float)n, z = nf + a, iz = 1.0f / z;
+    float t = nf * log1pf(a / nf);
+    t += (a - 0.5f) * logf(z);
+    t += 0.91893853320467274f - a;
+    t += iz * (0.083333333333333333f - iz * iz * 0.0027777777777777778f);
+    return t;
+}
 
 // Parent configuration j of a table laid out parents-major, child-last:
 // its r cells start at j * r, one apart.
@@ -63,19 +117,23 @@ struct DenseRows {
 //   LL  = sum N_ijk log2(N_ijk / N_ij) = -(1/ln2) sum N_ijk log1p((N_ij - N_ijk) / N_ijk):
 //         every term has the same sign and the integer difference is exact.
 //   MDL = -LL + (log2 m / 2)(r - 1) q.
-//   BDeu: lgamma differences accumulated in FP64.
+//   BDeu = sum_j [sum_k G(a_jk, N_ijk) - G(a_j, N_ij)], G(a, n) = lnGamma(a+n) - lnGamma(a).
+//         Writing G(a, n) = (n ln n - n) + R(a, n), the (n ln n - n) parts of a
+//         configuration sum to sum_k N_ijk ln(N_ijk / N_ij) (the -n terms cancel
+//         since sum_k N_ijk = N_ij), which takes the LL form above in nats; the
+//         remainders R are O(log n) each and are summed in FP32 as
+//         R'' = R + lnGamma(a) (bdeu_rem), the lnGamma(a) being added back once
+//         per query in FP64 by count.  Priors a >= 1 (tiny tables) take R in
+//         FP64 with lgamma.  No FP64 transcendental runs per cell.
 //   MI  = (1/ln2) sum_jk p_j p_k [(1 + x_jk) ln(1 + x_jk) - x_jk] over all cells
 //         with p_j, p_k > 0, x_jk = (N_jk m - N_j N_k) / (N_j N_k) with an exact
 //         int64 numerator; this equals the usual sum because sum p_j p_k x_jk = 0,
 //         and every term is >= 0.
 template <bool kGlobal, class Rows>
 __device__ ScoreAcc score_rows(const int32_t *tab, const Rows &rows, int64_t q, int32_t r, int kind,
-                               const int64_t *marg_child, int64_t m, double ess, int64_t j0, int64_t jstep)
+                               const int64_t *marg_child, int64_t m, const BdeuK &bk, int64_t j0, int64_t jstep)
 {
-    ScoreAcc acc{{0.0f, 0.0f}, 0.0};
-    const double aj = ess / (double)q, ajk = ess / ((double)r * (double)q);
-    const double lg_aj = kind == kBDeu ? lgamma(aj) : 0.0;
-    const double lg_ajk = kind == kBDeu ? lgamma(ajk) : 0.0;
+    ScoreAcc acc = score_zero();
     const int64_t cs = rows.step();
     for (int64_t j = j0; j < q; j += jstep) {
         const int64_t b = rows.base(j);
@@ -88,10 +146,22 @@ __device__ ScoreAcc score_rows(const int32_t *tab, const Rows &rows, int64_t q, 
                 if (n > 0) kahan_add(acc.k, (float)n * log1pf((float)(nij - n) / (float)n));
             }
         } else if (kind == kBDeu) {
-            acc.d += lg_aj - lgamma(aj + (double)nij);
             for (int k = 0; k < r; ++k) {
                 const int32_t n = tab_ld<kGlobal>(tab, b + k * cs);
-                if (n > 0) acc.d += lgamma(ajk + (double)n) - lg_ajk;
+                if (n <= 0) continue;
+                kahan_add(acc.k, -(float)n * log1pf((float)(nij - n) / (float)n));
+                if (bk.akd < 1.0) {
+                    kahan_add(acc.r, bdeu_rem(bk.ak, bk.g1k, n));
+                    ++acc.nk;
+                } else {
+                    acc.d += lgamma(bk.akd + (double)n) - bk.lgk - ((double)n * log((double)n) - (double)n);
+                }
+            }
+            if (bk.ajd < 1.0) {
+                kahan_add(acc.r, -bdeu_rem(bk.aj, bk.g1j, nij));
+                ++acc.nj;
+            } else {
+                acc.d -= lgamma(bk.ajd + (double)nij) - bk.lgj - ((double)nij * log((double)nij) - (double)nij);
             }
         } else {  // kMI
             const float pj = (float)nij / (float)m;
@@ -108,31 +178,89 @@ __device__ ScoreAcc score_rows(const int32_t *tab, const Rows &rows, int64_t q, 
     return acc;
 }
 
-template <bool kGlobal>
-__device__ ScoreAcc score_part(const int32_t *tab, int32_t cells, int32_t r, int kind,
-                               const int64_t *marg_child, int64_t m, double ess, int64_t j0,
-                               int64_t step)
+__device__ __forceinline__ void acc_merge(ScoreAcc &a, const ScoreAcc &b)
 {
-    return score_rows<kGlobal>(tab, DenseRows{r}, cells / r, r, kind, marg_child, m, ess, j0, step);
+    kahan_merge(a.k, b.k);
+    kahan_merge(a.r, b.r);
+    a.d += b.d;
+    a.nk += b.nk;
+    a.nj += b.nj;
 }
 
 __device__ __forceinline__ void warp_merge(ScoreAcc &acc)
 {
     for (int o = 16; o > 0; o >>= 1) {
-        Kahan other{__shfl_xor_sync(kFull, acc.k.s, o), __shfl_xor_sync(kFull, acc.k.c, o)};
-        kahan_merge(acc.k, other);
-        acc.d += __shfl_xor_sync(kFull, acc.d, o);
+        ScoreAcc other;
+        other.k = Kahan{__shfl_xor_sync(kFull, acc.k.s, o), __shfl_xor_sync(kFull, acc.k.c, o)};
+        other.r = Kahan{__shfl_xor_sync(kFull, acc.r.s, o), __shfl_xor_sync(kFull, acc.r.c, o)};
+        other.d = __shfl_xor_sync(kFull, acc.d, o);
+        other.nk = __shfl_xor_sync(kFull, acc.nk, o);
+        other.nj = __shfl_xor_sync(kFull, acc.nj, o);
+        acc_merge(acc, other);
     }
 }
 
-__device__ float score_finish(const ScoreAcc &t, int kind, int64_t m, int32_t r, int64_t q)
+__device__ float score_finish(const ScoreAcc &t, int kind, int64_t m, int32_t r, int64_t q, const BdeuK &bk)
 {
     const float sum = __fsub_rn(t.k.s, t.k.c);
     if (kind == kLL) return -sum * kInvLn2;
     if (kind == kMDL)
         return (float)((double)sum * (double)kInvLn2 + 0.5 * log2((double)m) * (double)(r - 1) * (double)q);
-    if (kind == kBDeu) return (float)t.d;
+    if (kind == kBDeu)
+        return (float)((double)sum + (double)__fsub_rn(t.r.s, t.r.c) + t.d - (double)t.nk * bk.lgk +
+                       (double)t.nj * bk.lgj);
     return sum * kInvLn2;
+}
+
+// BDeu constants of a (q, r) score computed by thread 0 of the block and
+// shared (uniform branch on kind).
+__device__ BdeuK block_bdeu_consts(int kind, int64_t q, int32_t r, double ess)
+{
+    __shared__ BdeuK s_bk;
+    BdeuK bk{};
+    if (kind == kBDeu) {
+        if (threadIdx.x == 0) s_bk = bdeu_consts(q, r, ess);
+        __syncthreads();
+        bk = s_bk;
+        __syncthreads();
+    }
+    return bk;
+}
+
+// The same for one warp (lane 0 computes, the others receive).
+__device__ BdeuK warp_bdeu_consts(int kind, int64_t q, int32_t r, double ess)
+{
+    BdeuK bk{};
+    if (kind == kBDeu) {
+        if ((threadIdx.x & 31) == 0) bk = bdeu_consts(q, r, ess);
+        bk.ak = __shfl_sync(kFull, bk.ak, 0);
+        bk.aj = __shfl_sync(kFull, bk.aj, 0);
+        bk.g1k = __shfl_sync(kFull, bk.g1k, 0);
+        bk.g1j = __shfl_sync(kFull, bk.g1j, 0);
+        bk.akd = __shfl_sync(kFull, bk.akd, 0);
+        bk.ajd = __shfl_sync(kFull, bk.ajd, 0);
+        bk.lgk = __shfl_sync(kFull, bk.lgk, 0);
+        bk.lgj = __shfl_sync(kFull, bk.lgj, 0);
+    }
+    return bk;
+}
+
+// Block-wide reduction of per-thread accumulators; thread 0 returns the score.
+__device__ float block_finish(ScoreAcc acc, ScoreAcc *red, int kind, int64_t m, int32_t r, int64_t q,
+                              const BdeuK &bk)
+{
+    warp_merge(acc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    float out = 0.0f;
+    if (threadIdx.x == 0) {
+        ScoreAcc t = score_zero();
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc_merge(t, red[w]);
+        out = score_finish(t, kind, m, r, q, bk);
+    }
+    __syncthreads();
+    return out;
 }
 
 // Whole block; the result is returned in thread 0.
@@ -140,31 +268,22 @@ template <bool kGlobal>
 __device__ float block_score(const int32_t *tab, int32_t cells, int32_t r, int kind,
                              const int64_t *marg_child, int64_t m, double ess, ScoreAcc *red)
 {
-    ScoreAcc acc = score_part<kGlobal>(tab, cells, r, kind, marg_child, m, ess, threadIdx.x, blockDim.x);
-    warp_merge(acc);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) red[warp] = acc;
-    __syncthreads();
-    float out = 0.0f;
-    if (threadIdx.x == 0) {
-        ScoreAcc t{{0.0f, 0.0f}, 0.0};
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            kahan_merge(t.k, red[w].k);
-            t.d += red[w].d;
-        }
-        out = score_finish(t, kind, m, r, cells / r);
-    }
-    __syncthreads();
-    return out;
+    const int64_t q = cells / r;
+    const BdeuK bk = block_bdeu_consts(kind, q, r, ess);
+    const ScoreAcc acc = score_rows<kGlobal>(tab, DenseRows{r}, q, r, kind, marg_child, m, bk, threadIdx.x,
+                                             blockDim.x);
+    return block_finish(acc, red, kind, m, r, q, bk);
 }
 
 // One warp; the result is returned in lane 0.
 __device__ float warp_score(const int32_t *tab, int32_t cells, int32_t r, int kind,
                             const int64_t *marg_child, int64_t m, double ess)
 {
-    ScoreAcc acc = score_part<true>(tab, cells, r, kind, marg_child, m, ess, threadIdx.x & 31, 32);
+    const int64_t q = cells / r;
+    const BdeuK bk = warp_bdeu_consts(kind, q, r, ess);
+    ScoreAcc acc = score_rows<true>(tab, DenseRows{r}, q, r, kind, marg_child, m, bk, threadIdx.x & 31, 32);
     warp_merge(acc);
-    return score_finish(acc, kind, m, r, cells / r);
+    return score_finish(acc, kind, m, r, q, bk);
 }
 
 // ------------------------------------------------------------ bitmap (Alg. 1)
@@ -618,13 +737,16 @@ struct FamilyRows {
     int32_t ar[kMaxFamily];
     int64_t st[kMaxFamily];
     int64_t cstep;
+    // 32-bit division: a joint table has fewer than 2^31 cells (int32 offsets).
     __device__ __forceinline__ int64_t base(int64_t j) const
     {
+        uint32_t u = (uint32_t)j;
         int64_t b = 0;
         for (int t = np - 1; t >= 0; --t) {
-            const int64_t d = j % ar[t];
-            j /= ar[t];
-            b += d * st[t];
+            const uint32_t a = (uint32_t)ar[t];
+            const uint32_t d = u % a;
+            u /= a;
+            b += (int64_t)d * st[t];
         }
         return b;
     }
@@ -663,21 +785,11 @@ __global__ void family_score_kernel(const FamilyJob *__restrict__ jobs, int64_t 
         }
         const int32_t rc = ar[job.child_pos];
         rows.cstep = st[job.child_pos];
-        ScoreAcc acc = score_rows<true>(tables + job.table_off, rows, q, rc, kind,
-                                        marg + soff[job.vars[job.child_pos]], m, ess, threadIdx.x, blockDim.x);
-        warp_merge(acc);
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        if (lane == 0) s_red[warp] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            ScoreAcc t{{0.0f, 0.0f}, 0.0};
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                kahan_merge(t.k, s_red[w].k);
-                t.d += s_red[w].d;
-            }
-            scores[job.slot] = score_finish(t, kind, m, rc, q);
-        }
-        __syncthreads();
+        const BdeuK bk = block_bdeu_consts(kind, q, rc, ess);
+        const ScoreAcc acc = score_rows<true>(tables + job.table_off, rows, q, rc, kind,
+                                              marg + soff[job.vars[job.child_pos]], m, bk, threadIdx.x, blockDim.x);
+        const float s = block_finish(acc, s_red, kind, m, rc, q, bk);
+        if (threadIdx.x == 0) scores[job.slot] = s;
     }
 }
 

@@ -83,7 +83,7 @@ cudaError_t launch_pack_bits(const uint8_t *D, int64_t m_pad, int64_t m, int32_t
                              const int32_t *d_arity, const int32_t *d_soff, uint64_t *bits,
                              int64_t wstride, int32_t max_arity, int32_t *bad_state,
                              cudaStream_t s, int64_t first_word = 0);
-// Appends (Sec. 5: a growing database updates the bitmaps in place).
+// Appends (Sec. 6: a growing database updates the bitmaps in place).
 cudaError_t launch_check_states(const uint8_t *D, int64_t m_pad, int64_t p0, int64_t p1, int32_t n,
                                 const int32_t *d_arity, int32_t *bad_state, cudaStream_t s);
 cudaError_t launch_state_counts(const uint8_t *D, int64_t m_pad, int64_t p0, int64_t p1, int32_t n,

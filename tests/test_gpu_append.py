@@ -1,4 +1,4 @@
-"""GPU parity of a growing database (Sec. 5: instances appended during
+"""GPU parity of a growing database (Sec. 6: instances appended during
 processing update the bitmaps; the radix/histogram path reads D as it stands).
 
 After any sequence of appends every query must equal the oracle on the

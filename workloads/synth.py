@@ -244,7 +244,7 @@ CONFIGS = {
     # database, parent sets of at most 4 (Sec. 4.2 query stream)
     "families": dict(m=1_000_000, nv=20, max_parents=4, seed=4),
     # streaming appends: the BN-score database loaded with 1e6 instances, then
-    # grown by blocks of 1e6 instances (Sec. 5)
+    # grown by blocks of 1e6 instances (Sec. 6)
     "append": dict(m=1_000_000, block=1_000_000),
     # bottom-up rule mining over the (variable, state) items of the BN-score
     # database: support > 0.2, confidence > 0.3, itemsets of at most 6 items
