@@ -616,7 +616,7 @@ def run_gpu(args, rank: int, world: int):
         if strategies is not None:
             cfg["strategies"] = dict(zip(["bitmap", "hist", "gatomic", "sort", "marginal"], strategies))
             cfg["cost_model_fs"] = {k: fc.fc_get_option(ctx, k) for k in
-                                    ("bitmap_cost", "hist_cost_row", "hist_cost_var")}
+                                    ("bitmap_cost", "bitmap_chunk_cost", "small_cost", "hist_cost_row", "hist_cost_var")}
         cores = os.cpu_count() or 1
         cpu = None
         if world == 1 and not args.no_cpu_baseline:

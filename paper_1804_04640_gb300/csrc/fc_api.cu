@@ -124,6 +124,10 @@ struct Options {
     int64_t hist_cost_row = 143;
     int64_t hist_cost_var = 124;
     int64_t flush_cost = 160;
+    // register-blocked bitmap path (2-3 variables of arity 2..5): per work
+    // unit (cell or state row) per 4096-row chunk
+    int64_t small_cost = 12000;
+    int32_t bitmap_small = 1;
     int32_t stage_slots = 16;         // bitmap rows a warp stages per chunk
     int32_t bitmap_threads = 256;
     int32_t support_warps = 16;
@@ -202,8 +206,9 @@ struct fc_plan {
     Item *d_items = nullptr;
     int32_t *d_qlist = nullptr;
     int32_t n_items = 0, n_qlist = 0, n_counters = 0;
-    int32_t *d_bq = nullptr;
-    int32_t n_bq = 0, tasks_per_query = 1, bm_grid = 0, bm_threads = 0, stage_slots = 0;
+    BTask *d_btasks = nullptr;
+    int32_t n_btasks = 0, bm_grid = 0, bm_threads = 0, stage_slots = 0;
+    int32_t small_paths = 1;
     bool zero_tables = false;
     int64_t table_buf_cells = 0;  // cells of the buffer the kernel writes
     int score_kind = kNoScore;
@@ -686,6 +691,25 @@ void entropy_order(const fc_ctx *c, QVar *v, int k)
 }
 
 // Staged slots of the query in entropy order; the ordered copy goes to o.
+// Queries the bitmap kernel counts on its register-blocked path (no tree
+// walk): 2 variables, or 3 whose last two in entropy order, of arities 2..5;
+// `o` is in entropy order.  Work units per 4096-row chunk: cells plus the
+// state rows loaded.
+bool small_ok(const QVar *o, int k)
+{
+    auto ok = [](int r) { return r >= 2 && r <= 5; };
+    if (k == 2) return ok(o[0].arity) && ok(o[1].arity);
+    if (k == 3) return ok(o[1].arity) && ok(o[2].arity);
+    return false;
+}
+
+double small_units(const QVar *o, int k)
+{
+    if (k == 2) return (double)o[0].arity * o[1].arity + o[0].arity + o[1].arity;
+    const double rb = o[1].arity, rc = o[2].arity;
+    return (double)o[0].arity * (1.0 + rb + rc + rb * rc);
+}
+
 bool bitmap_ok(const fc_ctx *c, const QVar *v, int k, QVar *o)
 {
     if (k < 1 || k > kMaxBitmapK) return false;
@@ -707,7 +731,9 @@ QPlan choose(const fc_ctx *c, const QVar *v, int k, int64_t cells, int32_t smem_
     const bool bm = bitmap_ok(c, v, k, ord);
     const double nodes = bm ? dfs_nodes(ord, k) : 0.0;
     const double hist = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) + flush;
-    const double bitmap = bm ? chunks * ((double)o.bitmap_chunk_cost + nodes * o.bitmap_cost) + flush : 1e300;
+    double bitmap = bm ? chunks * ((double)o.bitmap_chunk_cost + nodes * o.bitmap_cost) + flush : 1e300;
+    if (bm && o.bitmap_small && small_ok(ord, k))
+        bitmap = chunks * ((double)o.bitmap_chunk_cost + small_units(ord, k) * o.small_cost) + flush;
     const double gatomic = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) * 2.0 + (double)cells * 4.0;
     int32_t s = o.strategy;
     if (k == 0) s = fits ? FC_STRAT_HIST : FC_STRAT_GATOMIC;
@@ -838,20 +864,41 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     items.reserve(order.size());
     for (auto &x : order) items.push_back(x.second);
     p->n_items = (int32_t)items.size();
-    // bitmap queries: warp tasks of a few 4096-row chunks, heaviest queries first
+    // bitmap queries: warp tasks of consecutive 4096-row chunks, heaviest
+    // queries first.  A query gets tasks in proportion to its estimated cost
+    // (about four tasks' worth of work per warp of the launch), each of at
+    // least kMinTaskChunks chunks, so that light queries are not cut into
+    // tasks whose fixed costs (dispatch, one reduction and atomic per cell)
+    // outweigh their work.
     std::stable_sort(bmo.begin(), bmo.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
-    std::vector<int32_t> bq;
-    for (auto &x : bmo) bq.push_back(x.second);
-    p->n_bq = (int32_t)bq.size();
+    std::vector<BTask> btasks;
     p->bm_threads = std::max(32, std::min(1024, o.bitmap_threads / 32 * 32));
     p->stage_slots = o.stage_slots;
-    if (p->n_bq > 0) {
+    p->small_paths = o.bitmap_small;
+    if (!bmo.empty()) {
+        constexpr int64_t kMinTaskChunks = 4;
         p->bm_grid = c->num_sms * bitmap_ctas_per_sm(p->bm_threads, p->stage_slots);
         const int64_t warps = (int64_t)p->bm_grid * (p->bm_threads / 32);
-        const int64_t want = (8 * warps + p->n_bq - 1) / p->n_bq;
-        p->tasks_per_query = (int32_t)std::max<int64_t>(1, std::min<int64_t>(nchunks, want));
-        for (int32_t q : bq) qh[q].nparts = (int16_t)std::min<int64_t>(p->tasks_per_query, 32767);
+        double total = 0.0;
+        for (auto &x : bmo) total += x.first;
+        const double unit = std::max(total / (4.0 * (double)warps), 1e-30);
+        const int64_t max_tasks = std::max<int64_t>(1, std::min<int64_t>(nchunks / kMinTaskChunks, 32767));
+        for (auto &x : bmo) {
+            const int32_t q = x.second;
+            // a 3-variable register-blocked query splits by the first
+            // variable's state as well (one pass over the chunks per state)
+            const QVar *ov = qv.data() + qh[q].var_off;
+            const int32_t passes = (p->small_paths && qh[q].k == 3 && small_ok(ov, 3)) ? ov[0].arity : 0;
+            const double per = x.first / std::max(1, passes);
+            const int64_t t = std::max<int64_t>(1, std::min<int64_t>(max_tasks, (int64_t)std::ceil(per / unit)));
+            qh[q].nparts = (int16_t)std::min<int64_t>(t * std::max(1, passes), 32767);
+            for (int32_t s0 = passes > 0 ? 0 : -1; s0 < std::max(passes, 0); ++s0)
+                for (int64_t part = 0; part < t; ++part)
+                    btasks.push_back(
+                        BTask{q, (int32_t)(nchunks * part / t), (int32_t)(nchunks * (part + 1) / t), s0});
+        }
     }
+    p->n_btasks = (int32_t)btasks.size();
 
     // tables that must exist in global memory for score plans
     if (score_kind != kNoScore) {
@@ -885,7 +932,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     const size_t b_qv = sizeof(QVar) * std::max<size_t>(qv.size(), 1);
     const size_t b_it = sizeof(Item) * std::max<size_t>(items.size(), 1);
     const size_t b_ql = sizeof(int32_t) * std::max<size_t>(qlist.size(), 1);
-    const size_t b_bq = sizeof(int32_t) * std::max<size_t>(bq.size(), 1);
+    const size_t b_bq = sizeof(BTask) * std::max<size_t>(btasks.size(), 1);
     const size_t o_qv = round_up(b_qh, 256), o_it = o_qv + round_up(b_qv, 256), o_ql = o_it + round_up(b_it, 256);
     const size_t o_bq = o_ql + round_up(b_ql, 256);
     const size_t total = o_bq + round_up(b_bq, 256);
@@ -894,7 +941,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     std::memcpy(host.data() + o_qv, qv.data(), sizeof(QVar) * qv.size());
     std::memcpy(host.data() + o_it, items.data(), sizeof(Item) * items.size());
     std::memcpy(host.data() + o_ql, qlist.data(), sizeof(int32_t) * qlist.size());
-    std::memcpy(host.data() + o_bq, bq.data(), sizeof(int32_t) * bq.size());
+    std::memcpy(host.data() + o_bq, btasks.data(), sizeof(BTask) * btasks.size());
     cudaError_t e = plan_buf(c, p->desc, 0, total);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->desc.p, host.data(), total, cudaMemcpyHostToDevice, c->stream);
     p->upload_bytes = total;
@@ -926,7 +973,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     p->d_qv = (QVar *)(d + o_qv);
     p->d_items = (Item *)(d + o_it);
     p->d_qlist = (int32_t *)(d + o_ql);
-    p->d_bq = (int32_t *)(d + o_bq);
+    p->d_btasks = (BTask *)(d + o_bq);
     for (auto &j : p->sort_jobs) j.d_vars = p->d_qv + qh[j.q].var_off;
     *out = p;
     return FC_OK;
@@ -943,7 +990,7 @@ cudaError_t enqueue_count(fc_plan *p, int32_t *tables, float *scores, cudaStream
         e = cudaMemsetAsync(tab, 0, sizeof(int32_t) * p->table_buf_cells, s);
         if (e != cudaSuccess) return e;
     }
-    if (p->n_items > 0 || p->n_bq > 0) {
+    if (p->n_items > 0 || p->n_btasks > 0) {
         CountParams P{};
         P.D = c->d_D;
         P.m_pad = c->m_pad;
@@ -957,9 +1004,8 @@ cudaError_t enqueue_count(fc_plan *p, int32_t *tables, float *scores, cudaStream
         P.next_item = (int32_t *)p->counters.p;
         P.next_task = (int32_t *)p->counters.p + 1;
         P.tickets = (int32_t *)p->counters.p + 2;
-        P.bq = p->d_bq;
-        P.n_bq = p->n_bq;
-        P.tasks_per_query = p->tasks_per_query;
+        P.btasks = p->d_btasks;
+        P.n_btasks = p->n_btasks;
         P.stage_slots = p->stage_slots;
         P.tables = tab;
         P.scores = scores;
@@ -968,7 +1014,8 @@ cudaError_t enqueue_count(fc_plan *p, int32_t *tables, float *scores, cudaStream
         P.write_tables = p->kind == kPlanCount ? 1 : 0;
         P.smem_cells = p->smem_cells;
         P.hist_copies = c->opt.hist_copies;
-        if (p->n_bq > 0) {
+        P.small_paths = p->small_paths;
+        if (p->n_btasks > 0) {
             e = launch_bitmap(P, p->bm_grid, p->bm_threads, s);
             if (e != cudaSuccess) return e;
         }
@@ -1150,7 +1197,7 @@ int64_t plan_launches(const fc_plan *p)
     switch (p->kind) {
     case kPlanCount:
     case kPlanScore:
-        return (p->n_bq > 0) + (p->n_items > 0) + (int64_t)p->sort_jobs.size() +
+        return (p->n_btasks > 0) + (p->n_items > 0) + (int64_t)p->sort_jobs.size() +
                (p->kind == kPlanScore && p->n_qlist > 0);
     case kPlanSupport: return p->nq > 0 ? (p->sp.full_only ? 1 : 2) : 0;
     case kPlanPairs: return 2;
@@ -1709,6 +1756,8 @@ const OptDesc kOpts[] = {
     {"hist_cost_row", &Options::hist_cost_row, nullptr, 0, (int64_t)1 << 40},
     {"hist_cost_var", &Options::hist_cost_var, nullptr, 0, (int64_t)1 << 40},
     {"flush_cost", &Options::flush_cost, nullptr, 0, (int64_t)1 << 40},
+    {"small_cost", &Options::small_cost, nullptr, 0, (int64_t)1 << 40},
+    {"bitmap_small", nullptr, &Options::bitmap_small, 0, 1},
     {"stage_slots", nullptr, &Options::stage_slots, 1, 64},
     {"bitmap_threads", nullptr, &Options::bitmap_threads, 32, 1024},
     {"support_warps", nullptr, &Options::support_warps, 1, 32},
@@ -1858,6 +1907,7 @@ extern "C" int fc_autotune(fc_ctx *c, int32_t budget_ms)
         for (int s = 0; s < 2; ++s) {
             c->opt = saved;
             c->opt.strategy = s;
+            c->opt.bitmap_small = 0;  // the tree-walk fit; the small path is fitted below
             fc_plan *p = nullptr;
             if (fc_plan_count(c, nq, off.data(), vars.data(), nullptr, &p) != FC_OK) {
                 c->opt = saved;
@@ -1898,6 +1948,56 @@ extern "C" int fc_autotune(fc_ctx *c, int32_t budget_ms)
         c->opt.bitmap_chunk_cost = (int64_t)std::max(0.0, a);
         c->opt.bitmap_cost = (int64_t)std::max(1.0, b);
     }
+    // register-blocked path: batches of 2- and 3-variable queries over
+    // variables of arity 2..5, timed with the bitmap strategy forced;
+    // small_cost = (time - chunk costs) / (chunks x work units)
+    std::vector<int32_t> small_vars;
+    for (int v = 0; v < c->n; ++v)
+        if (c->arity[v] >= 2 && c->arity[v] <= 5) small_vars.push_back(v);
+    double num = 0.0, den = 0.0;
+    for (int k = 2; k <= 3 && (int)small_vars.size() >= k; ++k) {
+        std::vector<int32_t> off{0}, vars;
+        double units = 0.0;
+        const int ns = (int)small_vars.size();
+        std::vector<int32_t> pool(small_vars);
+        for (int q = 0; q < nq; ++q) {
+            for (int t = 0; t < k; ++t) {
+                const int j = t + (int)(lcg(seed) % (ns - t));
+                std::swap(pool[t], pool[j]);
+                vars.push_back(pool[t]);
+            }
+            off.push_back((int32_t)vars.size());
+            std::vector<QVar> qv;
+            int32_t ke = 0;
+            describe(c, vars.data() + off[q], k, qv, ke);
+            entropy_order(c, qv.data(), ke);
+            units += small_units(qv.data(), ke);
+        }
+        c->opt.strategy = FC_STRAT_BITMAP;
+        fc_plan *p = nullptr;
+        const int rc = fc_plan_count(c, nq, off.data(), vars.data(), nullptr, &p);
+        c->opt.strategy = saved.strategy;
+        if (rc != FC_OK) {
+            c->opt = saved;
+            return rc;
+        }
+        bool all = true;
+        for (int32_t q = 0; q < nq; ++q) all = all && p->strategy[q] == FC_STRAT_BITMAP;
+        DBuf out;
+        if (out.ensure(sizeof(int32_t) * std::max<int64_t>(p->out_cells, 1)) != cudaSuccess) {
+            fc_plan_free(p);
+            c->opt = saved;
+            return fail(FC_ERR_OOM, "autotune buffer");
+        }
+        if (all) {
+            const double tf = time_plan(p, out.p, 3) * 1e12;
+            num += std::max(0.0, tf - (double)nq * chunks * (double)c->opt.bitmap_chunk_cost);
+            den += units * chunks;
+        }
+        out.release();
+        fc_plan_free(p);
+    }
+    if (den > 0.0) c->opt.small_cost = (int64_t)std::max(1.0, num / den);
     return FC_OK;
 }
 
@@ -1919,6 +2019,7 @@ extern "C" int fc_autotune_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, 
         c->opt = base;
         c->opt.bitmap_cost = sc < 0 ? ((int64_t)1 << 50) : (int64_t)std::max(1.0, base.bitmap_cost * sc);
         c->opt.bitmap_chunk_cost = sc < 0 ? ((int64_t)1 << 50) : (int64_t)(base.bitmap_chunk_cost * sc);
+        c->opt.small_cost = sc < 0 ? ((int64_t)1 << 50) : (int64_t)std::max(1.0, base.small_cost * sc);
         fc_plan *p = nullptr;
         if ((rc = fc_plan_count(c, nq, var_off, vars, nullptr, &p)) != FC_OK) {
             c->opt = base;

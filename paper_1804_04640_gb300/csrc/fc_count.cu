@@ -374,30 +374,183 @@ __device__ __forceinline__ void bitmap_task(const CountParams &P, const QVar *qv
     }
 }
 
-__global__ void __launch_bounds__(256) bitmap_kernel(const CountParams P)
+// Register-blocked bitmap counts for small tables (no tree walk): every
+// cell is one AND + popcount of two words per lane per 4096-instance chunk,
+// counted in registers over the whole task and reduced across the warp once
+// per cell at the end.  Dense small tables gain nothing from zero-support
+// pruning, so the walk's per-node control and per-leaf atomics are dropped.
+// Two variables of arities RA x RB:
+template <int RA, int RB>
+__device__ __noinline__ void small2_task(const CountParams &P, const QVar *qv, int64_t c0, int64_t c1,
+                                         int32_t *tab, int lane)
+{
+    const uint64_t *row_a = P.bits + (int64_t)qv[0].soff * P.wstride + 2 * lane;
+    const uint64_t *row_b = P.bits + (int64_t)qv[1].soff * P.wstride + 2 * lane;
+    unsigned cnt[RA][RB];
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+        for (int b = 0; b < RB; ++b) cnt[a][b] = 0u;
+    // two chunks per iteration: twice the loads in flight per warp
+    constexpr int U = (RA + RB <= 8) ? 2 : 1;
+    int64_t c = c0;
+    for (; c + U <= c1; c += U) {
+        ulonglong2 xa[U][RA], xb[U][RB];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t w = (c + u) * kChunkWords;
+#pragma unroll
+            for (int a = 0; a < RA; ++a)
+                xa[u][a] = __ldg(reinterpret_cast<const ulonglong2 *>(row_a + (int64_t)a * P.wstride + w));
+#pragma unroll
+            for (int b = 0; b < RB; ++b)
+                xb[u][b] = __ldg(reinterpret_cast<const ulonglong2 *>(row_b + (int64_t)b * P.wstride + w));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int a = 0; a < RA; ++a)
+#pragma unroll
+                for (int b = 0; b < RB; ++b)
+                    cnt[a][b] += (unsigned)(__popcll(xa[u][a].x & xb[u][b].x) + __popcll(xa[u][a].y & xb[u][b].y));
+    }
+    for (; c < c1; ++c) {
+        const int64_t w = c * kChunkWords;
+        ulonglong2 xa[RA], xb[RB];
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+            xa[a] = __ldg(reinterpret_cast<const ulonglong2 *>(row_a + (int64_t)a * P.wstride + w));
+#pragma unroll
+        for (int b = 0; b < RB; ++b)
+            xb[b] = __ldg(reinterpret_cast<const ulonglong2 *>(row_b + (int64_t)b * P.wstride + w));
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+#pragma unroll
+            for (int b = 0; b < RB; ++b)
+                cnt[a][b] += (unsigned)(__popcll(xa[a].x & xb[b].x) + __popcll(xa[a].y & xb[b].y));
+    }
+    const int sa = qv[0].stride, sb = qv[1].stride;
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            const unsigned v = __reduce_add_sync(kFull, cnt[a][b]);
+            if (lane == 0 && v) atomicAdd(&tab[a * sa + b * sb], (int)v);
+        }
+}
+
+// Three variables: the first (any arity) is walked state by state, the other
+// two (RB x RC) are register-blocked.
+template <int RB, int RC>
+__device__ __noinline__ void small3_task(const CountParams &P, const QVar *qv, int64_t c0, int64_t c1,
+                                         int s0, int32_t *tab, int lane)
+{
+    const uint64_t *row_a = P.bits + (int64_t)qv[0].soff * P.wstride + 2 * lane;
+    const uint64_t *row_b = P.bits + (int64_t)qv[1].soff * P.wstride + 2 * lane;
+    const uint64_t *row_c = P.bits + (int64_t)qv[2].soff * P.wstride + 2 * lane;
+    const int sa = qv[0].stride, sb = qv[1].stride, sc = qv[2].stride;
+    const int a_lo = s0 >= 0 ? s0 : 0, a_hi = s0 >= 0 ? s0 + 1 : qv[0].arity;
+    for (int a = a_lo; a < a_hi; ++a) {
+        if (P.marg[qv[0].soff + a] == 0) continue;  // a state absent from D
+        unsigned cnt[RB][RC];
+#pragma unroll
+        for (int b = 0; b < RB; ++b)
+#pragma unroll
+            for (int cc = 0; cc < RC; ++cc) cnt[b][cc] = 0u;
+        for (int64_t c = c0; c < c1; ++c) {
+            const int64_t w = c * kChunkWords;
+            const ulonglong2 xa = __ldg(reinterpret_cast<const ulonglong2 *>(row_a + (int64_t)a * P.wstride + w));
+            ulonglong2 xb[RB], xc[RC];
+#pragma unroll
+            for (int b = 0; b < RB; ++b)
+                xb[b] = __ldg(reinterpret_cast<const ulonglong2 *>(row_b + (int64_t)b * P.wstride + w));
+#pragma unroll
+            for (int cc = 0; cc < RC; ++cc)
+                xc[cc] = __ldg(reinterpret_cast<const ulonglong2 *>(row_c + (int64_t)cc * P.wstride + w));
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                const uint64_t px = xa.x & xb[b].x, py = xa.y & xb[b].y;
+#pragma unroll
+                for (int cc = 0; cc < RC; ++cc)
+                    cnt[b][cc] += (unsigned)(__popcll(px & xc[cc].x) + __popcll(py & xc[cc].y));
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < RB; ++b)
+#pragma unroll
+            for (int cc = 0; cc < RC; ++cc) {
+                const unsigned v = __reduce_add_sync(kFull, cnt[b][cc]);
+                if (lane == 0 && v) atomicAdd(&tab[a * sa + b * sb + cc * sc], (int)v);
+            }
+    }
+}
+
+// Arities the register-blocked paths are compiled for.
+constexpr int kSmallLo = 2, kSmallHi = 5;
+__device__ __forceinline__ bool small_arity(int r) { return r >= kSmallLo && r <= kSmallHi; }
+
+template <int K>
+__device__ bool small_dispatch(const CountParams &P, const QVar *qv_in, int64_t c0, int64_t c1, int s0,
+                               int32_t *tab, int lane)
+{
+    // the two blocked variables are symmetric (each carries its own stride),
+    // so they are ordered by arity and only RX <= RY is compiled
+    QVar qv[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) qv[t] = qv_in[t];
+    if (qv[K - 2].arity > qv[K - 1].arity) {
+        const QVar tmp = qv[K - 2];
+        qv[K - 2] = qv[K - 1];
+        qv[K - 1] = tmp;
+    }
+    const int r1 = qv[K - 2].arity, r2 = qv[K - 1].arity;
+    if (!small_arity(r1) || !small_arity(r2)) return false;
+#define FC_SMALL_CASE(X, Y)                                                         \
+    case (X - kSmallLo) * 4 + (Y - kSmallLo):                                       \
+        if constexpr (K == 2) small2_task<X, Y>(P, qv, c0, c1, tab, lane);          \
+        else small3_task<X, Y>(P, qv, c0, c1, s0, tab, lane);                       \
+        return true;
+    switch ((r1 - kSmallLo) * 4 + (r2 - kSmallLo)) {
+        FC_SMALL_CASE(2, 2) FC_SMALL_CASE(2, 3) FC_SMALL_CASE(2, 4) FC_SMALL_CASE(2, 5)
+        FC_SMALL_CASE(3, 3) FC_SMALL_CASE(3, 4) FC_SMALL_CASE(3, 5)
+        FC_SMALL_CASE(4, 4) FC_SMALL_CASE(4, 5)
+        FC_SMALL_CASE(5, 5)
+    }
+#undef FC_SMALL_CASE
+    return false;
+}
+
+__global__ void __launch_bounds__(256, 2) bitmap_kernel(const CountParams P)
 {
     extern __shared__ __align__(16) ulonglong2 stage_all[];
     __shared__ QVar s_qv[kBitmapWarps][kMaxBitmapK];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ulonglong2 *stage = stage_all + (size_t)warp * P.stage_slots * 32;
-    const int64_t nchunks = (P.m + kChunkRows - 1) / kChunkRows;
-    const int64_t n_tasks = (int64_t)P.n_bq * P.tasks_per_query;
+    const int64_t n_tasks = P.n_btasks;
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(P.next_task, 1);
         t = __shfl_sync(kFull, t, 0);
         if (t >= n_tasks) break;
-        const int qi = t / P.tasks_per_query, part = t % P.tasks_per_query;
-        const int q = P.bq[qi];
+        const BTask bt = P.btasks[t];
+        const int q = bt.q;
         const QHead h = P.qh[q];
         const int k = h.k;
         if (lane < k) s_qv[warp][lane] = P.qv[h.var_off + lane];
         __syncwarp();
-        const int64_t c0 = nchunks * part / P.tasks_per_query;
-        const int64_t c1 = nchunks * (part + 1) / P.tasks_per_query;
+        const int64_t c0 = bt.c0, c1 = bt.c1;
         int32_t *tab = P.tables + h.table_off;
         const QVar *qv = s_qv[warp];
-        switch (k) {
+        bool done = false;
+        if (P.small_paths) {
+            if (k == 2) done = small_dispatch<2>(P, qv, c0, c1, -1, tab, lane);
+            else if (k == 3) done = small_dispatch<3>(P, qv, c0, c1, bt.s0, tab, lane);
+        }
+        // a state-split task that did not take the register-blocked path
+        // (cannot happen: planner and kernel test the same arities) leaves
+        // the whole walk to the task of state 0
+        if (!done && bt.s0 > 0) done = true;
+        if (!done) switch (k) {
         case 1: bitmap_task<1>(P, qv, c0, c1, stage, tab, lane); break;
         case 2: bitmap_task<2>(P, qv, c0, c1, stage, tab, lane); break;
         case 3: bitmap_task<3>(P, qv, c0, c1, stage, tab, lane); break;
@@ -411,7 +564,7 @@ __global__ void __launch_bounds__(256) bitmap_kernel(const CountParams P)
         if (h.score_kind != kNoScore) {
             __threadfence();
             int last = 0;
-            if (lane == 0) last = atomicAdd(&P.tickets[q], 1) == P.tasks_per_query - 1;
+            if (lane == 0) last = atomicAdd(&P.tickets[q], 1) == h.nparts - 1;
             last = __shfl_sync(kFull, last, 0);
             if (last) {
                 __threadfence();

@@ -48,6 +48,15 @@ struct Item {
     int32_t part;
 };
 
+// One warp task of the bitmap strategy: query q over 4096-row chunks
+// [c0, c1); s0 >= 0 restricts a 3-variable register-blocked query to state
+// s0 of its first variable (-1: every state).
+struct BTask {
+    int32_t q;
+    int32_t c0, c1;
+    int32_t s0;
+};
+
 struct CountParams {
     const uint8_t *D;        // n columns of m_pad bytes
     int64_t m_pad;
@@ -67,11 +76,12 @@ struct CountParams {
     int32_t write_tables;    // 1: every cell is written (nparts == 1 queries store zeros too)
     int32_t smem_cells;      // int32 cells of dynamic shared memory for tables
     int32_t hist_copies;     // maximum table copies for the histogram strategy
-    int32_t pad;
-    // bitmap strategy: warp-granular tasks (query, chunk range)
-    const int32_t *bq;       // bitmap queries in processing order
-    int32_t n_bq;
-    int32_t tasks_per_query;
+    int32_t small_paths;     // 1: bitmap queries of 2-3 small variables skip the tree walk
+    // bitmap strategy: warp-granular tasks (query, chunk range); a query's
+    // tasks are consecutive and number qh[q].nparts
+    const BTask *btasks;
+    int32_t n_btasks;
+    int32_t pad2;
     int32_t *next_task;      // warp task counter, zero before the launch
     int32_t stage_slots;     // state bitmaps a warp stages (levels 1..k-1)
 };

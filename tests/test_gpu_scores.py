@@ -1,5 +1,6 @@
-"""GPU parity of the score reductions (Sec. 3.1): FP32 scores (FP64 BDeu
-accumulation) within 1e-5 relative of the FP64 oracle, counts exact."""
+"""GPU parity of the score reductions (Sec. 3.1): FP32 scores (BDeu as an LL
+term plus FP32 remainders, FP64 only for per-query constants) within 1e-5
+relative of the FP64 oracle, counts exact."""
 import concurrent.futures as cf
 import os
 
@@ -61,6 +62,35 @@ def test_bdeu_ess_and_row_splits(ess):
         got = fc.fc_score_batch(ctx, child, po, pa, kind, ess)
         want = oracle_scores(orc, child, parents, kind, ess, range(4))
         assert_close(got, want, kind)
+
+
+@pytest.mark.parametrize("m", [1, 7, 8, 9, 1000, 1_000_003])
+def test_bdeu_adversarial_tables(m):
+    """Tables where the BDeu remainder terms matter most: deterministic and
+    near-deterministic children (the LL part is ~0), counts at the switch
+    between the small-count and Stirling branches, priors from 1e-3 to 100
+    (a >= 1 takes the FP64 branch)."""
+    rng = np.random.default_rng(m)
+    n = 8
+    D = np.zeros((n, m), dtype=np.uint8)
+    D[0] = rng.integers(0, 4, size=m)                  # parent
+    D[1] = D[0] % 2                                     # deterministic child of 0
+    D[2] = np.where(rng.random(m) < 0.999, D[0] % 3, 2 - D[0] % 3)  # near-deterministic
+    D[3] = 0                                            # constant
+    D[4] = rng.integers(0, 2, size=m)
+    D[5] = (D[4] + D[0]) % 2                            # deterministic given {0, 4}
+    D[6] = rng.integers(0, 3, size=m)
+    D[7] = rng.integers(0, 4, size=m)
+    ar = [4, 2, 3, 1, 2, 2, 3, 4]
+    ctx = fc.fc_load(D, ar)
+    orc = oracle.DB(D, ar)
+    child = [1, 2, 3, 5, 5, 1, 6, 7, 0]
+    parents = [[0], [0], [0], [0, 4], [0, 4, 6, 7], [], [0, 1, 2, 4, 5], [6], [1, 2, 4, 5, 6, 7]]
+    po, pa = fc.pack_lists(parents)
+    for ess in (1e-3, 1.0, 10.0, 100.0):
+        got = fc.fc_score_batch(ctx, child, po, pa, "bdeu", ess)
+        want = oracle_scores(orc, child, parents, "bdeu", ess, range(len(child)))
+        assert_close(got, want, f"bdeu ess={ess}")
 
 
 def test_bn_score_workload_full_size_sampled():
