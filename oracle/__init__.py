@@ -66,6 +66,9 @@ def _load():
             lib.orc_support_rules.argtypes = [_u64p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                               _i32p, ctypes.c_int32, _i64p, _i64p, _f64p]
             lib.orc_support_rules.restype = ctypes.c_int
+            lib.orc_support_splits.argtypes = [_u64p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                               _i32p, ctypes.c_int32, _i64p, _i64p, _f64p]
+            lib.orc_support_splits.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -144,3 +147,22 @@ def support_rules(bitmaps: np.ndarray, m: int, items):
     if rc != 0:
         raise OracleError(f"orc_support_rules failed with {rc}")
     return int(supp[0]), sub[:k].copy(), conf[:k].copy()
+
+
+def support_splits(bitmaps: np.ndarray, m: int, items):
+    """(supp(S), [supp(A)], [conf(A => S minus A)]) for every antecedent mask
+    A = 1 .. 2^k - 2 over the positions of ``items``."""
+    lib = _load()
+    b = np.ascontiguousarray(np.asarray(bitmaps, dtype=np.uint64))
+    it = np.ascontiguousarray(np.asarray(items, dtype=np.int32))
+    k = len(it)
+    n = max((1 << k) - 2, 1)
+    supp = np.zeros(1, dtype=np.int64)
+    sub = np.zeros(n, dtype=np.int64)
+    conf = np.zeros(n, dtype=np.float64)
+    rc = lib.orc_support_splits(_p(b, _u64p), b.shape[1], m, b.shape[0], _p(it, _i32p), k,
+                                _p(supp, _i64p), _p(sub, _i64p), _p(conf, _f64p))
+    if rc != 0:
+        raise OracleError(f"orc_support_splits failed with {rc}")
+    nn = max((1 << k) - 2, 0)
+    return int(supp[0]), sub[:nn].copy(), conf[:nn].copy()

@@ -212,3 +212,32 @@ int orc_support_rules(const uint64_t *bitmaps, int64_t words, int64_t m, int32_t
     }
     return 0;
 }
+
+/* Every split of an itemset S of k items into a non-empty antecedent A and a
+ * non-empty consequent S \ A (Sec. 4.3: rules A => S \ A with support
+ * supp(S) and confidence supp(S) / supp(A)).  Antecedents are numbered by
+ * their bit mask over the positions of `items` (bit t = item t in A),
+ * mask = 1 .. 2^k - 2; for each, sub[mask - 1] = supp(A) counted by scanning
+ * the transactions, and conf[mask - 1] = supp(S) / supp(A), 0 when supp(A)
+ * = 0.  supp[0] = supp(S).  k <= 20. */
+int orc_support_splits(const uint64_t *bitmaps, int64_t words, int64_t m, int32_t n_items,
+                       const int32_t *items, int32_t k, int64_t *supp, int64_t *sub, double *conf)
+{
+    if (!bitmaps || !supp || k < 0 || k > 20 || m < 0 || words * 64 < m || (k > 0 && !items)) return -1;
+    for (int32_t t = 0; t < k; ++t)
+        if (items[t] < 0 || items[t] >= n_items) return -1;
+    supp[0] = support_skip(bitmaps, words, m, items, k, -1);
+    const int64_t full = ((int64_t)1 << k) - 1;
+    for (int64_t mask = 1; mask < full; ++mask) {
+        int64_t count = 0;
+        for (int64_t p = 0; p < m; ++p) {
+            int all = 1;
+            for (int32_t t = 0; t < k && all; ++t)
+                if (((mask >> t) & 1) && !holds(bitmaps, words, items[t], p)) all = 0;
+            count += all;
+        }
+        sub[mask - 1] = count;
+        conf[mask - 1] = count > 0 ? (double)supp[0] / (double)count : 0.0;
+    }
+    return 0;
+}

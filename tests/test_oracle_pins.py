@@ -228,6 +228,31 @@ def test_support_rules_brute_force():
         assert oracle.support_rules(bits, m, [i])[0] == int(holds[i].sum())
 
 
+def test_support_splits_brute_force():
+    """Every antecedent split of an itemset against transaction lists; the
+    single-consequent masks agree with the leave-one-out supports."""
+    m = 150
+    bits = zipf_transaction_bitmaps(10, m, 1.1, 4.0, 37)
+    holds = np.unpackbits(bits.view(np.uint8), axis=1, bitorder="little")[:, :m].astype(bool)
+    trans = [set(np.nonzero(holds[:, p])[0].tolist()) for p in range(m)]
+    rng = np.random.default_rng(4)
+    for _ in range(25):
+        k = int(rng.integers(0, 6))
+        items = [int(x) for x in rng.choice(10, size=k, replace=False)]
+        supp, sub, conf = oracle.support_splits(bits, m, items)
+        assert supp == sum(1 for T in trans if set(items) <= T)
+        assert len(sub) == max((1 << k) - 2, 0)
+        for mask in range(1, (1 << k) - 1):
+            A = {items[t] for t in range(k) if mask >> t & 1}
+            s = sum(1 for T in trans if A <= T)
+            assert sub[mask - 1] == s and supp <= s
+            assert conf[mask - 1] == (supp / s if s else 0.0)
+        if k >= 2:
+            s1, loo, _ = oracle.support_rules(bits, m, items)
+            full = (1 << k) - 1
+            assert [sub[(full ^ (1 << t)) - 1] for t in range(k)] == loo.tolist()
+
+
 # ---- association-rule miner (Sec. 4.3) -------------------------------------
 
 def _rules_cases():
