@@ -163,7 +163,7 @@ def make_workload(name: str, m: int | None = None, nq: int | None = None):
         return {"db": db, "child": child, "parents": parents}
     if name == "pairs":
         return {"db": config_database(name, c["m"])}
-    if name == "support":
+    if name in ("support", "splits"):
         bits = zipf_transaction_bitmaps(c["n_items"], c["m"], c["zipf_s"], c["mean_len"], c["seed"])
         probs = zipf_item_probs(c["n_items"], c["zipf_s"], c["mean_len"])
         sets = weighted_itemsets(c["n_items"], c["nq"], c["k"][0], c["k"][1], probs, c["seed"])
@@ -205,8 +205,10 @@ def describe(name: str, w) -> dict:
         n = w["db"].n
         return {"workload": f"pairs: n={n}, m={w['db'].m}, all {n * (n - 1) // 2} pairwise tables + MI",
                 "n": n, "m": w["db"].m, "sum_arity": int(w["db"].arities.sum())}
-    return {"workload": f"support: {len(w['bits'])} items, m={w['m']}, {len(w['sets'])} itemsets of "
-                        f"{c['k'][0]}-{c['k'][1]} items, supports + rule confidences",
+    what = ("supports + supports and confidences of every antecedent split (2^k - 2 rules each)"
+            if name == "splits" else "supports + single-consequent rule confidences")
+    return {"workload": f"{name}: {len(w['bits'])} items, m={w['m']}, {len(w['sets'])} itemsets of "
+                        f"{c['k'][0]}-{c['k'][1]} items, {what}",
             "n_items": len(w["bits"]), "m": w["m"], "queries": len(w["sets"])}
 
 
@@ -308,8 +310,9 @@ def oracle_rate(name: str, w, seconds: float, cores: int):
             sample = f"{units} pair tables + MI by row scan, {cores} threads"
         else:
             bits, m, sets = w["bits"], w["m"], w["sets"]
+            ofn = oracle.support_splits if name == "splits" else oracle.support_rules
             def fn(s):
-                return oracle.support_rules(bits, m, s)
+                return ofn(bits, m, s)
             t0 = time.perf_counter()
             i = 0
             while time.perf_counter() - t0 < seconds:
@@ -317,7 +320,8 @@ def oracle_rate(name: str, w, seconds: float, cores: int):
                 list(ex.map(fn, chunk))
                 units += len(chunk)
                 i += len(chunk)
-            sample = f"{units} itemsets (support + k leave-one-out supports) by transaction scan, {cores} threads"
+            what = "every antecedent split" if name == "splits" else "support + k leave-one-out supports"
+            sample = f"{units} itemsets ({what}) by transaction scan, {cores} threads"
     dt = time.perf_counter() - t0
     return units / dt, sample
 
@@ -325,7 +329,7 @@ def oracle_rate(name: str, w, seconds: float, cores: int):
 METRIC = "count queries/s (exact full contingency tables, batched persistent launch)"
 UNITS = {"tiny": "queries/s", "random": "queries/s", "large": "queries/s", "scores": "queries/s",
          "pairs": "pairs/s", "support": "itemsets/s", "assign": "assignments/s", "families": "families/s",
-         "rules": "candidate itemsets/s", "append": "instances/s"}
+         "rules": "candidate itemsets/s", "append": "instances/s", "splits": "itemsets/s"}
 
 
 def run_reference(args, rank: int, world: int):
@@ -492,10 +496,12 @@ def run_gpu(args, rank: int, world: int):
     else:
         ctx = fc.fc_load_bits(w["bits"], w["m"])
         so, it = fc.pack_lists(w["sets"])
-        plan = fc.fc_plan_support(ctx, so, it)
+        splits = name == "splits"
+        plan = fc.fc_plan_support_splits(ctx, so, it) if splits else fc.fc_plan_support(ctx, so, it)
+        n_out = fc.fc_plan_size(plan, 3)
         outs = (torch.empty(len(w["sets"]), dtype=torch.int32, device="cuda"),
-                torch.empty(len(it), dtype=torch.int32, device="cuda"),
-                torch.empty(len(it), dtype=torch.float32, device="cuda"))
+                torch.empty(n_out, dtype=torch.int32, device="cuda"),
+                torch.empty(n_out, dtype=torch.float32, device="cuda"))
         units = len(w["sets"])
         alg_bytes = int(len(it)) * (w["m"] // 8)
         pins = tuple(torch.empty(o.numel(), dtype=o.dtype).pin_memory() for o in outs)
@@ -503,11 +509,14 @@ def run_gpu(args, rank: int, world: int):
         d2h = sum(4 * o.numel() for o in outs)
 
         def e2e_call():
-            fc.fc_support_batch(ctx, so, it, out=pins)
+            if splits:
+                fc.fc_support_splits_batch(ctx, so, it, out=pins)
+            else:
+                fc.fc_support_batch(ctx, so, it, out=pins)
         strategies = None
 
     # bytes the step's kernels read from the database (columns or state bitmaps)
-    if name == "support":
+    if name in ("support", "splits"):
         resident_bytes = int(np.asarray(w["bits"]).nbytes)
     elif name == "assign":
         resident_bytes = int(w["db"].arities.sum()) * ((w["db"].m + 63) // 64) * 8

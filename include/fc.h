@@ -235,6 +235,18 @@ int64_t fc_pairs_cells(const fc_ctx *ctx);
 int fc_support_batch(fc_ctx *ctx, int32_t nq, const int32_t *set_off, const int32_t *items,
                      int32_t *support, int32_t *sub_support, float *confidence);
 
+/* Every split of each itemset into antecedent A and consequent S \ A
+ * (Sec. 4.3, rules A => S \ A): for itemset q of k items (k <= 16),
+ * sub_support and confidence hold 2^k - 2 entries starting at
+ * sum over earlier itemsets of (2^k' - 2) (none for k <= 1), one per
+ * antecedent mask 1 .. 2^k - 2 in increasing order (bit t = item t of the
+ * itemset's list is in A): sub_support = supp(A), confidence =
+ * supp(S) / supp(A) (0 when supp(A) = 0).  support[q] = supp(S).  Host
+ * buffers; sub_support and confidence may be NULL.  Applies to fc_load_bits
+ * contexts.  Errors as fc_support_batch, FC_ERR_SIZE for k > 16. */
+int fc_support_splits_batch(fc_ctx *ctx, int32_t nq, const int32_t *set_off, const int32_t *items,
+                            int32_t *support, int32_t *sub_support, float *confidence);
+
 /* ----------------------------------------------- association-rule mining
  *
  * Bottom-up search of the itemset lattice (Sec. 4.3): level 1 is every item,
@@ -305,6 +317,12 @@ int fc_plan_score(fc_ctx *ctx, int32_t nq, const int32_t *child, const int32_t *
 /* Plan of a support batch (arguments as fc_support_batch). */
 int fc_plan_support(fc_ctx *ctx, int32_t nq, const int32_t *set_off, const int32_t *items,
                     fc_plan **out);
+
+/* Plan of an all-splits support batch (arguments as fc_support_splits_batch);
+ * fc_plan_run takes the outputs of a support plan, fc_plan_size(plan, 3) is
+ * the number of split entries. */
+int fc_plan_support_splits(fc_ctx *ctx, int32_t nq, const int32_t *set_off, const int32_t *items,
+                           fc_plan **out);
 
 /* Plan of an assignment-count batch (arguments as fc_count_assignment_batch);
  * fc_plan_run writes nq int32 counts to out0. */

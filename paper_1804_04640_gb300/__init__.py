@@ -33,7 +33,8 @@ EXPORTS = (
     "fc_selftest_wait_timeout", "fc_count_sorted_noalloc", "fc_autotune_batch",
     "fc_count_assignment_batch", "fc_plan_assignments", "fc_families_count", "fc_score_families",
     "fc_plan_families", "fc_mine_rules", "fc_rules_size", "fc_rules_itemsets", "fc_rules_list",
-    "fc_rules_free", "fc_append", "fc_append_bits", "fc_reserve",
+    "fc_rules_free", "fc_append", "fc_append_bits", "fc_reserve", "fc_support_splits_batch",
+    "fc_plan_support_splits",
 )
 
 
@@ -103,6 +104,8 @@ def load_library(build_if_missing: bool = False):
                                             ctypes.c_double, ctypes.POINTER(_vp)]),
         "fc_count_assignment_batch": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p, _i32p, _i64p]),
         "fc_plan_assignments": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p, _i32p, ctypes.POINTER(_vp)]),
+        "fc_support_splits_batch": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p, _vp, _vp, _vp]),
+        "fc_plan_support_splits": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p, ctypes.POINTER(_vp)]),
         "fc_mine_rules": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.POINTER(_vp)]),
         "fc_rules_size": (ctypes.c_int64, [_vp, ctypes.c_int32]),
@@ -426,6 +429,38 @@ def fc_support_batch(ctx: Handle, set_off, items, out=None):
     s, sub, conf = out
     _check(lib.fc_support_batch(ctx.ptr, nq, _ptr(so, _i32p), _ptr(it, _i32p), _ptr(s), _ptr(sub), _ptr(conf)))
     return s, sub, conf
+
+
+def split_offsets(set_off) -> np.ndarray:
+    """Start of each itemset's 2^k - 2 split entries (nq + 1 int64)."""
+    so = np.asarray(set_off, dtype=np.int64)
+    k = np.diff(so)
+    n = np.where(k >= 2, (np.int64(1) << np.minimum(k, 62)) - 2, 0)
+    return np.concatenate([[0], np.cumsum(n)]).astype(np.int64)
+
+
+def fc_support_splits_batch(ctx: Handle, set_off, items, out=None):
+    """(support, sub_support, confidence) over every antecedent split."""
+    lib = load_library()
+    so, it = _host(set_off, np.int32), _host(items, np.int32)
+    nq = len(so) - 1
+    ns = int(split_offsets(so)[-1])
+    if out is None:
+        out = (np.zeros(max(nq, 1), dtype=np.int32), np.zeros(max(ns, 1), dtype=np.int32),
+               np.zeros(max(ns, 1), dtype=np.float32))
+    s, sub, conf = out
+    _check(lib.fc_support_splits_batch(ctx.ptr, nq, _ptr(so, _i32p), _ptr(it, _i32p), _ptr(s), _ptr(sub),
+                                       _ptr(conf)))
+    return s, sub, conf
+
+
+def fc_plan_support_splits(ctx: Handle, set_off, items) -> Handle:
+    lib = load_library()
+    so, it = _host(set_off, np.int32), _host(items, np.int32)
+    out = _vp()
+    _check(lib.fc_plan_support_splits(ctx.ptr, len(so) - 1, _ptr(so, _i32p), _ptr(it, _i32p),
+                                      ctypes.byref(out)))
+    return Handle(out, lib.fc_plan_free, ctx)
 
 
 def fc_plan_count(ctx: Handle, var_off, vars_, table_off=None) -> Handle:

@@ -1408,12 +1408,30 @@ cudaError_t enqueue_support(fc_plan *p, int32_t *support, int32_t *sub, float *c
 }  // namespace
 
 namespace {
-int build_set_plan(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *items, int full_only,
+int build_set_plan(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *items, int mode,
                    fc_plan **out);
+}  // namespace
+
+namespace {
+int plan_itemsets(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *items, int mode, fc_plan **out);
 }  // namespace
 
 extern "C" int fc_plan_support(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *items,
                                fc_plan **out)
+{
+    return plan_itemsets(c, nq, set_off, items, 0, out);
+}
+
+extern "C" int fc_plan_support_splits(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *items,
+                                      fc_plan **out)
+{
+    return plan_itemsets(c, nq, set_off, items, 2, out);
+}
+
+namespace {
+// Validated itemset plan: mode 0 = supports with leave-one-out sets, 2 = every
+// antecedent split.
+int plan_itemsets(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *items, int mode, fc_plan **out)
 {
     if (!c || !out || (nq > 0 && !set_off)) return fail(FC_ERR_ARG, "fc_plan_support: null argument");
     *out = nullptr;
@@ -1421,10 +1439,11 @@ extern "C" int fc_plan_support(fc_ctx *c, int32_t nq, const int32_t *set_off, co
     if (nq < 0) return fail(FC_ERR_ARG, "nq < 0");
     DevGuard g(c->device);
     if (nq > 0 && set_off[0] != 0) return fail(FC_ERR_ARG, "set_off[0] must be 0");
+    const int32_t kmax = mode == 2 ? kMaxSplitK : kMaxK;
     for (int32_t q = 0; q < nq; ++q) {
         const int32_t a = set_off[q], b = set_off[q + 1];
         if (b < a) return fail(FC_ERR_ARG, "set_off must be non-decreasing");
-        if (b - a > kMaxK) return fail(FC_ERR_SIZE, "itemset %d has %d items, at most %d supported", q, b - a, kMaxK);
+        if (b - a > kmax) return fail(FC_ERR_SIZE, "itemset %d has %d items, at most %d supported", q, b - a, kmax);
         if (b > a && !items) return fail(FC_ERR_ARG, "null items");
         if (++c->epoch == 0) {
             std::fill(c->mark.begin(), c->mark.end(), 0u);
@@ -1437,17 +1456,20 @@ extern "C" int fc_plan_support(fc_ctx *c, int32_t nq, const int32_t *set_off, co
             c->mark[it] = c->epoch;
         }
     }
-    return build_set_plan(c, nq, set_off, items, 0, out);
+    return build_set_plan(c, nq, set_off, items, mode, out);
 }
+}  // namespace
 
 namespace {
 
 // A plan over sets of bitmap rows: itemset supports with their leave-one-out
-// supports (full_only = 0), or the support of each set alone (full_only = 1,
-// specific-assignment counts).  set_off[0] == 0 and the rows are valid.
-int build_set_plan(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *items, int full_only,
+// supports (mode 0), the support of each set alone (mode 1, specific-
+// assignment counts), or the supports of every antecedent split (mode 2).
+// set_off[0] == 0 and the rows are valid.
+int build_set_plan(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *items, int mode,
                    fc_plan **out)
 {
+    const int full_only = mode == 1;
     fc_plan *p = new (std::nothrow) fc_plan();
     if (!p) return fail(FC_ERR_OOM, "host allocation failed");
     p->ctx = c;
@@ -1457,6 +1479,15 @@ int build_set_plan(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t 
     p->nq = nq;
     const int64_t n_sub = nq > 0 ? set_off[nq] : 0;
     p->n_sub = full_only ? 0 : n_sub;
+    std::vector<int64_t> split_off;
+    if (mode == 2) {
+        split_off.assign(nq + 1, 0);
+        for (int32_t q = 0; q < nq; ++q) {
+            const int k = set_off[q + 1] - set_off[q];
+            split_off[q + 1] = split_off[q] + std::max<int64_t>(((int64_t)1 << k) - 2, 0);
+        }
+        p->n_sub = split_off[nq];
+    }
     const Options &o = c->opt;
     // itemsets in decreasing size so that the heavy ones start first
     std::vector<int32_t> order(nq);
@@ -1466,18 +1497,20 @@ int build_set_plan(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t 
     });
     const size_t b_off = sizeof(int32_t) * (nq + 1), b_it = sizeof(int32_t) * std::max<int64_t>(n_sub, 1);
     const size_t o_it = round_up(b_off, 256), o_ord = o_it + round_up(b_it, 256);
-    const size_t total = o_ord + round_up(sizeof(int32_t) * std::max(nq, 1), 256);
+    const size_t o_spl = o_ord + round_up(sizeof(int32_t) * std::max(nq, 1), 256);
+    const size_t total = o_spl + (mode == 2 ? round_up(sizeof(int64_t) * (nq + 1), 256) : 0);
     std::vector<uint8_t> host(total, 0);
     if (nq > 0) {
         std::memcpy(host.data(), set_off, b_off);
         if (n_sub > 0) std::memcpy(host.data() + o_it, items, sizeof(int32_t) * n_sub);
         std::memcpy(host.data() + o_ord, order.data(), sizeof(int32_t) * nq);
     }
+    if (mode == 2) std::memcpy(host.data() + o_spl, split_off.data(), sizeof(int64_t) * (nq + 1));
     cudaError_t e = plan_buf(c, p->desc, 0, total);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->desc.p, host.data(), total, cudaMemcpyHostToDevice, c->stream);
     p->upload_bytes = total;
     if (e == cudaSuccess) e = plan_buf(c, p->counters, 1, 16);
-    if (e == cudaSuccess) e = plan_buf(c, p->scratch_tables, 2, sizeof(int32_t) * std::max<int64_t>(n_sub, 1));
+    if (e == cudaSuccess) e = plan_buf(c, p->scratch_tables, 2, sizeof(int32_t) * std::max<int64_t>(p->n_sub, 1));
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         fc_plan_free(p);
@@ -1501,9 +1534,15 @@ int build_set_plan(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t 
     P.words_per_part = (int32_t)round_up((c->words + P.nparts - 1) / P.nparts, 64);
     P.m_tail = c->m;
     P.full_only = full_only;
+    P.all_splits = mode == 2;
+    P.split_off = mode == 2 ? (const int64_t *)(d + o_spl) : nullptr;
     if (full_only) p->sup_threads = std::min(p->sup_threads, 512);
+    if (mode == 2) {
+        p->sup_threads = std::min(p->sup_threads, 256);
+        P.sets_per_item = (p->sup_threads / 32) * std::max(1, o.support_sets_per_warp);
+    }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, support_kernel_ptr(full_only), p->sup_threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, support_kernel_ptr(mode), p->sup_threads, 0);
     p->sup_grid = c->num_sms * std::max(1, per_sm);
     *out = p;
     return FC_OK;
@@ -1601,6 +1640,24 @@ extern "C" int fc_count_assignment_batch(fc_ctx *c, int32_t nq, const int32_t *v
     fc_plan_free(p);
     if (rc == FC_OK)
         for (int32_t q = 0; q < nq; ++q) counts[q] = tmp[q];
+    return rc;
+}
+
+extern "C" int fc_support_splits_batch(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *items,
+                                       int32_t *support, int32_t *sub_support, float *confidence)
+{
+    if (!c || (nq > 0 && !support)) return fail(FC_ERR_ARG, "fc_support_splits_batch: null argument");
+    DevGuard g(c->device);
+    fc_plan *p = nullptr;
+    int rc;
+    {
+        BorrowScope b(c);
+        rc = fc_plan_support_splits(c, nq, set_off, items, &p);
+    }
+    if (rc != FC_OK) return rc;
+    rc = run_to_host(p, support, sizeof(int32_t) * nq, sub_support, sizeof(int32_t) * p->n_sub,
+                     confidence, sizeof(float) * p->n_sub);
+    fc_plan_free(p);
     return rc;
 }
 

@@ -170,11 +170,17 @@ struct SupportParams {
     int32_t sets_per_item;   // itemsets one CTA takes per work item
     int32_t full_only;       // 1: only supp(S) (assignment counts), no leave-one-out sets
     int64_t m_tail;          // m: bits at positions >= m are not transactions
+    // all-splits mode: sub_support / confidence hold 2^k - 2 entries per
+    // itemset from split_off[q], antecedent masks 1 .. 2^k - 2 in order
+    const int64_t *split_off;
+    int32_t all_splits;
+    int32_t pad;
 };
+constexpr int kMaxSplitK = 16;  // itemset size limit of the all-splits mode
 cudaError_t launch_support(const SupportParams &p, int grid, int threads, size_t smem,
                            cudaStream_t s);
 cudaError_t launch_support_confidence(const SupportParams &p, cudaStream_t s);
-const void *support_kernel_ptr(int full_only);
+const void *support_kernel_ptr(int mode);  // 0 leave-one-out, 1 full only, 2 all splits
 
 // All-pairs one-hot co-occurrence on tcgen05 tensor cores.
 struct PairsParams {

@@ -237,6 +237,146 @@ __global__ void __launch_bounds__(512, 2) assign_kernel(const SupportParams P)
     }
 }
 
+// ---- every split of an itemset into antecedent A and consequent S \ A
+//
+// supp(A) is needed for all 2^k - 2 non-empty proper subsets A of S.  Per
+// word the subsets are walked depth-first (include or skip each item in
+// turn), so every subset costs one AND of its parent's word with one item's
+// word and one popcount, and the walk keeps only one partial AND per level.
+// With k fixed at compile time the walk unrolls completely and the 2^k - 1
+// counters (subset masks 1 .. 2^k - 1) sit in registers.
+
+template <int K, int T, int MASK>
+struct SubsetWalk {
+    // subsets MASK | {some items >= T}; acc is the AND of MASK's words
+    static __device__ __forceinline__ void run(const uint64_t (&x)[K], uint64_t acc, unsigned (&cnt)[1 << K])
+    {
+        if constexpr (T < K) {
+            const uint64_t a = MASK == 0 ? x[T] : (acc & x[T]);
+            cnt[MASK | (1 << T)] += (unsigned)__popcll(a);
+            SubsetWalk<K, T + 1, MASK | (1 << T)>::run(x, a, cnt);
+            SubsetWalk<K, T + 1, MASK>::run(x, acc, cnt);
+        }
+    }
+};
+
+template <int K>
+__device__ __forceinline__ void splits_set(const SupportParams &P, const int32_t *items, int64_t w0, int64_t w1,
+                                           int lane, int32_t *supp, int32_t *sub, bool atomic)
+{
+    const uint64_t *row[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) row[t] = P.bits + (int64_t)items[t] * P.wstride;
+    unsigned cnt[1 << K];
+#pragma unroll
+    for (int i = 0; i < (1 << K); ++i) cnt[i] = 0u;
+#pragma unroll 1
+    for (int64_t w = w0 + 2 * lane; w < w1; w += 64) {
+        ulonglong2 a[K];
+#pragma unroll
+        for (int t = 0; t < K; ++t) a[t] = __ldg(reinterpret_cast<const ulonglong2 *>(row[t] + w));
+        uint64_t x[K];
+#pragma unroll
+        for (int t = 0; t < K; ++t) x[t] = a[t].x;
+        SubsetWalk<K, 0, 0>::run(x, ~0ull, cnt);
+#pragma unroll
+        for (int t = 0; t < K; ++t) x[t] = a[t].y;
+        SubsetWalk<K, 0, 0>::run(x, ~0ull, cnt);
+    }
+    constexpr int kFull = (1 << K) - 1;
+#pragma unroll
+    for (int i = 1; i <= kFull; ++i) {
+        const unsigned v = __reduce_add_sync(kFullMask, cnt[i]);
+        if (lane == 0) {
+            int32_t *dst = i == kFull ? supp : sub + (i - 1);
+            if (atomic) {
+                if (v) atomicAdd(dst, (int)v);
+            } else {
+                *dst = (int)v;
+            }
+        }
+    }
+}
+
+// Any size up to kMaxSplitK (and 0 or 1 items): one pass over the words per
+// subset, the last word masked to the m transactions.
+__device__ void splits_set_any(const SupportParams &P, const int32_t *items, int k, int64_t w0, int64_t w1,
+                               int lane, int32_t *supp, int32_t *sub, bool atomic)
+{
+    const int64_t last = P.words - 1;
+    const int rem = (int)(P.m_tail & 63);
+    const uint64_t tail = rem ? ((1ull << rem) - 1ull) : ~0ull;
+    const int full = (1 << k) - 1;
+    for (int mask = (k == 0 ? 0 : 1); mask <= full; ++mask) {
+        unsigned c = 0u;
+        for (int64_t w = w0 + lane; w < w1; w += 32) {
+            uint64_t x = w == last ? tail : ~0ull;
+            for (int t = 0; t < k; ++t)
+                if (mask >> t & 1) x &= __ldg(P.bits + (int64_t)items[t] * P.wstride + w);
+            c += (unsigned)__popcll(x);
+        }
+        c = __reduce_add_sync(kFullMask, c);
+        if (lane == 0) {
+            int32_t *dst = mask == full ? supp : sub + (mask - 1);
+            if (atomic) {
+                if (c) atomicAdd(dst, (int)c);
+            } else {
+                *dst = (int)c;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) splits_kernel(const SupportParams P)
+{
+    __shared__ int s_item;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t ngroups = ((int64_t)P.nq + P.sets_per_item - 1) / P.sets_per_item;
+    const int64_t n_work = ngroups * P.nparts;
+    const bool atomic = P.nparts > 1;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(P.next_item, 1);
+        __syncthreads();
+        const int64_t it = s_item;
+        __syncthreads();
+        if (it >= n_work) break;
+        const int64_t part = it / ngroups, group = it % ngroups;
+        const int64_t w0 = part * P.words_per_part;
+        const int64_t w1 = min(P.words, w0 + P.words_per_part);
+        const int64_t g0 = group * P.sets_per_item;
+        const int64_t g1 = min((int64_t)P.nq, g0 + P.sets_per_item);
+        for (int64_t i = g0 + warp; i < g1; i += nwarps) {
+            const int32_t q = P.order[i];
+            const int32_t a = P.set_off[q], k = P.set_off[q + 1] - a;
+            const int32_t *items = P.items + a;
+            int32_t *supp = P.support + q;
+            int32_t *sub = P.sub_support + P.split_off[q];
+            switch (k) {
+            case 2: splits_set<2>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 3: splits_set<3>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 4: splits_set<4>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 5: splits_set<5>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 6: splits_set<6>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            default: splits_set_any(P, items, k, w0, w1, lane, supp, sub, atomic); break;
+            }
+        }
+    }
+}
+
+// conf(A => S \ A) = supp(S) / supp(A) for every split, 0 when supp(A) = 0.
+__global__ void splits_confidence_kernel(const SupportParams P)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < P.nq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = P.split_off[q], b = P.split_off[q + 1];
+        const float s = (float)P.support[q];
+        for (int64_t t = a; t < b; ++t) {
+            const int32_t d = P.sub_support[t];
+            P.confidence[t] = d > 0 ? __fdiv_rn(s, (float)d) : 0.0f;
+        }
+    }
+}
+
 // conf((S without item t) => item t) = supp(S) / supp(S without item t), 0 when
 // the denominator is 0 (then supp(S) is 0 as well).
 __global__ void confidence_kernel(const SupportParams P)
@@ -254,15 +394,19 @@ __global__ void confidence_kernel(const SupportParams P)
 
 }  // namespace
 
-const void *support_kernel_ptr(int full_only)
+const void *support_kernel_ptr(int mode)
 {
-    return full_only ? (const void *)assign_kernel : (const void *)support_kernel;
+    return mode == 1 ? (const void *)assign_kernel
+         : mode == 2 ? (const void *)splits_kernel
+                     : (const void *)support_kernel;
 }
 
 cudaError_t launch_support(const SupportParams &p, int grid, int threads, size_t smem, cudaStream_t s)
 {
     if (p.full_only)
         assign_kernel<<<grid, threads > 512 ? 512 : threads, smem, s>>>(p);
+    else if (p.all_splits)
+        splits_kernel<<<grid, threads > 256 ? 256 : threads, smem, s>>>(p);
     else
         support_kernel<<<grid, threads, smem, s>>>(p);
     return cudaGetLastError();
@@ -273,7 +417,10 @@ cudaError_t launch_support_confidence(const SupportParams &p, cudaStream_t s)
     int64_t blocks = ((int64_t)p.nq + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    confidence_kernel<<<(unsigned)blocks, 256, 0, s>>>(p);
+    if (p.all_splits)
+        splits_confidence_kernel<<<(unsigned)blocks, 256, 0, s>>>(p);
+    else
+        confidence_kernel<<<(unsigned)blocks, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

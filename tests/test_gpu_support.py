@@ -83,3 +83,74 @@ def test_support_full_workload_sampled():
     assert np.array_equal(sub[a + 1], item_supp[it[a]])
     idx = sorted(np.random.default_rng(11).choice(len(sets), size=48, replace=False).tolist())
     check(bits, m, sets, idx, (supp, sub, conf))
+
+
+def check_splits(bits, m, sets, idx, got):
+    supp, sub, conf = got
+    so, _ = fc.pack_lists(sets)
+    off = fc.split_offsets(so)
+
+    def one(q):
+        return oracle.support_splits(bits, m, sets[q])
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        res = list(ex.map(one, idx))
+    for q, (s, sb, cf_) in zip(idx, res):
+        a, b = off[q], off[q + 1]
+        assert supp[q] == s, (q, sets[q])
+        assert np.array_equal(sub[a:b].astype(np.int64), sb), (q, sets[q])
+        assert np.allclose(conf[a:b], cf_, rtol=1e-6, atol=0), (q, conf[a:b], cf_)
+
+
+@pytest.mark.parametrize("m", [1, 64, 65, 4097, 200_003])
+def test_support_splits_all(m):
+    """Every antecedent split (2^k - 2 per itemset), sizes 0 to 9 (the
+    unrolled walk covers 2-6, the generic loop the rest)."""
+    bits = zipf_transaction_bitmaps(40, m, 1.1, 6.0, seed=m % 997 + 5)
+    probs = zipf_item_probs(40, 1.1, 6.0)
+    sets = weighted_itemsets(40, 300, 2, 7, probs, seed=3) + [[3], [], [0, 1, 2, 3, 4, 5, 6, 7, 8]]
+    ctx = fc.fc_load_bits(bits, m)
+    so, it = fc.pack_lists(sets)
+    got = fc.fc_support_splits_batch(ctx, so, it)
+    check_splits(bits, m, sets, range(len(sets)), got)
+    # the single-consequent masks equal the leave-one-out supports
+    s1, sub1, _ = fc.fc_support_batch(ctx, so, it)
+    off = fc.split_offsets(so)
+    for q, S in enumerate(sets):
+        k = len(S)
+        if k >= 2:
+            full = (1 << k) - 1
+            want = sub1[so[q]:so[q + 1]]
+            got_loo = [got[1][off[q] + (full ^ (1 << t)) - 1] for t in range(k)]
+            assert np.array_equal(np.array(got_loo), want)
+    assert np.array_equal(got[0][:len(sets)], s1[:len(sets)])
+
+
+def test_support_splits_row_ranges_and_plan():
+    """Long bitmaps split into word ranges (atomic partial counts), through a
+    device-resident plan replayed twice."""
+    torch = pytest.importorskip("torch")
+    m = 1_000_003
+    bits = zipf_transaction_bitmaps(30, m, 1.1, 8.0, seed=77)
+    probs = zipf_item_probs(30, 1.1, 8.0)
+    sets = weighted_itemsets(30, 200, 2, 6, probs, seed=8)
+    ctx = fc.fc_load_bits(bits, m)
+    fc.fc_set_option(ctx, "support_part_words", 2048)
+    so, it = fc.pack_lists(sets)
+    plan = fc.fc_plan_support_splits(ctx, so, it)
+    ns = fc.fc_plan_size(plan, 3)
+    assert ns == int(fc.split_offsets(so)[-1])
+    outs = [torch.empty(len(sets), dtype=torch.int32, device="cuda"),
+            torch.empty(ns, dtype=torch.int32, device="cuda"),
+            torch.empty(ns, dtype=torch.float32, device="cuda")]
+    res = []
+    for _ in range(2):
+        fc.fc_plan_run(plan, *outs)
+        torch.cuda.synchronize()
+        res.append([o.cpu().numpy().copy() for o in outs])
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+    idx = np.random.default_rng(1).choice(len(sets), size=24, replace=False)
+    check_splits(bits, m, sets, idx, res[1])
+    with pytest.raises(fc.FcError):
+        fc.fc_support_splits_batch(ctx, *fc.pack_lists([list(range(17))]))

@@ -240,6 +240,9 @@ CONFIGS = {
                    nq=50_000, pa=(0, 4), ess=1.0),
     "support": dict(n_items=1000, m=10_000_000, zipf_s=1.1, mean_len=10.0, seed=5,
                     nq=1_000_000, k=(2, 5)),
+    # the same itemsets with every antecedent split (2^k - 2 rules each)
+    "splits": dict(n_items=1000, m=10_000_000, zipf_s=1.1, mean_len=10.0, seed=5,
+                   nq=1_000_000, k=(2, 5)),
     # the parent-set lattice over the first 20 variables of the BN-score
     # database, parent sets of at most 4 (Sec. 4.2 query stream)
     "families": dict(m=1_000_000, nv=20, max_parents=4, seed=4),
