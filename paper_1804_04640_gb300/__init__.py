@@ -303,16 +303,32 @@ def fc_plan_assignments(ctx: Handle, var_off, vars_, states) -> Handle:
     return Handle(out, lib.fc_plan_free, ctx)
 
 
+def _table_offsets(ar, vo, vv) -> np.ndarray:
+    """Dense table offsets (cells = product of arities per query, last fastest)."""
+    nq = len(vo) - 1
+    to = np.zeros(nq + 1, dtype=np.int64)
+    if nq == 0:
+        return to
+    ar = np.asarray(ar, dtype=np.float64)
+    k = np.diff(np.asarray(vo, dtype=np.int64))
+    cells = np.ones(nq, dtype=np.float64)
+    nz = k > 0
+    if len(vv):
+        prods = np.multiply.reduceat(ar[np.asarray(vv, dtype=np.int64)], np.minimum(vo[:-1], len(vv) - 1))
+        cells[nz] = prods[nz]
+    # tables past 2^31 cells are refused by the library (FC_ERR_SIZE); clamp
+    # them so the offsets stay representable
+    to[1:] = np.cumsum(np.minimum(cells, 2.0 ** 40).astype(np.int64))
+    return to
+
+
 def fc_count_batch(ctx: Handle, var_off, vars_, table_off=None, out=None):
     """Tables of a batch; returns (tables int32, table_off int64)."""
     lib = load_library()
     vo, vv = _host(var_off, np.int32), _host(vars_, np.int32)
     nq = len(vo) - 1
     if table_off is None:
-        ar = fc_arities(ctx)
-        cells = np.array([int(np.prod(ar[vv[vo[q]:vo[q + 1]]])) for q in range(nq)], dtype=np.int64)
-        to = np.zeros(nq + 1, dtype=np.int64)
-        to[1:] = np.cumsum(cells)
+        to = _table_offsets(fc_arities(ctx), vo, vv)
     else:
         to = _host(table_off, np.int64)
     if out is None:

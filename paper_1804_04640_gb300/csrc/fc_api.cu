@@ -687,7 +687,17 @@ struct QPlan {
 // stages the state bitmaps of every level but the first.
 void entropy_order(const fc_ctx *c, QVar *v, int k)
 {
-    std::stable_sort(v, v + k, [&](const QVar &a, const QVar &b) { return c->entropy[a.var] < c->entropy[b.var]; });
+    // stable insertion sort: k is small and this runs once or twice per query
+    for (int i = 1; i < k; ++i) {
+        const QVar x = v[i];
+        const double h = c->entropy[x.var];
+        int j = i - 1;
+        while (j >= 0 && c->entropy[v[j].var] > h) {
+            v[j + 1] = v[j];
+            --j;
+        }
+        v[j + 1] = x;
+    }
 }
 
 // Staged slots of the query in entropy order; the ordered copy goes to o.
@@ -720,14 +730,15 @@ bool bitmap_ok(const fc_ctx *c, const QVar *v, int k, QVar *o)
     return slots <= c->opt.stage_slots;
 }
 
-QPlan choose(const fc_ctx *c, const QVar *v, int k, int64_t cells, int32_t smem_cells)
+// Strategy and cost of one query.  When the bitmap strategy is chosen, the
+// variables are left in v in entropy order (the order its kernel walks).
+QPlan choose(const fc_ctx *c, QVar *v, int k, int64_t cells, int32_t smem_cells, double chunks)
 {
     const Options &o = c->opt;
-    const double chunks = (double)((c->m + kChunkRows - 1) / kChunkRows);
     const double rows = (double)c->m;
     const double flush = (double)cells * o.flush_cost;
     const bool fits = cells <= smem_cells;
-    QVar ord[kMaxK];
+    QVar ord[kMaxBitmapK];
     const bool bm = bitmap_ok(c, v, k, ord);
     const double nodes = bm ? dfs_nodes(ord, k) : 0.0;
     const double hist = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) + flush;
@@ -747,7 +758,32 @@ QPlan choose(const fc_ctx *c, const QVar *v, int k, int64_t cells, int32_t smem_
             s = cells >= o.sort_min_cells ? FC_STRAT_SORT : FC_STRAT_GATOMIC;
     }
     double cost = s == FC_STRAT_BITMAP ? bitmap : s == FC_STRAT_HIST ? hist : gatomic;
+    if (s == FC_STRAT_BITMAP) std::copy(ord, ord + k, v);
     return QPlan{s, cost};
+}
+
+// Positions 0..n-1 ordered by decreasing key(i) (a positive cost), ties in
+// increasing position: a counting sort on the cost's exponent and top three
+// mantissa bits (1/8-octave classes), which is as much order as the
+// longest-processing-time-first assignment needs and avoids a comparison
+// sort's mispredicted branches on thousands of queries.
+template <class Key>
+void order_by_cost_desc(size_t n, Key key, std::vector<int32_t> &out)
+{
+    constexpr int kBits = 14;  // 11 exponent + 3 mantissa bits of a positive double
+    std::vector<uint32_t> cls(n);
+    std::vector<int32_t> start((1 << kBits) + 1, 0);
+    for (size_t i = 0; i < n; ++i) {
+        double v = key(i);
+        if (!(v > 0.0)) v = 0.0;
+        uint64_t b;
+        std::memcpy(&b, &v, sizeof b);
+        cls[i] = ((1u << kBits) - 1u) - (uint32_t)(b >> (52 - 3));  // descending
+        ++start[cls[i] + 1];
+    }
+    for (int c = 0; c < (1 << kBits); ++c) start[c + 1] += start[c];
+    out.resize(n);
+    for (size_t i = 0; i < n; ++i) out[start[cls[i]]++] = (int32_t)i;
 }
 
 // Builds a count or score plan.  vars lists are read through `get`.
@@ -771,8 +807,10 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     const int max_cells = std::max(1, std::min<int>(o.smem_cells, (c->max_smem_optin - 4096) / 4));
     p->smem_cells = max_cells;
 
+    const double chunks_d = (double)((c->m + kChunkRows - 1) / kChunkRows);
     std::vector<QHead> qh(nq);
     std::vector<QVar> qv;
+    qv.reserve((size_t)nq * 4);
     std::vector<double> cost(nq);
     p->strategy.resize(nq);
     p->table_off.assign(nq + 1, 0);
@@ -792,8 +830,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
             fc_plan_free(p);
             return (int)cells;
         }
-        QPlan ch = choose(c, qv.data() + first, k_eff, cells, max_cells);
-        if (ch.strategy == FC_STRAT_BITMAP) entropy_order(c, qv.data() + first, k_eff);
+        QPlan ch = choose(c, qv.data() + first, k_eff, cells, max_cells, chunks_d);
         QHead &h = qh[q];
         h.cells = (int32_t)cells;
         h.var_off = (int32_t)first;
@@ -845,6 +882,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     std::vector<std::pair<double, Item>> order;
     std::vector<int32_t> qlist;
     std::vector<std::pair<double, int32_t>> bmo;
+    order.reserve((size_t)nq * (size_t)parts);
     for (int32_t q = 0; q < nq; ++q) {
         QHead &h = qh[q];
         if (h.strategy == kSort) {
@@ -859,10 +897,11 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
         h.nparts = (int16_t)qparts;
         for (int32_t part = 0; part < qparts; ++part) order.push_back({cost[q] / qparts, Item{q, part}});
     }
-    std::stable_sort(order.begin(), order.end(),
-                     [](const auto &a, const auto &b) { return a.first > b.first; });
+    // heaviest first; within a cost class, query and part order
+    std::vector<int32_t> perm;
+    order_by_cost_desc(order.size(), [&](size_t i) { return order[i].first; }, perm);
     items.reserve(order.size());
-    for (auto &x : order) items.push_back(x.second);
+    for (int32_t i : perm) items.push_back(order[i].second);
     p->n_items = (int32_t)items.size();
     // bitmap queries: warp tasks of consecutive 4096-row chunks, heaviest
     // queries first.  A query gets tasks in proportion to its estimated cost
@@ -870,8 +909,15 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     // least kMinTaskChunks chunks, so that light queries are not cut into
     // tasks whose fixed costs (dispatch, one reduction and atomic per cell)
     // outweigh their work.
-    std::stable_sort(bmo.begin(), bmo.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    {
+        order_by_cost_desc(bmo.size(), [&](size_t i) { return bmo[i].first; }, perm);
+        std::vector<std::pair<double, int32_t>> sorted;
+        sorted.reserve(bmo.size());
+        for (int32_t i : perm) sorted.push_back(bmo[i]);
+        bmo.swap(sorted);
+    }
     std::vector<BTask> btasks;
+    btasks.reserve(bmo.size() * 4);
     p->bm_threads = std::max(32, std::min(1024, o.bitmap_threads / 32 * 32));
     p->stage_slots = o.stage_slots;
     p->small_paths = o.bitmap_small;

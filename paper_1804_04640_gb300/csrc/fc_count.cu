@@ -30,6 +30,8 @@
 // query's whole table, else by the last CTA or warp to finish one of the
 // query's pieces (an atomic ticket).
 #include "fc_internal.h"
+
+#include <mutex>
 #include "fc_score.cuh"
 
 namespace fc {
@@ -969,20 +971,56 @@ size_t bitmap_smem_bytes(int threads, int stage_slots)
 
 // CTAs of bitmap_kernel one SM holds (the dynamic shared-memory limit of the
 // kernel is raised first, or the occupancy query would report none).
+// The dynamic shared-memory limit a kernel was last given on each device:
+// raising it is a driver call, so it is made only when a launch needs more.
+namespace {
+std::mutex g_attr_mu;
+constexpr int kMaxDevices = 64;
+int g_count_smem[kMaxDevices], g_bitmap_smem[kMaxDevices];
+
+cudaError_t ensure_smem_attr(const void *fn, int *cache, size_t smem)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (dev >= 0 && dev < kMaxDevices && cache[dev] >= (int)smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) cache[dev] = (int)smem;
+    return e;
+}
+
+struct OccKey {
+    int dev, threads, slots, per_sm;
+};
+OccKey g_occ[16];
+int g_n_occ = 0;
+}  // namespace
+
 int bitmap_ctas_per_sm(int threads, int stage_slots)
 {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    {
+        std::lock_guard<std::mutex> lock(g_attr_mu);
+        for (int i = 0; i < g_n_occ; ++i)
+            if (g_occ[i].dev == dev && g_occ[i].threads == threads && g_occ[i].slots == stage_slots)
+                return g_occ[i].per_sm;
+    }
     const size_t smem = bitmap_smem_bytes(threads, stage_slots);
-    if (cudaFuncSetAttribute(bitmap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return 1;
+    if (ensure_smem_attr((const void *)bitmap_kernel, g_bitmap_smem, smem) != cudaSuccess) return 1;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bitmap_kernel, threads, smem) != cudaSuccess)
         return 1;
-    return per_sm > 0 ? per_sm : 1;
+    per_sm = per_sm > 0 ? per_sm : 1;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (g_n_occ < 16) g_occ[g_n_occ++] = OccKey{dev, threads, stage_slots, per_sm};
+    return per_sm;
 }
 
 cudaError_t launch_count(const CountParams &p, int grid, int threads, size_t smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_attr((const void *)count_kernel, g_count_smem, smem);
     if (e != cudaSuccess) return e;
     count_kernel<<<grid, threads, smem, s>>>(p);
     return cudaGetLastError();
@@ -992,7 +1030,7 @@ cudaError_t launch_bitmap(const CountParams &p, int grid, int threads, cudaStrea
 {
     if (threads > kBitmapWarps * 32) return cudaErrorInvalidValue;
     const size_t smem = bitmap_smem_bytes(threads, p.stage_slots);
-    cudaError_t e = cudaFuncSetAttribute(bitmap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_attr((const void *)bitmap_kernel, g_bitmap_smem, smem);
     if (e != cudaSuccess) return e;
     bitmap_kernel<<<grid, threads, smem, s>>>(p);
     return cudaGetLastError();
