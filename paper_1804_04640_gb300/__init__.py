@@ -314,7 +314,10 @@ def _table_offsets(ar, vo, vv) -> np.ndarray:
     cells = np.ones(nq, dtype=np.float64)
     nz = k > 0
     if len(vv):
-        prods = np.multiply.reduceat(ar[np.asarray(vv, dtype=np.int64)], np.minimum(vo[:-1], len(vv) - 1))
+        # out-of-range ids count as arity 1 here; the library rejects them
+        ids = np.asarray(vv, dtype=np.int64)
+        ids = np.where((ids >= 0) & (ids < len(ar)), ids, len(ar))
+        prods = np.multiply.reduceat(np.append(ar, 1.0)[ids], np.minimum(vo[:-1], len(vv) - 1))
         cells[nz] = prods[nz]
     # tables past 2^31 cells are refused by the library (FC_ERR_SIZE); clamp
     # them so the offsets stay representable

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 using namespace fc;
@@ -638,22 +639,31 @@ namespace {
 // Validates one variable list and appends its device description: strides in
 // the caller's order (last fastest), arity-1 variables dropped (they add no
 // digit).  Returns the number of cells or a negative FC_ERR code.
-int64_t describe(fc_ctx *c, const int32_t *vars, int32_t k, std::vector<QVar> &qv, int32_t &k_eff)
+// Validates one query's variables and appends its QVars (arity-1 variables
+// dropped, strides of the caller's order, last fastest); returns the cells.
+// Reads the context only, so planner threads may call it concurrently (an
+// error's message goes to the calling thread's fc_last_error).
+int64_t describe(const fc_ctx *c, const int32_t *vars, int32_t k, std::vector<QVar> &qv, int32_t &k_eff)
 {
     if (k < 0 || k > c->n) return fail(FC_ERR_ARG, "query has %d variables, n = %d", k, c->n);
     if (k > 0 && !vars) return fail(FC_ERR_ARG, "null variable list");
-    if (++c->epoch == 0) {
-        std::fill(c->mark.begin(), c->mark.end(), 0u);
-        c->epoch = 1;
-    }
     int64_t cells = 1;
     for (int t = 0; t < k; ++t) {
         const int v = vars[t];
         if (v < 0 || v >= c->n) return fail(FC_ERR_ARG, "variable %d out of range 0..%d", v, c->n - 1);
-        if (c->mark[v] == c->epoch) return fail(FC_ERR_ARG, "variable %d listed twice in one query", v);
-        c->mark[v] = c->epoch;
         cells *= c->arity[v];
         if (cells > INT32_MAX) return fail(FC_ERR_SIZE, "table over %d variables exceeds 2^31-1 cells", k);
+    }
+    // duplicates: pairwise for short lists, a sorted copy otherwise
+    if (k <= 48) {
+        for (int t = 1; t < k; ++t)
+            for (int u = 0; u < t; ++u)
+                if (vars[u] == vars[t]) return fail(FC_ERR_ARG, "variable %d listed twice in one query", vars[t]);
+    } else {
+        std::vector<int32_t> sorted(vars, vars + k);
+        std::sort(sorted.begin(), sorted.end());
+        for (int t = 1; t < k; ++t)
+            if (sorted[t] == sorted[t - 1]) return fail(FC_ERR_ARG, "variable %d listed twice in one query", sorted[t]);
     }
     int64_t stride = 1;
     const size_t first = qv.size();
@@ -810,39 +820,92 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     const double chunks_d = (double)((c->m + kChunkRows - 1) / kChunkRows);
     std::vector<QHead> qh(nq);
     std::vector<QVar> qv;
-    qv.reserve((size_t)nq * 4);
     std::vector<double> cost(nq);
     p->strategy.resize(nq);
     p->table_off.assign(nq + 1, 0);
+
+    // Per query: validation, QVars and strategy.  Large batches split into
+    // contiguous query ranges on host threads (each query's work only reads
+    // the context); the ranges' QVars are concatenated in query order.
+    struct Range {
+        std::vector<QVar> qv;
+        int32_t err_q = -1;
+        int err_code = 0;
+        std::string err_msg;
+    };
+    const int nthreads = nq >= 4096 ? (int)std::max<int64_t>(1, std::min<int64_t>({8, nq / 2048,
+                                          (int64_t)std::max(1u, std::thread::hardware_concurrency())}))
+                                    : 1;
+    std::vector<Range> ranges(nthreads);
+    auto work = [&](int t) {
+        Range &R = ranges[t];
+        const int32_t q0 = (int32_t)((int64_t)nq * t / nthreads), q1 = (int32_t)((int64_t)nq * (t + 1) / nthreads);
+        R.qv.reserve((size_t)(q1 - q0) * 4);
+        std::vector<int32_t> buf;
+        for (int32_t q = q0; q < q1; ++q) {
+            const int32_t *vars;
+            int32_t k;
+            int32_t child;
+            if (!get(q, vars, k, child, buf)) {
+                R.err_q = q;
+                R.err_code = FC_ERR_ARG;
+                R.err_msg = g_err;
+                return;
+            }
+            const size_t first = R.qv.size();
+            int32_t k_eff = 0;
+            const int64_t cells = describe(c, vars, k, R.qv, k_eff);
+            if (cells < 0) {
+                R.err_q = q;
+                R.err_code = (int)cells;
+                R.err_msg = g_err;
+                return;
+            }
+            const QPlan ch = choose(c, R.qv.data() + first, k_eff, cells, max_cells, chunks_d);
+            QHead &h = qh[q];
+            h.cells = (int32_t)cells;
+            h.var_off = (int32_t)first;  // within the range for now
+            h.k = (int16_t)k_eff;
+            h.strategy = (int16_t)ch.strategy;
+            h.nparts = 1;
+            h.score_kind = (int16_t)score_kind;
+            h.r_child = score_kind == kNoScore ? 1 : c->arity[child];
+            h.child_soff = score_kind == kNoScore ? 0 : c->soff[child];
+            h.score_slot = q;
+            p->strategy[q] = ch.strategy;
+            cost[q] = ch.cost;
+        }
+    };
+    if (nthreads == 1) {
+        work(0);
+    } else {
+        std::vector<std::thread> pool;
+        pool.reserve(nthreads - 1);
+        for (int t = 1; t < nthreads; ++t) pool.emplace_back(work, t);
+        work(0);
+        for (auto &th : pool) th.join();
+    }
+    for (const Range &R : ranges)
+        if (R.err_q >= 0) {  // the first failing range holds the lowest failing query
+            fc_plan_free(p);
+            return fail(R.err_code, "%s", R.err_msg.c_str());
+        }
+    {
+        size_t total = 0;
+        for (const Range &R : ranges) total += R.qv.size();
+        qv.reserve(total);
+        for (int t = 0; t < nthreads; ++t) {
+            const int32_t base = (int32_t)qv.size();
+            const int32_t q0 = (int32_t)((int64_t)nq * t / nthreads), q1 = (int32_t)((int64_t)nq * (t + 1) / nthreads);
+            for (int32_t q = q0; q < q1; ++q) qh[q].var_off += base;
+            qv.insert(qv.end(), ranges[t].qv.begin(), ranges[t].qv.end());
+        }
+    }
+
     int64_t scratch = 0;
     for (int32_t q = 0; q < nq; ++q) {
-        const int32_t *vars;
-        int32_t k;
-        int32_t child;
-        if (!get(q, vars, k, child)) {
-            fc_plan_free(p);
-            return FC_ERR_ARG;
-        }
-        const size_t first = qv.size();
-        int32_t k_eff = 0;
-        const int64_t cells = describe(c, vars, k, qv, k_eff);
-        if (cells < 0) {
-            fc_plan_free(p);
-            return (int)cells;
-        }
-        QPlan ch = choose(c, qv.data() + first, k_eff, cells, max_cells, chunks_d);
         QHead &h = qh[q];
-        h.cells = (int32_t)cells;
-        h.var_off = (int32_t)first;
-        h.k = (int16_t)k_eff;
-        h.strategy = (int16_t)ch.strategy;
-        h.nparts = 1;
-        h.score_kind = (int16_t)score_kind;
-        h.r_child = score_kind == kNoScore ? 1 : c->arity[child];
-        h.child_soff = score_kind == kNoScore ? 0 : c->soff[child];
-        h.score_slot = q;
-        p->strategy[q] = ch.strategy;
-        cost[q] = ch.cost;
+        const int64_t cells = h.cells;
         if (score_kind == kNoScore) {
             if (user_off) {
                 if (user_off[q + 1] - user_off[q] < cells || user_off[q] < 0) {
@@ -1192,7 +1255,7 @@ extern "C" int fc_plan_count(fc_ctx *c, int32_t nq, const int32_t *var_off, cons
     if (table_off)
         for (int32_t q = 0; q < nq; ++q)
             if (table_off[q + 1] < table_off[q]) return fail(FC_ERR_ARG, "table_off must be non-decreasing");
-    auto get = [&](int32_t q, const int32_t *&v, int32_t &k, int32_t &child) {
+    auto get = [&](int32_t q, const int32_t *&v, int32_t &k, int32_t &child, std::vector<int32_t> &) {
         const int32_t a = var_off[q], b = var_off[q + 1];
         if (a < 0 || b < a) {
             fail(FC_ERR_ARG, "var_off must be non-decreasing and non-negative");
@@ -1214,8 +1277,7 @@ extern "C" int fc_plan_score(fc_ctx *c, int32_t nq, const int32_t *child, const 
     if (kind < FC_LL || kind > FC_MI) return fail(FC_ERR_ARG, "unknown score kind %d", kind);
     if (kind == FC_BDEU && !(ess > 0.0)) return fail(FC_ERR_ARG, "BDeu needs ess > 0");
     DevGuard g(c->device);
-    std::vector<int32_t> buf;
-    auto get = [&](int32_t q, const int32_t *&v, int32_t &k, int32_t &ch) {
+    auto get = [&](int32_t q, const int32_t *&v, int32_t &k, int32_t &ch, std::vector<int32_t> &buf) {
         const int32_t a = par_off[q], b = par_off[q + 1];
         if (a < 0 || b < a || (b > a && !parents)) {
             fail(FC_ERR_ARG, "par_off must be non-decreasing and non-negative");

@@ -143,6 +143,36 @@ def test_edge_cases():
     assert toff.tolist() == [0]
 
 
+def test_large_batch_validation_errors():
+    """Batches large enough to be planned on several host threads report the
+    first invalid query with its own message, and a valid batch of the same
+    size still matches the oracle."""
+    db = random_dag_database(12, 5003, 2, 4, 3, 1.0, seed=19)
+    ctx = fc.fc_load(db.D, db.arities)
+    queries = random_queries(db.n, 9000, 1, 4, seed=20)
+    bad = [list(q) for q in queries]
+    bad[6100] = [0, 99]
+    bad[7000] = [3, 3]
+    with pytest.raises(fc.FcError) as e:
+        fc.fc_count_batch(ctx, *fc.pack_lists(bad))
+    assert e.value.code == fc.FC_ERR_ARG and "99" in str(e.value)
+    bad[6100] = [0, 1]
+    with pytest.raises(fc.FcError) as e:
+        fc.fc_count_batch(ctx, *fc.pack_lists(bad))
+    assert e.value.code == fc.FC_ERR_ARG and "twice" in str(e.value)
+    off, flat = fc.pack_lists(queries)
+    tables, toff = fc.fc_count_batch(ctx, off, flat)
+    orc = oracle.DB(db.D, db.arities)
+    for q in range(0, len(queries), 97):
+        assert np.array_equal(tables[toff[q]:toff[q + 1]].astype(np.int64), orc.table(queries[q]))
+    child = [q[-1] for q in queries]
+    po, pa = fc.pack_lists([q[:-1] for q in queries])
+    s1 = fc.fc_score_batch(ctx, child, po, pa, "mdl")
+    for q in range(0, len(queries), 211):
+        w = orc.score(child[q], queries[q][:-1], "mdl")
+        assert abs(float(s1[q]) - w) <= 1e-5 * abs(w) + 1e-12
+
+
 def test_row_major_load_and_assignment_count():
     """fc_load with a row-major database; Count of a specific assignment
     (the worked example of Sec. 2 lives in tests/golden)."""
