@@ -14,6 +14,10 @@
 #include <numeric>
 #include <string>
 #include <thread>
+#include <mutex>
+#include <memory>
+#include <functional>
+#include <condition_variable>
 #include <vector>
 
 using namespace fc;
@@ -138,6 +142,69 @@ struct Options {
 
 }  // namespace
 
+namespace {
+// Host worker threads of a context (the planner's per-query work).  run(n, f)
+// calls f(0) on the calling thread and f(1..n-1) on workers, and returns when
+// all have finished; workers sleep between runs.
+class PlanPool {
+public:
+    ~PlanPool()
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : th_) t.join();
+    }
+    int size() const { return (int)th_.size() + 1; }
+    void start(int workers)
+    {
+        for (int i = 0; i < workers; ++i) th_.emplace_back([this, i] { loop(i + 1); });
+    }
+    void run(int n, const std::function<void(int)> &f)
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            job_ = &f;
+            job_n_ = n;
+            pending_ = (int)th_.size();
+            ++gen_;
+        }
+        cv_.notify_all();
+        f(0);
+        std::unique_lock<std::mutex> lk(mu_);
+        done_.wait(lk, [&] { return pending_ == 0; });
+        job_ = nullptr;
+    }
+
+private:
+    void loop(int idx)
+    {
+        uint64_t seen = 0;
+        for (;;) {
+            std::unique_lock<std::mutex> lk(mu_);
+            cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+            if (stop_) return;
+            seen = gen_;
+            const std::function<void(int)> *f = job_;
+            const int n = job_n_;
+            lk.unlock();
+            if (idx < n) (*f)(idx);
+            lk.lock();
+            if (--pending_ == 0) done_.notify_one();
+        }
+    }
+    std::vector<std::thread> th_;
+    std::mutex mu_;
+    std::condition_variable cv_, done_;
+    const std::function<void(int)> *job_ = nullptr;
+    int job_n_ = 0, pending_ = 0;
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+};
+}  // namespace
+
 struct fc_ctx {
     int device = 0;
     int num_sms = 0;
@@ -165,6 +232,12 @@ struct fc_ctx {
     uint32_t epoch = 0;
     uint64_t generation = 0;  // bumped by every append; plans of older generations refuse to run
     std::vector<fc_plan *> live_plans;  // orphaned (device memory released) if the context goes first
+    // pinned staging of plan descriptors: written on the host, copied by DMA;
+    // the event marks the end of the last copy out of it
+    uint8_t *h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    cudaEvent_t h_stage_ev = nullptr;
+    std::unique_ptr<PlanPool> pool_threads;  // started by the first large plan
 };
 
 namespace {
@@ -255,6 +328,36 @@ struct BorrowScope {
     explicit BorrowScope(fc_ctx *ctx) : c(ctx) { c->borrow = true; }
     ~BorrowScope() { c->borrow = false; }
 };
+
+// Pinned host staging of at least `bytes` for plan descriptors, free of any
+// copy still reading it; nullptr on failure.
+uint8_t *stage_host(fc_ctx *c, size_t bytes)
+{
+    if (c->h_stage_ev && cudaEventSynchronize(c->h_stage_ev) != cudaSuccess) return nullptr;
+    if (bytes > c->h_stage_bytes) {
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        c->h_stage = nullptr;
+        c->h_stage_bytes = 0;
+        const size_t want = std::max(bytes, c->h_stage_bytes + c->h_stage_bytes / 2);
+        if (cudaHostAlloc((void **)&c->h_stage, want, cudaHostAllocDefault) != cudaSuccess) {
+            c->h_stage = nullptr;
+            return nullptr;
+        }
+        c->h_stage_bytes = want;
+    }
+    if (!c->h_stage_ev && cudaEventCreateWithFlags(&c->h_stage_ev, cudaEventDisableTiming) != cudaSuccess)
+        return nullptr;
+    return c->h_stage;
+}
+
+// Copies `bytes` of the staging buffer to dst on the context stream and
+// marks the staging buffer busy until the copy ends.
+cudaError_t upload_stage(fc_ctx *c, void *dst, size_t bytes)
+{
+    cudaError_t e = cudaMemcpyAsync(dst, c->h_stage, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->h_stage_ev, c->stream);
+    return e;
+}
 
 }  // namespace
 
@@ -435,6 +538,8 @@ extern "C" void fc_free(fc_ctx *c)
         p->ctx = nullptr;
     }
     c->live_plans.clear();
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->h_stage_ev) cudaEventDestroy(c->h_stage_ev);
     for (auto &b : c->io) b.release();
     for (auto &b : c->pool) b.release();
     cudaFree(c->d_D);
@@ -833,9 +938,16 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
         int err_code = 0;
         std::string err_msg;
     };
-    const int nthreads = nq >= 4096 ? (int)std::max<int64_t>(1, std::min<int64_t>({8, nq / 2048,
-                                          (int64_t)std::max(1u, std::thread::hardware_concurrency())}))
-                                    : 1;
+    int nthreads = 1;
+    if (nq >= 4096) {
+        if (!c->pool_threads) {
+            const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+            c->pool_threads.reset(new (std::nothrow) PlanPool());
+            if (c->pool_threads) c->pool_threads->start(std::max(0, std::min(7, hw - 1)));
+        }
+        if (c->pool_threads)
+            nthreads = (int)std::max<int64_t>(1, std::min<int64_t>(c->pool_threads->size(), nq / 1024));
+    }
     std::vector<Range> ranges(nthreads);
     auto work = [&](int t) {
         Range &R = ranges[t];
@@ -876,15 +988,10 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
             cost[q] = ch.cost;
         }
     };
-    if (nthreads == 1) {
+    if (nthreads == 1)
         work(0);
-    } else {
-        std::vector<std::thread> pool;
-        pool.reserve(nthreads - 1);
-        for (int t = 1; t < nthreads; ++t) pool.emplace_back(work, t);
-        work(0);
-        for (auto &th : pool) th.join();
-    }
+    else
+        c->pool_threads->run(nthreads, work);
     for (const Range &R : ranges)
         if (R.err_q >= 0) {  // the first failing range holds the lowest failing query
             fc_plan_free(p);
@@ -942,10 +1049,11 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
         parts = std::min<int64_t>({nchunks, max_parts_rows, (target + persistent - 1) / persistent, 32767});
     parts = std::max<int64_t>(1, parts);
     std::vector<Item> items;
-    std::vector<std::pair<double, Item>> order;
+    std::vector<int32_t> hq;  // queries that become work items of count_kernel
     std::vector<int32_t> qlist;
     std::vector<std::pair<double, int32_t>> bmo;
-    order.reserve((size_t)nq * (size_t)parts);
+    hq.reserve(nq);
+    size_t n_items = 0;
     for (int32_t q = 0; q < nq; ++q) {
         QHead &h = qh[q];
         if (h.strategy == kSort) {
@@ -958,13 +1066,18 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
         }
         const int64_t qparts = h.strategy == kMarginal ? 1 : parts;
         h.nparts = (int16_t)qparts;
-        for (int32_t part = 0; part < qparts; ++part) order.push_back({cost[q] / qparts, Item{q, part}});
+        hq.push_back(q);
+        n_items += (size_t)qparts;
     }
-    // heaviest first; within a cost class, query and part order
+    // heaviest first by cost per part; a query's parts are consecutive, and
+    // within a cost class queries keep their order
     std::vector<int32_t> perm;
-    order_by_cost_desc(order.size(), [&](size_t i) { return order[i].first; }, perm);
-    items.reserve(order.size());
-    for (int32_t i : perm) items.push_back(order[i].second);
+    order_by_cost_desc(hq.size(), [&](size_t i) { return cost[hq[i]] / qh[hq[i]].nparts; }, perm);
+    items.reserve(n_items);
+    for (int32_t i : perm) {
+        const int32_t q = hq[i];
+        for (int32_t part = 0; part < qh[q].nparts; ++part) items.push_back(Item{q, part});
+    }
     p->n_items = (int32_t)items.size();
     // bitmap queries: warp tasks of consecutive 4096-row chunks, heaviest
     // queries first.  A query gets tasks in proportion to its estimated cost
@@ -1001,10 +1114,16 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
             const double per = x.first / std::max(1, passes);
             const int64_t t = std::max<int64_t>(1, std::min<int64_t>(max_tasks, (int64_t)std::ceil(per / unit)));
             qh[q].nparts = (int16_t)std::min<int64_t>(t * std::max(1, passes), 32767);
-            for (int32_t s0 = passes > 0 ? 0 : -1; s0 < std::max(passes, 0); ++s0)
-                for (int64_t part = 0; part < t; ++part)
-                    btasks.push_back(
-                        BTask{q, (int32_t)(nchunks * part / t), (int32_t)(nchunks * (part + 1) / t), s0});
+            // t balanced chunk ranges: the first nchunks % t get one extra chunk
+            const int64_t base = nchunks / t, rem = nchunks % t;
+            for (int32_t s0 = passes > 0 ? 0 : -1; s0 < std::max(passes, 0); ++s0) {
+                int64_t c0 = 0;
+                for (int64_t part = 0; part < t; ++part) {
+                    const int64_t c1 = c0 + base + (part < rem ? 1 : 0);
+                    btasks.push_back(BTask{q, (int32_t)c0, (int32_t)c1, s0});
+                    c0 = c1;
+                }
+            }
         }
     }
     p->n_btasks = (int32_t)btasks.size();
@@ -1045,14 +1164,18 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     const size_t o_qv = round_up(b_qh, 256), o_it = o_qv + round_up(b_qv, 256), o_ql = o_it + round_up(b_it, 256);
     const size_t o_bq = o_ql + round_up(b_ql, 256);
     const size_t total = o_bq + round_up(b_bq, 256);
-    std::vector<uint8_t> host(total, 0);
-    std::memcpy(host.data(), qh.data(), sizeof(QHead) * nq);
-    std::memcpy(host.data() + o_qv, qv.data(), sizeof(QVar) * qv.size());
-    std::memcpy(host.data() + o_it, items.data(), sizeof(Item) * items.size());
-    std::memcpy(host.data() + o_ql, qlist.data(), sizeof(int32_t) * qlist.size());
-    std::memcpy(host.data() + o_bq, btasks.data(), sizeof(BTask) * btasks.size());
+    uint8_t *host = stage_host(c, total);
+    if (!host) {
+        fc_plan_free(p);
+        return fail(FC_ERR_OOM, "pinned staging of %zu bytes", total);
+    }
+    std::memcpy(host, qh.data(), sizeof(QHead) * nq);
+    std::memcpy(host + o_qv, qv.data(), sizeof(QVar) * qv.size());
+    std::memcpy(host + o_it, items.data(), sizeof(Item) * items.size());
+    std::memcpy(host + o_ql, qlist.data(), sizeof(int32_t) * qlist.size());
+    std::memcpy(host + o_bq, btasks.data(), sizeof(BTask) * btasks.size());
     cudaError_t e = plan_buf(c, p->desc, 0, total);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->desc.p, host.data(), total, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = upload_stage(c, p->desc.p, total);
     p->upload_bytes = total;
     p->n_counters = 2 + nq;
     if (e == cudaSuccess) e = plan_buf(c, p->counters, 1, sizeof(int32_t) * p->n_counters);
@@ -1072,7 +1195,10 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
             p->sort_sc.cap_blocks = (int32_t)nb;
         }
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    // a plan lent to a synchronous call runs on the context stream, after
+    // its upload; a plan the caller keeps may run on any stream, so its
+    // upload must be complete on return
+    if (e == cudaSuccess && !c->borrow) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         fc_plan_free(p);
         return cuda_fail(e, "plan upload");
@@ -1607,19 +1733,26 @@ int build_set_plan(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t 
     const size_t o_it = round_up(b_off, 256), o_ord = o_it + round_up(b_it, 256);
     const size_t o_spl = o_ord + round_up(sizeof(int32_t) * std::max(nq, 1), 256);
     const size_t total = o_spl + (mode == 2 ? round_up(sizeof(int64_t) * (nq + 1), 256) : 0);
-    std::vector<uint8_t> host(total, 0);
-    if (nq > 0) {
-        std::memcpy(host.data(), set_off, b_off);
-        if (n_sub > 0) std::memcpy(host.data() + o_it, items, sizeof(int32_t) * n_sub);
-        std::memcpy(host.data() + o_ord, order.data(), sizeof(int32_t) * nq);
+    uint8_t *host = stage_host(c, total);
+    if (!host) {
+        fc_plan_free(p);
+        return fail(FC_ERR_OOM, "pinned staging of %zu bytes", total);
     }
-    if (mode == 2) std::memcpy(host.data() + o_spl, split_off.data(), sizeof(int64_t) * (nq + 1));
+    if (nq > 0) {
+        std::memcpy(host, set_off, b_off);
+        if (n_sub > 0) std::memcpy(host + o_it, items, sizeof(int32_t) * n_sub);
+        std::memcpy(host + o_ord, order.data(), sizeof(int32_t) * nq);
+    }
+    if (mode == 2) std::memcpy(host + o_spl, split_off.data(), sizeof(int64_t) * (nq + 1));
     cudaError_t e = plan_buf(c, p->desc, 0, total);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->desc.p, host.data(), total, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = upload_stage(c, p->desc.p, total);
     p->upload_bytes = total;
     if (e == cudaSuccess) e = plan_buf(c, p->counters, 1, 16);
     if (e == cudaSuccess) e = plan_buf(c, p->scratch_tables, 2, sizeof(int32_t) * std::max<int64_t>(p->n_sub, 1));
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    // a plan lent to a synchronous call runs on the context stream, after
+    // its upload; a plan the caller keeps may run on any stream, so its
+    // upload must be complete on return
+    if (e == cudaSuccess && !c->borrow) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         fc_plan_free(p);
         return cuda_fail(e, "plan upload");
