@@ -834,6 +834,48 @@ def run_append_gpu(args, rank, world, fc, torch, barrier, dist, dev):
     return line
 
 
+def measure_gemm_peaks():
+    """Dense GEMM rates of the vendor library on this GPU (bf16, fp8 e4m3,
+    int8), for the roofline denominators of the one-hot contraction; prints
+    one JSON line.  Not part of any timed workload."""
+    import torch
+    res = {}
+    n = 8192
+    a16 = torch.randn(n, n, device="cuda", dtype=torch.bfloat16)
+    b16 = torch.randn(n, n, device="cuda", dtype=torch.bfloat16)
+
+    def rate(fn, flops, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return flops * reps / (e0.elapsed_time(e1) / 1e3) / 1e12
+
+    res["bf16_tflops"] = rate(lambda: a16 @ b16, 2.0 * n ** 3)
+    try:
+        a8 = a16.to(torch.float8_e4m3fn)
+        b8 = b16.to(torch.float8_e4m3fn).t().contiguous().t()
+        one = torch.tensor(1.0, device="cuda")
+        res["fp8_e4m3_tflops"] = rate(lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one,
+                                                               out_dtype=torch.bfloat16), 2.0 * n ** 3)
+    except Exception as e:  # noqa: BLE001
+        res["fp8_e4m3_tflops"] = f"unavailable: {type(e).__name__}"
+    try:
+        ai = torch.randint(-8, 8, (n, n), device="cuda", dtype=torch.int8)
+        bi = torch.randint(-8, 8, (n, n), device="cuda", dtype=torch.int8)
+        res["int8_tops"] = rate(lambda: torch._int_mm(ai, bi), 2.0 * n ** 3)
+    except Exception as e:  # noqa: BLE001
+        res["int8_tops"] = f"unavailable: {type(e).__name__}"
+    res["shape"] = f"{n} x {n} x {n}"
+    res["library"] = "torch matmul / _scaled_mm / _int_mm (cuBLAS / cuBLASLt)"
+    print(json.dumps(res), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -850,7 +892,12 @@ def main():
     ap.add_argument("--strategy", type=int, default=-1, help="force one counting strategy (-1 = planner's choice)")
     ap.add_argument("--m", type=int, default=None, help="instances (default: the workload's own)")
     ap.add_argument("--nq", type=int, default=None, help="queries / itemsets (default: the workload's own)")
+    ap.add_argument("--gemm-peaks", action="store_true",
+                    help="only measure the vendor library's dense GEMM rates (bf16, fp8, int8) and exit")
     args = ap.parse_args()
+    if args.gemm_peaks:
+        measure_gemm_peaks()
+        return
     if args.warmup < 3:
         args.warmup = 3
     rank = int(os.environ.get("RANK", "0"))

@@ -116,12 +116,35 @@ def test_support_as_benchmarked():
             torch.empty(len(it), dtype=torch.float32, device="cuda")]
     supp, sub, conf = _replay(plan, outs, torch)
     owner = np.repeat(np.arange(len(sets)), np.diff(so))
+    # invariants on all 1e6 itemsets: anti-monotone supports, confidences in
+    # [0, 1] equal to the float quotient of the reported supports
     assert np.all(supp[owner] <= sub)
+    want_conf = np.where(sub > 0, supp[owner].astype(np.float32) / np.maximum(sub, 1).astype(np.float32), 0)
+    assert np.array_equal(conf, want_conf.astype(np.float32))
+    assert np.all((conf >= 0) & (conf <= 1))
+    # exact parity on 32 itemsets against the C oracle's transaction scan ...
     idx = np.random.default_rng(9).choice(len(sets), size=32, replace=False)
     for q, (s, sb, c) in zip(idx, _pool_map(lambda q: oracle.support_rules(bits, m, sets[q]), idx)):
         a, b = so[q], so[q + 1]
         assert supp[q] == s and np.array_equal(sub[a:b].astype(np.int64), sb)
         assert np.allclose(conf[a:b], c, rtol=1e-6, atol=0)
+    # ... and on 4,096 more (every size) against the oracle's item-matrix
+    # definition, unpacking only the items each itemset names
+    from oracle import miner
+    rng = np.random.default_rng(10)
+    sizes = np.diff(so)
+    idx = np.concatenate([rng.choice(np.flatnonzero(sizes == k), size=1024, replace=False)
+                          for k in range(2, 6)])
+
+    def one(q):
+        S = sets[q]
+        X = miner.item_matrix_from_bits(bits[S], m)
+        loc = list(range(len(S)))
+        return (miner.itemset_support(X, loc),
+                [miner.itemset_support(X, loc[:t] + loc[t + 1:]) for t in range(len(S))])
+
+    for q, (s, sb) in zip(idx, _pool_map(one, idx)):
+        assert supp[q] == s and sub[so[q]:so[q + 1]].tolist() == sb, q
 
 
 def test_families_as_benchmarked():
