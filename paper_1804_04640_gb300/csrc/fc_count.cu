@@ -917,8 +917,11 @@ __global__ void family_score_kernel(const FamilyJob *__restrict__ jobs, int64_t 
                                     const int32_t *__restrict__ soff, const int64_t *__restrict__ marg,
                                     int64_t m, int kind, double ess, float *scores)
 {
-    __shared__ ScoreAcc s_red[32];
-    for (int64_t jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
+    // one warp per job: most families' tables have a few hundred cells, so
+    // a warp-level reduction replaces the block barriers
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t jb = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); jb < njobs; jb += warps) {
         const FamilyJob job = jobs[jb];
         int32_t ar[kMaxFamily];
         int64_t st[kMaxFamily];
@@ -940,11 +943,11 @@ __global__ void family_score_kernel(const FamilyJob *__restrict__ jobs, int64_t 
         }
         const int32_t rc = ar[job.child_pos];
         rows.cstep = st[job.child_pos];
-        const BdeuK bk = block_bdeu_consts(kind, q, rc, ess);
-        const ScoreAcc acc = score_rows<true>(tables + job.table_off, rows, q, rc, kind,
-                                              marg + soff[job.vars[job.child_pos]], m, bk, threadIdx.x, blockDim.x);
-        const float s = block_finish(acc, s_red, kind, m, rc, q, bk);
-        if (threadIdx.x == 0) scores[job.slot] = s;
+        const BdeuK bk = warp_bdeu_consts(kind, q, rc, ess);
+        ScoreAcc acc = score_rows<true>(tables + job.table_off, rows, q, rc, kind,
+                                        marg + soff[job.vars[job.child_pos]], m, bk, lane, 32);
+        warp_merge(acc);
+        if (lane == 0) scores[job.slot] = score_finish(acc, kind, m, rc, q, bk);
     }
 }
 
