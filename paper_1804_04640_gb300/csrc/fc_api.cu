@@ -939,15 +939,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
         std::string err_msg;
     };
     int nthreads = 1;
-    if (nq >= 4096) {
-        if (!c->pool_threads) {
-            const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-            c->pool_threads.reset(new (std::nothrow) PlanPool());
-            if (c->pool_threads) c->pool_threads->start(std::max(0, std::min(7, hw - 1)));
-        }
-        if (c->pool_threads)
-            nthreads = (int)std::max<int64_t>(1, std::min<int64_t>(c->pool_threads->size(), nq / 1024));
-    }
+    if (nq >= 4096) nthreads = (int)std::max<int64_t>(1, std::min<int64_t>(fc::host_threads(c), nq / 1024));
     std::vector<Range> ranges(nthreads);
     auto work = [&](int t) {
         Range &R = ranges[t];
@@ -988,10 +980,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
             cost[q] = ch.cost;
         }
     };
-    if (nthreads == 1)
-        work(0);
-    else
-        c->pool_threads->run(nthreads, work);
+    fc::run_host_threads(c, nthreads, work);
     for (const Range &R : ranges)
         if (R.err_q >= 0) {  // the first failing range holds the lowest failing query
             fc_plan_free(p);
@@ -1696,6 +1685,28 @@ int plan_itemsets(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t *
 
 namespace {
 
+// CTAs of a support-family kernel per SM (cached per device, mode, block size).
+int support_ctas_per_sm(int mode, int threads)
+{
+    static std::mutex mu;
+    static int cache[64][3][33];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int ti = std::min(32, threads / 32);
+    if (dev >= 0 && dev < 64 && mode >= 0 && mode < 3) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (cache[dev][mode][ti] > 0) return cache[dev][mode][ti];
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, support_kernel_ptr(mode), threads, 0);
+    per_sm = std::max(1, per_sm);
+    if (dev >= 0 && dev < 64 && mode >= 0 && mode < 3) {
+        std::lock_guard<std::mutex> lk(mu);
+        cache[dev][mode][ti] = per_sm;
+    }
+    return per_sm;
+}
+
 // A plan over sets of bitmap rows: itemset supports with their leave-one-out
 // supports (mode 0), the support of each set alone (mode 1, specific-
 // assignment counts), or the supports of every antecedent split (mode 2).
@@ -1769,10 +1780,6 @@ int build_set_plan(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t 
     P.n_items = c->n;
     p->sup_threads = std::max(1, std::min(32, o.support_warps)) * 32;
     P.sets_per_item = (p->sup_threads / 32) * std::max(1, o.support_sets_per_warp);
-    // word ranges of whole 64-word steps (32 lanes x 2 words)
-    const int64_t part_words = std::max<int64_t>(64, round_up(o.support_part_words, 64));
-    P.nparts = (int32_t)std::max<int64_t>(1, (c->words + part_words - 1) / part_words);
-    P.words_per_part = (int32_t)round_up((c->words + P.nparts - 1) / P.nparts, 64);
     P.m_tail = c->m;
     P.full_only = full_only;
     P.all_splits = mode == 2;
@@ -1782,9 +1789,18 @@ int build_set_plan(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t 
         p->sup_threads = std::min(p->sup_threads, 256);
         P.sets_per_item = (p->sup_threads / 32) * std::max(1, o.support_sets_per_warp);
     }
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, support_kernel_ptr(mode), p->sup_threads, 0);
-    p->sup_grid = c->num_sms * std::max(1, per_sm);
+    p->sup_grid = c->num_sms * support_ctas_per_sm(mode, p->sup_threads);
+    // word ranges of whole 64-word steps (32 lanes x 2 words): at most
+    // support_part_words each, and more of them when the batch has too few
+    // itemset groups to give every CTA two work items (a small rule-miner
+    // level, a handful of long itemsets)
+    const int64_t part_words = std::max<int64_t>(64, round_up(o.support_part_words, 64));
+    const int64_t ngroups = std::max<int64_t>(1, ((int64_t)nq + P.sets_per_item - 1) / P.sets_per_item);
+    int64_t nparts = std::max<int64_t>(1, (c->words + part_words - 1) / part_words);
+    const int64_t want = (2 * (int64_t)p->sup_grid + ngroups - 1) / ngroups;
+    nparts = std::max(nparts, std::min(want, std::max<int64_t>(1, (c->words + 63) / 64)));
+    P.nparts = (int32_t)std::min<int64_t>(nparts, 1 << 20);
+    P.words_per_part = (int32_t)round_up((c->words + P.nparts - 1) / P.nparts, 64);
     *out = p;
     return FC_OK;
 }
@@ -1814,6 +1830,25 @@ extern "C" int fc_plan_assignments(fc_ctx *c, int32_t nq, const int32_t *var_off
         }
     }
     return build_set_plan(c, nq, var_off, rows.data(), 1, out);
+}
+
+int fc::host_threads(fc_ctx *c)
+{
+    if (!c->pool_threads) {
+        const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+        c->pool_threads.reset(new (std::nothrow) PlanPool());
+        if (c->pool_threads) c->pool_threads->start(std::max(0, std::min(7, hw - 1)));
+    }
+    return c->pool_threads ? c->pool_threads->size() : 1;
+}
+
+void fc::run_host_threads(fc_ctx *c, int n, const std::function<void(int)> &f)
+{
+    if (n <= 1 || !c->pool_threads) {
+        for (int i = 0; i < std::max(n, 0); ++i) f(i);
+        return;
+    }
+    c->pool_threads->run(std::min(n, c->pool_threads->size()), f);
 }
 
 void fc::itemset_universe(const fc_ctx *c, int32_t *n_items, int64_t *m)

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+
 namespace fc {
 
 constexpr int kMaxK = 32;          // variables of one query in a device descriptor
@@ -211,6 +213,11 @@ int set_error(int code, const char *fmt, ...);
 // ---- items of a context, for the rule miner (fc_rules.cu)
 struct fc_ctx;
 namespace fc {
+// The context's host worker threads (started on first use): how many can run
+// at once (the caller counts as one), and f(0..n-1) run on them, f(0) on the
+// caller; returns when all are done.  n must not exceed host_threads(c).
+int host_threads(fc_ctx *c);
+void run_host_threads(fc_ctx *c, int n, const std::function<void(int)> &f);
 // Number of items (bitmap rows) of a context and its instance count m.
 void itemset_universe(const fc_ctx *c, int32_t *n_items, int64_t *m);
 // For each item: the variable it belongs to (an item of a categorical context

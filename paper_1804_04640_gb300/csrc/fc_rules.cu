@@ -91,17 +91,15 @@ namespace {
 // Level k candidates from the frequent (k-1)-itemsets (k >= 2): two sets that
 // share their first k-2 items join into prefix + {x, y} (x < y, different
 // groups), kept when every other (k-1)-subset is frequent too.  The order of
-// `prev` makes the candidates come out lexicographically sorted.
-void generate(const Level &prev, const std::vector<int32_t> &group, int k, std::vector<int32_t> &cand)
+// `prev` makes the candidates come out lexicographically sorted.  Prefix
+// groups [g0, g1) of prev, indexed by the run starts in `runs`.
+void generate_runs(const Level &prev, const std::vector<int32_t> &group, int k, const std::vector<int64_t> &runs,
+                   int64_t g0, int64_t g1, std::vector<int32_t> &cand)
 {
-    cand.clear();
-    const int64_t n = prev.size();
     const int pk = k - 2;  // shared prefix length
     std::vector<int32_t> T(k), sub(k - 1);
-    int64_t i = 0;
-    while (i < n) {
-        int64_t j = i + 1;
-        while (j < n && std::memcmp(prev.at(i), prev.at(j), sizeof(int32_t) * pk) == 0) ++j;
+    for (int64_t g = g0; g < g1; ++g) {
+        const int64_t i = runs[g], j = runs[g + 1];
         for (int64_t a = i; a < j; ++a) {
             const int32_t x = prev.at(a)[pk];
             for (int64_t b = a + 1; b < j; ++b) {
@@ -120,8 +118,49 @@ void generate(const Level &prev, const std::vector<int32_t> &group, int k, std::
                 if (ok) cand.insert(cand.end(), T.begin(), T.end());
             }
         }
+    }
+}
+
+// All level-k candidates, the prefix groups split over the context's host
+// threads by their pair counts; per-thread lists are joined in group order,
+// so the result does not depend on the split.
+void generate(fc_ctx *c, const Level &prev, const std::vector<int32_t> &group, int k, std::vector<int32_t> &cand)
+{
+    cand.clear();
+    const int64_t n = prev.size();
+    const int pk = k - 2;
+    std::vector<int64_t> runs;  // starts of the prefix groups, then n
+    double work = 0.0;
+    for (int64_t i = 0; i < n;) {
+        int64_t j = i + 1;
+        while (j < n && std::memcmp(prev.at(i), prev.at(j), sizeof(int32_t) * pk) == 0) ++j;
+        runs.push_back(i);
+        work += 0.5 * (double)(j - i) * (double)(j - i - 1);
         i = j;
     }
+    runs.push_back(n);
+    const int64_t ngroups = (int64_t)runs.size() - 1;
+    const int nt = work > 4000.0 ? (int)std::min<int64_t>(fc::host_threads(c), ngroups) : 1;
+    if (nt <= 1) {
+        generate_runs(prev, group, k, runs, 0, ngroups, cand);
+        return;
+    }
+    // split points of roughly equal pair counts
+    std::vector<int64_t> cut(nt + 1, ngroups);
+    cut[0] = 0;
+    double acc = 0.0;
+    int t = 1;
+    for (int64_t g = 0; g < ngroups && t < nt; ++g) {
+        const double sz = (double)(runs[g + 1] - runs[g]);
+        acc += 0.5 * sz * (sz - 1.0);
+        if (acc >= work * t / nt) cut[t++] = g + 1;
+    }
+    std::vector<std::vector<int32_t>> part(nt);
+    fc::run_host_threads(c, nt, [&](int i) { generate_runs(prev, group, k, runs, cut[i], cut[i + 1], part[i]); });
+    size_t total = 0;
+    for (auto &v : part) total += v.size();
+    cand.reserve(total);
+    for (auto &v : part) cand.insert(cand.end(), v.begin(), v.end());
 }
 
 // Device counts of `nc` candidates of k items, in batches that keep the
@@ -179,7 +218,7 @@ extern "C" int fc_mine_rules(fc_ctx *ctx, double min_support, double min_confide
 
     std::vector<int32_t> cand, counts;
     for (int k = 2; k <= max_size && levels.back().size() > 0; ++k) {
-        generate(levels.back(), group, k, cand);
+        generate(ctx, levels.back(), group, k, cand);
         const int64_t nc = (int64_t)cand.size() / k;
         if (nc == 0) break;
         if (nc > INT32_MAX) {
@@ -206,7 +245,6 @@ extern "C" int fc_mine_rules(fc_ctx *ctx, double min_support, double min_confide
     }
 
     // itemsets, then rules A => S \ A in itemset order and mask order
-    std::vector<int32_t> A;
     std::vector<uint32_t> masks;
     int64_t idx = 0;
     int64_t total_items = 0;
@@ -222,6 +260,12 @@ extern "C" int fc_mine_rules(fc_ctx *ctx, double min_support, double min_confide
             R->support.push_back(L.supp[s]);
         }
     }
+    struct RuleOut {
+        std::vector<int64_t> set;
+        std::vector<uint32_t> mask;
+        std::vector<float> conf;
+        bool missing = false;
+    };
     for (const Level &L : levels) {
         const int k = L.k;
         if (k < 2) {
@@ -236,27 +280,49 @@ extern "C" int fc_mine_rules(fc_ctx *ctx, double min_support, double min_confide
             for (uint32_t mk = 1; mk < full; ++mk) masks.push_back(mk);
         else
             for (int t = k - 1; t >= 0; --t) masks.push_back(full ^ (1u << t));
-        for (int64_t s = 0; s < L.size(); ++s, ++idx) {
-            const int32_t *S = L.at(s);
-            for (const uint32_t mk : masks) {
-                const int na = popcount32(mk);
-                A.clear();
-                for (int t = 0; t < k; ++t)
-                    if (mk >> t & 1u) A.push_back(S[t]);
-                const Level &LA = levels[na - 1];
-                const int64_t ia = LA.find(A.data());
-                if (ia < 0) {  // cannot happen: every subset of a frequent set is frequent
-                    fc_rules_free(R);
-                    return set_error(FC_ERR_STATE, "internal: missing subset of a frequent itemset");
-                }
-                const int64_t sa = LA.supp[ia];
-                if ((double)L.supp[s] > min_confidence * (double)sa) {
-                    R->rule_set.push_back(idx);
-                    R->rule_mask.push_back(mk);
-                    R->rule_conf.push_back((float)((double)L.supp[s] / (double)sa));
+        // itemsets of the level in contiguous ranges on the host threads,
+        // each range's rules kept in order and joined in range order
+        const int64_t ns = L.size();
+        const int nt = ns * (int64_t)masks.size() > 4000 ? (int)std::min<int64_t>(fc::host_threads(ctx), ns) : 1;
+        std::vector<RuleOut> outs(nt);
+        const int64_t base = idx;
+        auto rules_of = [&](int t) {
+            RuleOut &o = outs[t];
+            std::vector<int32_t> A;
+            const int64_t s0 = ns * t / nt, s1 = ns * (t + 1) / nt;
+            for (int64_t s = s0; s < s1; ++s) {
+                const int32_t *S = L.at(s);
+                for (const uint32_t mk : masks) {
+                    const int na = popcount32(mk);
+                    A.clear();
+                    for (int u = 0; u < k; ++u)
+                        if (mk >> u & 1u) A.push_back(S[u]);
+                    const Level &LA = levels[na - 1];
+                    const int64_t ia = LA.find(A.data());
+                    if (ia < 0) {  // cannot happen: every subset of a frequent set is frequent
+                        o.missing = true;
+                        return;
+                    }
+                    const int64_t sa = LA.supp[ia];
+                    if ((double)L.supp[s] > min_confidence * (double)sa) {
+                        o.set.push_back(base + s);
+                        o.mask.push_back(mk);
+                        o.conf.push_back((float)((double)L.supp[s] / (double)sa));
+                    }
                 }
             }
+        };
+        fc::run_host_threads(ctx, nt, rules_of);
+        for (RuleOut &o : outs) {
+            if (o.missing) {
+                fc_rules_free(R);
+                return set_error(FC_ERR_STATE, "internal: missing subset of a frequent itemset");
+            }
+            R->rule_set.insert(R->rule_set.end(), o.set.begin(), o.set.end());
+            R->rule_mask.insert(R->rule_mask.end(), o.mask.begin(), o.mask.end());
+            R->rule_conf.insert(R->rule_conf.end(), o.conf.begin(), o.conf.end());
         }
+        idx += ns;
     }
     *out = R;
     return FC_OK;
