@@ -210,3 +210,102 @@ def test_rules_as_benchmarked():
             if keep:
                 assert rules[(i, mk)] == np.float32(float(sp[i]) / float(sa))
     assert len(rules) == len(r["rule_set"])
+
+
+def test_tiny_and_large_as_benchmarked():
+    """The 92-query tiny batch in full and the large-table batch (global-atomic
+    path) sampled, through autotuned, graph-replayed plans."""
+    torch = pytest.importorskip("torch")
+    for name, sample in (("tiny", None), ("large", 12)):
+        w = bench.make_workload(name)
+        db, queries = w["db"], w["queries"]
+        ctx = fc.fc_load(db.D, db.arities)
+        off, flat = fc.pack_lists(queries)
+        fc.fc_autotune_batch(ctx, off, flat)
+        plan = fc.fc_plan_count(ctx, off, flat)
+        toff = fc.fc_plan_table_offsets(plan)
+        (tables,) = _replay(plan, [torch.empty(int(toff[-1]), dtype=torch.int32, device="cuda")], torch)
+        orc = oracle.DB(db.D, db.arities)
+        idx = range(len(queries)) if sample is None else \
+            np.random.default_rng(3).choice(len(queries), size=sample, replace=False)
+        want = _pool_map(lambda q: orc.table(queries[q]), idx)
+        for q, t in zip(idx, want):
+            assert np.array_equal(tables[toff[q]:toff[q + 1]].astype(np.int64), t), (name, q)
+        for q in range(len(queries)):
+            assert int(tables[toff[q]:toff[q + 1]].astype(np.int64).sum()) == db.m
+
+
+def test_assign_as_benchmarked():
+    torch = pytest.importorskip("torch")
+    w = bench.make_workload("assign")
+    db = w["db"]
+    ctx = fc.fc_load(db.D, db.arities)
+    vo, vv = fc.pack_lists([q[0] for q in w["assign"]])
+    _, ss = fc.pack_lists([q[1] for q in w["assign"]])
+    plan = fc.fc_plan_assignments(ctx, vo, vv, ss)
+    (counts,) = _replay(plan, [torch.empty(len(w["assign"]), dtype=torch.int32, device="cuda")], torch)
+    orc = oracle.DB(db.D, db.arities)
+    idx = np.random.default_rng(4).choice(len(w["assign"]), size=2000, replace=False)
+    want = _pool_map(lambda q: orc.count_assignment(*w["assign"][q]), idx)
+    assert [int(counts[q]) for q in idx] == want
+
+
+def test_splits_as_benchmarked():
+    """All-splits plan at full size: 64 itemsets (16 of each size) exact
+    against the item-matrix definition, and invariants on every split."""
+    torch = pytest.importorskip("torch")
+    from oracle import miner
+    w = bench.make_workload("splits")
+    bits, m, sets = w["bits"], w["m"], w["sets"]
+    ctx = fc.fc_load_bits(bits, m)
+    so, it = fc.pack_lists(sets)
+    plan = fc.fc_plan_support_splits(ctx, so, it)
+    ns = fc.fc_plan_size(plan, 3)
+    outs = [torch.empty(len(sets), dtype=torch.int32, device="cuda"),
+            torch.empty(ns, dtype=torch.int32, device="cuda"),
+            torch.empty(ns, dtype=torch.float32, device="cuda")]
+    supp, sub, conf = _replay(plan, outs, torch)
+    off = fc.split_offsets(so)
+    owner = np.repeat(np.arange(len(sets)), np.diff(off))
+    assert np.all(supp[owner] <= sub)
+    want_conf = np.where(sub > 0, supp[owner].astype(np.float32) / np.maximum(sub, 1).astype(np.float32), 0)
+    assert np.array_equal(conf, want_conf.astype(np.float32))
+    sizes = np.diff(so)
+    rng = np.random.default_rng(12)
+    idx = np.concatenate([rng.choice(np.flatnonzero(sizes == k), size=16, replace=False) for k in range(2, 6)])
+
+    def one(q):
+        S = sets[q]
+        X = miner.item_matrix_from_bits(bits[S], m)
+        k = len(S)
+        return (miner.itemset_support(X, list(range(k))),
+                [miner.itemset_support(X, [t for t in range(k) if mk >> t & 1]) for mk in range(1, (1 << k) - 1)])
+
+    for q, (s, sb) in zip(idx, _pool_map(one, idx)):
+        assert supp[q] == s and sub[off[q]:off[q + 1]].tolist() == sb, q
+
+
+def test_append_as_benchmarked():
+    """The append workload's context after warm-up-sized appends from device
+    memory equals one load of the same rows (marginals and a query batch)."""
+    torch = pytest.importorskip("torch")
+    w = bench.make_workload("append")
+    db, m0, B = w["db"], w["m0"], w["block"]
+    D = np.ascontiguousarray(db.D)
+    ctx = fc.fc_load(D[:, :m0], db.arities)
+    fc.fc_reserve(ctx, m0 + 4 * B)
+    block = torch.from_numpy(np.ascontiguousarray(D[:, m0:m0 + B])).cuda()
+    for _ in range(3):
+        fc.fc_append(ctx, block)
+    full = np.concatenate([D[:, :m0]] + [D[:, m0:m0 + B]] * 3, axis=1)
+    ref = fc.fc_load(full, db.arities)
+    assert fc.fc_info(ctx, 1) == full.shape[1]
+    assert np.array_equal(fc.fc_marginals(ctx), fc.fc_marginals(ref))
+    queries = [[0, 1, 2], [5, 9], [10, 20, 30, 40], [63]]
+    off, flat = fc.pack_lists(queries)
+    a = fc.fc_count_batch(ctx, off, flat)[0]
+    assert np.array_equal(a, fc.fc_count_batch(ref, off, flat)[0])
+    orc = oracle.DB(full, db.arities)
+    toff = np.concatenate([[0], np.cumsum([int(np.prod([db.arities[v] for v in q])) for q in queries])])
+    for q, t in zip(range(len(queries)), _pool_map(lambda q: orc.table(queries[q]), range(len(queries)))):
+        assert np.array_equal(a[toff[q]:toff[q + 1]].astype(np.int64), t)
