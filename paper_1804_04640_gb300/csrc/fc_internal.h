@@ -1,5 +1,6 @@
 // fc_internal.h -- device descriptors and kernel launchers shared by the
-// host runtime (fc_api.cu) and the kernel translation units.
+// host runtime (fc_host.h and its translation units) and the kernel
+// translation units.
 #pragma once
 
 #include <cuda_runtime.h>

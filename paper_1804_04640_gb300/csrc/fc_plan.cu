@@ -1,0 +1,861 @@
+// fc_plan.cu -- the count and score planner (validation, strategy choice by
+// a cost model, work items in longest-first order, bitmap tasks), plan
+// execution as CUDA graphs, the plan API and the host-buffer count and score
+// calls.
+#include "fc_host.h"
+
+#include <cmath>
+#include <cstdio>
+#include <numeric>
+
+using namespace fc;
+
+// ------------------------------------------------------------------ planner
+
+namespace fc {
+
+// Validates one query's variables and appends its QVars (arity-1 variables
+// dropped, strides of the caller's order, last fastest); returns the cells.
+// Reads the context only, so planner threads may call it concurrently (an
+// error's message goes to the calling thread's fc_last_error).
+int64_t describe(const fc_ctx *c, const int32_t *vars, int32_t k, std::vector<QVar> &qv, int32_t &k_eff)
+{
+    if (k < 0 || k > c->n) return fail(FC_ERR_ARG, "query has %d variables, n = %d", k, c->n);
+    if (k > 0 && !vars) return fail(FC_ERR_ARG, "null variable list");
+    int64_t cells = 1;
+    for (int t = 0; t < k; ++t) {
+        const int v = vars[t];
+        if (v < 0 || v >= c->n) return fail(FC_ERR_ARG, "variable %d out of range 0..%d", v, c->n - 1);
+        cells *= c->arity[v];
+        if (cells > INT32_MAX) return fail(FC_ERR_SIZE, "table over %d variables exceeds 2^31-1 cells", k);
+    }
+    // duplicates: pairwise for short lists, a sorted copy otherwise
+    if (k <= 48) {
+        for (int t = 1; t < k; ++t)
+            for (int u = 0; u < t; ++u)
+                if (vars[u] == vars[t]) return fail(FC_ERR_ARG, "variable %d listed twice in one query", vars[t]);
+    } else {
+        std::vector<int32_t> sorted(vars, vars + k);
+        std::sort(sorted.begin(), sorted.end());
+        for (int t = 1; t < k; ++t)
+            if (sorted[t] == sorted[t - 1]) return fail(FC_ERR_ARG, "variable %d listed twice in one query", sorted[t]);
+    }
+    int64_t stride = 1;
+    const size_t first = qv.size();
+    for (int t = k - 1; t >= 0; --t) {
+        const int v = vars[t];
+        if (c->arity[v] > 1) qv.push_back(QVar{v, (int32_t)stride, c->arity[v], c->soff[v]});
+        stride *= c->arity[v];
+    }
+    std::reverse(qv.begin() + first, qv.end());
+    k_eff = (int32_t)(qv.size() - first);
+    return cells;
+}
+
+// DFS nodes of the bitmap tree in the given variable order (no pruning).
+double dfs_nodes(const QVar *v, int k)
+{
+    double nodes = 0.0, level = 1.0;
+    for (int t = 0; t < k; ++t) {
+        level *= v[t].arity;
+        nodes += level;
+    }
+    return nodes;
+}
+
+struct QPlan {
+    int32_t strategy;
+    double cost;  // femtoseconds for the whole query
+};
+
+// The bitmap DFS visits variables in ascending entropy (Sec. 3.2); a warp
+// stages the state bitmaps of every level but the first.
+void entropy_order(const fc_ctx *c, QVar *v, int k)
+{
+    // stable insertion sort: k is small and this runs once or twice per query
+    for (int i = 1; i < k; ++i) {
+        const QVar x = v[i];
+        const double h = c->entropy[x.var];
+        int j = i - 1;
+        while (j >= 0 && c->entropy[v[j].var] > h) {
+            v[j + 1] = v[j];
+            --j;
+        }
+        v[j + 1] = x;
+    }
+}
+
+// Staged slots of the query in entropy order; the ordered copy goes to o.
+// Queries the bitmap kernel counts on its register-blocked path (no tree
+// walk): 2 variables, or 3 whose last two in entropy order, of arities 2..5;
+// `o` is in entropy order.  Work units per 4096-row chunk: cells plus the
+// state rows loaded.
+bool small_ok(const QVar *o, int k)
+{
+    auto ok = [](int r) { return r >= 2 && r <= 5; };
+    if (k == 2) return ok(o[0].arity) && ok(o[1].arity);
+    if (k == 3) return ok(o[1].arity) && ok(o[2].arity);
+    return false;
+}
+
+double small_units(const QVar *o, int k)
+{
+    if (k == 2) return (double)o[0].arity * o[1].arity + o[0].arity + o[1].arity;
+    const double rb = o[1].arity, rc = o[2].arity;
+    return (double)o[0].arity * (1.0 + rb + rc + rb * rc);
+}
+
+bool bitmap_ok(const fc_ctx *c, const QVar *v, int k, QVar *o)
+{
+    if (k < 1 || k > kMaxBitmapK) return false;
+    std::copy(v, v + k, o);
+    entropy_order(c, o, k);
+    int slots = 0;
+    for (int t = 1; t < k; ++t) slots += o[t].arity;
+    return slots <= c->opt.stage_slots;
+}
+
+// Strategy and cost of one query.  When the bitmap strategy is chosen, the
+// variables are left in v in entropy order (the order its kernel walks).
+QPlan choose(const fc_ctx *c, QVar *v, int k, int64_t cells, int32_t smem_cells, double chunks)
+{
+    const Options &o = c->opt;
+    const double rows = (double)c->m;
+    const double flush = (double)cells * o.flush_cost;
+    const bool fits = cells <= smem_cells;
+    QVar ord[kMaxBitmapK];
+    const bool bm = bitmap_ok(c, v, k, ord);
+    const double nodes = bm ? dfs_nodes(ord, k) : 0.0;
+    const double hist = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) + flush;
+    double bitmap = bm ? chunks * ((double)o.bitmap_chunk_cost + nodes * o.bitmap_cost) + flush : 1e300;
+    if (bm && o.bitmap_small && small_ok(ord, k))
+        bitmap = chunks * ((double)o.bitmap_chunk_cost + small_units(ord, k) * o.small_cost) + flush;
+    const double gatomic = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) * 2.0 + (double)cells * 4.0;
+    int32_t s = o.strategy;
+    if (k == 0) s = fits ? FC_STRAT_HIST : FC_STRAT_GATOMIC;
+    if (k == 1 && fits && (s == FC_STRAT_AUTO || s == FC_STRAT_HIST)) return QPlan{FC_STRAT_MARGINAL, flush};
+    if (s == FC_STRAT_BITMAP && !bm) s = FC_STRAT_AUTO;
+    if (s == FC_STRAT_HIST && !fits) s = FC_STRAT_AUTO;
+    if (s == FC_STRAT_AUTO) {
+        if (fits)
+            s = bitmap < hist ? FC_STRAT_BITMAP : FC_STRAT_HIST;
+        else
+            s = cells >= o.sort_min_cells ? FC_STRAT_SORT : FC_STRAT_GATOMIC;
+    }
+    double cost = s == FC_STRAT_BITMAP ? bitmap : s == FC_STRAT_HIST ? hist : gatomic;
+    if (s == FC_STRAT_BITMAP) std::copy(ord, ord + k, v);
+    return QPlan{s, cost};
+}
+
+// Positions 0..n-1 ordered by decreasing key(i) (a positive cost), ties in
+// increasing position: a counting sort on the cost's exponent and top three
+// mantissa bits (1/8-octave classes), which is as much order as the
+// longest-processing-time-first assignment needs and avoids a comparison
+// sort's mispredicted branches on thousands of queries.
+template <class Key>
+void order_by_cost_desc(size_t n, Key key, std::vector<int32_t> &out)
+{
+    constexpr int kBits = 14;  // 11 exponent + 3 mantissa bits of a positive double
+    std::vector<uint32_t> cls(n);
+    std::vector<int32_t> start((1 << kBits) + 1, 0);
+    for (size_t i = 0; i < n; ++i) {
+        double v = key(i);
+        if (!(v > 0.0)) v = 0.0;
+        uint64_t b;
+        std::memcpy(&b, &v, sizeof b);
+        cls[i] = ((1u << kBits) - 1u) - (uint32_t)(b >> (52 - 3));  // descending
+        ++start[cls[i] + 1];
+    }
+    for (int c = 0; c < (1 << kBits); ++c) start[c + 1] += start[c];
+    out.resize(n);
+    for (size_t i = 0; i < n; ++i) out[start[cls[i]]++] = (int32_t)i;
+}
+
+// Builds a count or score plan.  vars lists are read through `get`.
+template <class GetVars>
+int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off, int score_kind,
+                     double ess, fc_plan **out)
+{
+    if (c->transactions) return fail(FC_ERR_STATE, "context holds transaction bitmaps; use the support calls");
+    if (nq < 0) return fail(FC_ERR_ARG, "nq < 0");
+    fc_plan *p = new (std::nothrow) fc_plan();
+    if (!p) return fail(FC_ERR_OOM, "host allocation failed");
+    p->ctx = c;
+    p->generation = c->generation;
+    c->live_plans.push_back(p);
+    p->kind = score_kind == kNoScore ? kPlanCount : kPlanScore;
+    p->nq = nq;
+    p->score_kind = score_kind;
+    p->ess = ess;
+    const Options &o = c->opt;
+    p->threads = std::max(32, std::min(1024, o.threads / 32 * 32));
+    const int max_cells = std::max(1, std::min<int>(o.smem_cells, (c->max_smem_optin - 4096) / 4));
+    p->smem_cells = max_cells;
+
+    const double chunks_d = (double)((c->m + kChunkRows - 1) / kChunkRows);
+    std::vector<QHead> qh(nq);
+    std::vector<QVar> qv;
+    std::vector<double> cost(nq);
+    p->strategy.resize(nq);
+    p->table_off.assign(nq + 1, 0);
+
+    // Per query: validation, QVars and strategy.  Large batches split into
+    // contiguous query ranges on host threads (each query's work only reads
+    // the context); the ranges' QVars are concatenated in query order.
+    struct Range {
+        std::vector<QVar> qv;
+        int32_t err_q = -1;
+        int err_code = 0;
+        std::string err_msg;
+    };
+    int nthreads = 1;
+    if (nq >= 4096) nthreads = (int)std::max<int64_t>(1, std::min<int64_t>(fc::host_threads(c), nq / 1024));
+    std::vector<Range> ranges(nthreads);
+    auto work = [&](int t) {
+        Range &R = ranges[t];
+        const int32_t q0 = (int32_t)((int64_t)nq * t / nthreads), q1 = (int32_t)((int64_t)nq * (t + 1) / nthreads);
+        R.qv.reserve((size_t)(q1 - q0) * 4);
+        std::vector<int32_t> buf;
+        for (int32_t q = q0; q < q1; ++q) {
+            const int32_t *vars;
+            int32_t k;
+            int32_t child;
+            if (!get(q, vars, k, child, buf)) {
+                R.err_q = q;
+                R.err_code = FC_ERR_ARG;
+                R.err_msg = g_err;
+                return;
+            }
+            const size_t first = R.qv.size();
+            int32_t k_eff = 0;
+            const int64_t cells = describe(c, vars, k, R.qv, k_eff);
+            if (cells < 0) {
+                R.err_q = q;
+                R.err_code = (int)cells;
+                R.err_msg = g_err;
+                return;
+            }
+            const QPlan ch = choose(c, R.qv.data() + first, k_eff, cells, max_cells, chunks_d);
+            QHead &h = qh[q];
+            h.cells = (int32_t)cells;
+            h.var_off = (int32_t)first;  // within the range for now
+            h.k = (int16_t)k_eff;
+            h.strategy = (int16_t)ch.strategy;
+            h.nparts = 1;
+            h.score_kind = (int16_t)score_kind;
+            h.r_child = score_kind == kNoScore ? 1 : c->arity[child];
+            h.child_soff = score_kind == kNoScore ? 0 : c->soff[child];
+            h.score_slot = q;
+            p->strategy[q] = ch.strategy;
+            cost[q] = ch.cost;
+        }
+    };
+    fc::run_host_threads(c, nthreads, work);
+    for (const Range &R : ranges)
+        if (R.err_q >= 0) {  // the first failing range holds the lowest failing query
+            fc_plan_free(p);
+            return fail(R.err_code, "%s", R.err_msg.c_str());
+        }
+    {
+        size_t total = 0;
+        for (const Range &R : ranges) total += R.qv.size();
+        qv.reserve(total);
+        for (int t = 0; t < nthreads; ++t) {
+            const int32_t base = (int32_t)qv.size();
+            const int32_t q0 = (int32_t)((int64_t)nq * t / nthreads), q1 = (int32_t)((int64_t)nq * (t + 1) / nthreads);
+            for (int32_t q = q0; q < q1; ++q) qh[q].var_off += base;
+            qv.insert(qv.end(), ranges[t].qv.begin(), ranges[t].qv.end());
+        }
+    }
+
+    int64_t scratch = 0;
+    for (int32_t q = 0; q < nq; ++q) {
+        QHead &h = qh[q];
+        const int64_t cells = h.cells;
+        if (score_kind == kNoScore) {
+            if (user_off) {
+                if (user_off[q + 1] - user_off[q] < cells || user_off[q] < 0) {
+                    fc_plan_free(p);
+                    return fail(FC_ERR_ARG, "table_off of query %d leaves %lld cells, it needs %lld", q,
+                                (long long)(user_off[q + 1] - user_off[q]), (long long)cells);
+                }
+                p->table_off[q] = user_off[q];
+            } else {
+                p->table_off[q] = scratch;
+                scratch += cells;
+            }
+            h.table_off = p->table_off[q];
+        }
+        if (user_off) p->table_off[nq] = user_off[nq];
+        else p->table_off[nq] = scratch;
+    }
+    if (score_kind == kNoScore) p->out_cells = p->table_off[nq];
+
+    // work items: split rows when the batch alone cannot fill the GPU
+    const size_t smem_bytes = (size_t)max_cells * 4;
+    int per_sm = std::max(1, o.ctas_per_sm);
+    p->grid = c->num_sms * per_sm;
+    p->smem = smem_bytes;
+    const int64_t nchunks = (c->m + kChunkRows - 1) / kChunkRows;
+    const int64_t max_parts_rows = std::max<int64_t>(1, c->m / std::max<int64_t>(o.min_part_rows, kChunkRows));
+    int32_t persistent = 0;
+    for (int32_t q = 0; q < nq; ++q)
+        if (qh[q].strategy == kHist || qh[q].strategy == kGAtomic) ++persistent;
+    // (marginal items hold no rows, so they never split)
+    const int64_t target = (int64_t)p->grid * 4;
+    int64_t parts = 1;
+    if (persistent > 0 && persistent < target)
+        parts = std::min<int64_t>({nchunks, max_parts_rows, (target + persistent - 1) / persistent, 32767});
+    parts = std::max<int64_t>(1, parts);
+    std::vector<Item> items;
+    std::vector<int32_t> hq;  // queries that become work items of count_kernel
+    std::vector<int32_t> qlist;
+    std::vector<std::pair<double, int32_t>> bmo;
+    hq.reserve(nq);
+    size_t n_items = 0;
+    for (int32_t q = 0; q < nq; ++q) {
+        QHead &h = qh[q];
+        if (h.strategy == kSort) {
+            p->sort_jobs.push_back(SortJob{q, h.k, 0, h.cells, 0, nullptr});
+            continue;
+        }
+        if (h.strategy == kBitmap) {
+            bmo.push_back({cost[q], q});
+            continue;
+        }
+        const int64_t qparts = h.strategy == kMarginal ? 1 : parts;
+        h.nparts = (int16_t)qparts;
+        hq.push_back(q);
+        n_items += (size_t)qparts;
+    }
+    // heaviest first by cost per part; a query's parts are consecutive, and
+    // within a cost class queries keep their order
+    std::vector<int32_t> perm;
+    order_by_cost_desc(hq.size(), [&](size_t i) { return cost[hq[i]] / qh[hq[i]].nparts; }, perm);
+    items.reserve(n_items);
+    for (int32_t i : perm) {
+        const int32_t q = hq[i];
+        for (int32_t part = 0; part < qh[q].nparts; ++part) items.push_back(Item{q, part});
+    }
+    p->n_items = (int32_t)items.size();
+    // bitmap queries: warp tasks of consecutive 4096-row chunks, heaviest
+    // queries first.  A query gets tasks in proportion to its estimated cost
+    // (about four tasks' worth of work per warp of the launch), each of at
+    // least kMinTaskChunks chunks, so that light queries are not cut into
+    // tasks whose fixed costs (dispatch, one reduction and atomic per cell)
+    // outweigh their work.
+    {
+        order_by_cost_desc(bmo.size(), [&](size_t i) { return bmo[i].first; }, perm);
+        std::vector<std::pair<double, int32_t>> sorted;
+        sorted.reserve(bmo.size());
+        for (int32_t i : perm) sorted.push_back(bmo[i]);
+        bmo.swap(sorted);
+    }
+    std::vector<BTask> btasks;
+    btasks.reserve(bmo.size() * 4);
+    p->bm_threads = std::max(32, std::min(1024, o.bitmap_threads / 32 * 32));
+    p->stage_slots = o.stage_slots;
+    p->small_paths = o.bitmap_small;
+    if (!bmo.empty()) {
+        constexpr int64_t kMinTaskChunks = 4;
+        p->bm_grid = c->num_sms * bitmap_ctas_per_sm(p->bm_threads, p->stage_slots);
+        const int64_t warps = (int64_t)p->bm_grid * (p->bm_threads / 32);
+        double total = 0.0;
+        for (auto &x : bmo) total += x.first;
+        const double unit = std::max(total / (4.0 * (double)warps), 1e-30);
+        const int64_t max_tasks = std::max<int64_t>(1, std::min<int64_t>(nchunks / kMinTaskChunks, 32767));
+        for (auto &x : bmo) {
+            const int32_t q = x.second;
+            // a 3-variable register-blocked query splits by the first
+            // variable's state as well (one pass over the chunks per state)
+            const QVar *ov = qv.data() + qh[q].var_off;
+            const int32_t passes = (p->small_paths && qh[q].k == 3 && small_ok(ov, 3)) ? ov[0].arity : 0;
+            const double per = x.first / std::max(1, passes);
+            const int64_t t = std::max<int64_t>(1, std::min<int64_t>(max_tasks, (int64_t)std::ceil(per / unit)));
+            qh[q].nparts = (int16_t)std::min<int64_t>(t * std::max(1, passes), 32767);
+            // t balanced chunk ranges: the first nchunks % t get one extra chunk
+            const int64_t base = nchunks / t, rem = nchunks % t;
+            for (int32_t s0 = passes > 0 ? 0 : -1; s0 < std::max(passes, 0); ++s0) {
+                int64_t c0 = 0;
+                for (int64_t part = 0; part < t; ++part) {
+                    const int64_t c1 = c0 + base + (part < rem ? 1 : 0);
+                    btasks.push_back(BTask{q, (int32_t)c0, (int32_t)c1, s0});
+                    c0 = c1;
+                }
+            }
+        }
+    }
+    p->n_btasks = (int32_t)btasks.size();
+
+    // tables that must exist in global memory for score plans
+    if (score_kind != kNoScore) {
+        for (int32_t q = 0; q < nq; ++q) {
+            QHead &h = qh[q];
+            const bool global = (h.strategy != kHist && h.strategy != kMarginal) || h.nparts > 1;
+            if (global) {
+                h.table_off = scratch;
+                scratch += h.cells;
+            } else {
+                h.table_off = 0;
+            }
+        }
+        p->table_buf_cells = scratch;
+    } else {
+        p->table_buf_cells = p->out_cells;
+    }
+    for (int32_t q = 0; q < nq; ++q) {
+        const QHead &h = qh[q];
+        if ((h.strategy != kHist && h.strategy != kMarginal) || h.nparts > 1) p->zero_tables = true;
+    }
+    for (auto &j : p->sort_jobs) {
+        j.table_off = qh[j.q].table_off;
+        j.key_bits = j.cells > 1 ? 32 - __builtin_clz((uint32_t)(j.cells - 1)) : 0;
+        if (score_kind != kNoScore) qlist.push_back(j.q);
+    }
+    p->n_qlist = (int32_t)qlist.size();
+
+    // one device allocation for all descriptors
+    const size_t b_qh = sizeof(QHead) * std::max(nq, 1);
+    const size_t b_qv = sizeof(QVar) * std::max<size_t>(qv.size(), 1);
+    const size_t b_it = sizeof(Item) * std::max<size_t>(items.size(), 1);
+    const size_t b_ql = sizeof(int32_t) * std::max<size_t>(qlist.size(), 1);
+    const size_t b_bq = sizeof(BTask) * std::max<size_t>(btasks.size(), 1);
+    const size_t o_qv = round_up(b_qh, 256), o_it = o_qv + round_up(b_qv, 256), o_ql = o_it + round_up(b_it, 256);
+    const size_t o_bq = o_ql + round_up(b_ql, 256);
+    const size_t total = o_bq + round_up(b_bq, 256);
+    uint8_t *host = stage_host(c, total);
+    if (!host) {
+        fc_plan_free(p);
+        return fail(FC_ERR_OOM, "pinned staging of %zu bytes", total);
+    }
+    std::memcpy(host, qh.data(), sizeof(QHead) * nq);
+    std::memcpy(host + o_qv, qv.data(), sizeof(QVar) * qv.size());
+    std::memcpy(host + o_it, items.data(), sizeof(Item) * items.size());
+    std::memcpy(host + o_ql, qlist.data(), sizeof(int32_t) * qlist.size());
+    std::memcpy(host + o_bq, btasks.data(), sizeof(BTask) * btasks.size());
+    cudaError_t e = plan_buf(c, p->desc, 0, total);
+    if (e == cudaSuccess) e = upload_stage(c, p->desc.p, total);
+    p->upload_bytes = total;
+    p->n_counters = 2 + nq;
+    if (e == cudaSuccess) e = plan_buf(c, p->counters, 1, sizeof(int32_t) * p->n_counters);
+    if (e == cudaSuccess && score_kind != kNoScore)
+        e = plan_buf(c, p->scratch_tables, 2, sizeof(int32_t) * std::max<int64_t>(p->table_buf_cells, 1));
+    if (e == cudaSuccess && !p->sort_jobs.empty()) {
+        const int tile = sort_tile_rows();
+        const int64_t nb = (c->m + tile - 1) / tile;
+        const size_t kb = round_up(sizeof(uint32_t) * c->m, 256);
+        e = plan_buf(c, p->sort_mem, 3, 2 * kb + sizeof(uint32_t) * 256 * nb);
+        if (e == cudaSuccess) {
+            uint8_t *base = (uint8_t *)p->sort_mem.p;
+            p->sort_sc.keys_a = (uint32_t *)base;
+            p->sort_sc.keys_b = (uint32_t *)(base + kb);
+            p->sort_sc.block_hist = (uint32_t *)(base + 2 * kb);
+            p->sort_sc.cap_rows = c->m;
+            p->sort_sc.cap_blocks = (int32_t)nb;
+        }
+    }
+    // a plan lent to a synchronous call runs on the context stream, after
+    // its upload; a plan the caller keeps may run on any stream, so its
+    // upload must be complete on return
+    if (e == cudaSuccess && !c->borrow) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        fc_plan_free(p);
+        return cuda_fail(e, "plan upload");
+    }
+    uint8_t *d = (uint8_t *)p->desc.p;
+    p->d_qh = (QHead *)d;
+    p->d_qv = (QVar *)(d + o_qv);
+    p->d_items = (Item *)(d + o_it);
+    p->d_qlist = (int32_t *)(d + o_ql);
+    p->d_btasks = (BTask *)(d + o_bq);
+    for (auto &j : p->sort_jobs) j.d_vars = p->d_qv + qh[j.q].var_off;
+    *out = p;
+    return FC_OK;
+}
+
+// Enqueues the work of a count/score plan on stream s.
+cudaError_t enqueue_count(fc_plan *p, int32_t *tables, float *scores, cudaStream_t s)
+{
+    fc_ctx *c = p->ctx;
+    cudaError_t e = cudaMemsetAsync(p->counters.p, 0, sizeof(int32_t) * p->n_counters, s);
+    if (e != cudaSuccess) return e;
+    int32_t *tab = p->kind == kPlanScore ? (int32_t *)p->scratch_tables.p : tables;
+    if (p->zero_tables && p->table_buf_cells > 0) {
+        e = cudaMemsetAsync(tab, 0, sizeof(int32_t) * p->table_buf_cells, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (p->n_items > 0 || p->n_btasks > 0) {
+        CountParams P{};
+        P.D = c->d_D;
+        P.m_pad = c->m_pad;
+        P.m = c->m;
+        P.bits = c->d_bits;
+        P.wstride = c->wstride;
+        P.qh = p->d_qh;
+        P.qv = p->d_qv;
+        P.items = p->d_items;
+        P.n_items = p->n_items;
+        P.next_item = (int32_t *)p->counters.p;
+        P.next_task = (int32_t *)p->counters.p + 1;
+        P.tickets = (int32_t *)p->counters.p + 2;
+        P.btasks = p->d_btasks;
+        P.n_btasks = p->n_btasks;
+        P.stage_slots = p->stage_slots;
+        P.tables = tab;
+        P.scores = scores;
+        P.marg = c->d_marg;
+        P.ess = p->ess;
+        P.write_tables = p->kind == kPlanCount ? 1 : 0;
+        P.smem_cells = p->smem_cells;
+        P.hist_copies = c->opt.hist_copies;
+        P.small_paths = p->small_paths;
+        if (p->n_btasks > 0) {
+            e = launch_bitmap(P, p->bm_grid, p->bm_threads, s);
+            if (e != cudaSuccess) return e;
+        }
+        if (p->n_items > 0) {
+            const int grid = std::min<int64_t>(p->grid, std::max(p->n_items, 1));
+            e = launch_count(P, grid, p->threads, p->smem, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    for (const SortJob &j : p->sort_jobs) {
+        e = launch_sort_count(c->d_D, c->m_pad, c->m, j.d_vars, j.k, j.key_bits, tab + j.table_off,
+                              j.cells, 0, p->sort_sc, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (p->kind == kPlanScore && p->n_qlist > 0)
+        e = launch_score_global(p->d_qh, p->d_qlist, p->n_qlist, tab, scores, c->d_marg, c->m, p->ess, s);
+    return e;
+}
+
+cudaError_t enqueue(fc_plan *p, void *o0, void *o1, void *o2, cudaStream_t s)
+{
+    switch (p->kind) {
+    case kPlanCount: return enqueue_count(p, (int32_t *)o0, nullptr, s);
+    case kPlanScore: return enqueue_count(p, nullptr, (float *)o0, s);
+    case kPlanSupport: return enqueue_support(p, (int32_t *)o0, (int32_t *)o1, (float *)o2, s);
+    case kPlanPairs: return enqueue_pairs(p, (int32_t *)o0, (float *)o1, s);
+    case kPlanFamilies: return enqueue_families(p, (float *)o0, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int run_plan(fc_plan *p, void *o0, void *o1, void *o2, cudaStream_t s, bool allow_graph)
+{
+    fc_ctx *c = p->ctx;
+    if (!s) s = c->stream;
+    if (!(allow_graph && c->opt.use_graph)) {
+        cudaError_t e = enqueue(p, o0, o1, o2, s);
+        if (e != cudaSuccess) return cuda_fail(e, "plan run");
+        return FC_OK;
+    }
+    for (auto &g : p->graphs)
+        if (g.o0 == o0 && g.o1 == o1 && g.o2 == o2 && g.s == s) {
+            cudaError_t e = cudaGraphLaunch(g.exec, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+            return FC_OK;
+        }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    cudaError_t e2 = enqueue(p, o0, o1, o2, s);
+    e = cudaStreamEndCapture(s, &graph);
+    if (e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(e2, "plan capture");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    p->graphs.push_back(GraphEntry{o0, o1, o2, s, exec});
+    e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return FC_OK;
+}
+
+int read_status(fc_ctx *c, cudaStream_t s)
+{
+    int32_t st[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(st, c->d_status, sizeof st, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "status");
+    if (st[0] != kStatusOk) {
+        cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), s);
+        cudaStreamSynchronize(s);
+        return fail(FC_ERR_TIMEOUT, "a bounded device wait ran out (status %d)", st[0]);
+    }
+    return FC_OK;
+}
+
+// Runs a plan on the context stream with runtime-owned device outputs and
+// copies them to the caller's host buffers.
+int run_to_host(fc_plan *p, void *h0, size_t b0, void *h1, size_t b1, void *h2, size_t b2)
+{
+    fc_ctx *c = p->ctx;
+    void *hs[3] = {h0, h1, h2};
+    size_t bs[3] = {b0, b1, b2};
+    void *ds[3] = {nullptr, nullptr, nullptr};
+    for (int i = 0; i < 3; ++i) {
+        if (!hs[i] || bs[i] == 0) continue;
+        cudaError_t e = c->io[i].ensure(bs[i]);
+        if (e != cudaSuccess) return cuda_fail(e, "output buffer");
+        ds[i] = c->io[i].p;
+    }
+    int rc = run_plan(p, ds[0], ds[1], ds[2], c->stream, false);
+    if (rc != FC_OK) return rc;
+    for (int i = 0; i < 3; ++i)
+        if (ds[i]) {
+            cudaError_t e = cudaMemcpyAsync(hs[i], ds[i], bs[i], cudaMemcpyDeviceToHost, c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "copy outputs");
+        }
+    return read_status(c, c->stream);
+}
+
+}  // namespace fc
+
+// ------------------------------------------------------------- plan API
+
+extern "C" int fc_plan_count(fc_ctx *c, int32_t nq, const int32_t *var_off, const int32_t *vars,
+                             const int64_t *table_off, fc_plan **out)
+{
+    if (!c || !out || (nq > 0 && (!var_off || !vars))) return fail(FC_ERR_ARG, "fc_plan_count: null argument");
+    *out = nullptr;
+    DevGuard g(c->device);
+    if (table_off)
+        for (int32_t q = 0; q < nq; ++q)
+            if (table_off[q + 1] < table_off[q]) return fail(FC_ERR_ARG, "table_off must be non-decreasing");
+    auto get = [&](int32_t q, const int32_t *&v, int32_t &k, int32_t &child, std::vector<int32_t> &) {
+        const int32_t a = var_off[q], b = var_off[q + 1];
+        if (a < 0 || b < a) {
+            fail(FC_ERR_ARG, "var_off must be non-decreasing and non-negative");
+            return false;
+        }
+        v = vars + a;
+        k = b - a;
+        child = -1;
+        return true;
+    };
+    return build_count_plan(c, nq, get, table_off, kNoScore, 1.0, out);
+}
+
+extern "C" int fc_plan_score(fc_ctx *c, int32_t nq, const int32_t *child, const int32_t *par_off,
+                             const int32_t *parents, int32_t kind, double ess, fc_plan **out)
+{
+    if (!c || !out || (nq > 0 && (!child || !par_off))) return fail(FC_ERR_ARG, "fc_plan_score: null argument");
+    *out = nullptr;
+    if (kind < FC_LL || kind > FC_MI) return fail(FC_ERR_ARG, "unknown score kind %d", kind);
+    if (kind == FC_BDEU && !(ess > 0.0)) return fail(FC_ERR_ARG, "BDeu needs ess > 0");
+    DevGuard g(c->device);
+    auto get = [&](int32_t q, const int32_t *&v, int32_t &k, int32_t &ch, std::vector<int32_t> &buf) {
+        const int32_t a = par_off[q], b = par_off[q + 1];
+        if (a < 0 || b < a || (b > a && !parents)) {
+            fail(FC_ERR_ARG, "par_off must be non-decreasing and non-negative");
+            return false;
+        }
+        if (child[q] < 0 || child[q] >= c->n) {
+            fail(FC_ERR_ARG, "child %d out of range", child[q]);
+            return false;
+        }
+        buf.assign(parents + a, parents + b);
+        buf.push_back(child[q]);
+        v = buf.data();
+        k = (int32_t)buf.size();
+        ch = child[q];
+        return true;
+    };
+    return build_count_plan(c, nq, get, nullptr, kind, ess, out);
+}
+
+namespace {
+// Kernels one fc_plan_run launches when every output is given (memsets and
+// graph bookkeeping excluded).
+int64_t plan_launches(const fc_plan *p)
+{
+    switch (p->kind) {
+    case kPlanCount:
+    case kPlanScore:
+        return (p->n_btasks > 0) + (p->n_items > 0) + (int64_t)p->sort_jobs.size() +
+               (p->kind == kPlanScore && p->n_qlist > 0);
+    case kPlanSupport: return p->nq > 0 ? (p->sp.full_only ? 1 : 2) : 0;
+    case kPlanPairs: return 2;
+    case kPlanFamilies: return plan_launches(p->inner) + (p->n_jobs > 0);
+    }
+    return 0;
+}
+}  // namespace
+
+extern "C" int64_t fc_plan_size(const fc_plan *p, int32_t key)
+{
+    if (!p) return -1;
+    switch (key) {
+    case 0: return p->kind == kPlanPairs ? p->pair_cells : p->out_cells;
+    case 1: return p->kind == kPlanScore ? p->nq : p->kind == kPlanPairs ? p->n_pairs
+                 : p->kind == kPlanFamilies ? p->n_jobs : 0;
+    case 2: return p->kind == kPlanSupport ? p->nq : 0;
+    case 3: return p->kind == kPlanSupport ? p->n_sub : 0;
+    case 4: return p->nq;
+    case 5: return (int64_t)p->upload_bytes;
+    case 6: return plan_launches(p);
+    default: return -1;
+    }
+}
+
+extern "C" int fc_plan_table_offsets(const fc_plan *p, int64_t *off)
+{
+    if (!p || !off) return fail(FC_ERR_ARG, "fc_plan_table_offsets: null argument");
+    if (p->kind != kPlanCount) return fail(FC_ERR_STATE, "not a count plan");
+    std::memcpy(off, p->table_off.data(), sizeof(int64_t) * (p->nq + 1));
+    return FC_OK;
+}
+
+extern "C" int fc_plan_strategies(const fc_plan *p, int32_t *s)
+{
+    if (!p || !s) return fail(FC_ERR_ARG, "fc_plan_strategies: null argument");
+    if (p->kind != kPlanCount && p->kind != kPlanScore) return fail(FC_ERR_STATE, "not a count or score plan");
+    std::memcpy(s, p->strategy.data(), sizeof(int32_t) * p->nq);
+    return FC_OK;
+}
+
+extern "C" int fc_plan_run(fc_plan *p, void *o0, void *o1, void *o2, void *stream)
+{
+    if (!p) return fail(FC_ERR_ARG, "fc_plan_run: null plan");
+    if (!p->ctx) return fail(FC_ERR_STATE, "fc_plan_run: the plan's context was freed");
+    if (p->generation != p->ctx->generation)
+        return fail(FC_ERR_STATE, "fc_plan_run: instances were appended since the plan was built; build a new plan");
+    DevGuard g(p->ctx->device);
+    if ((p->kind == kPlanCount && p->out_cells > 0 && !o0) || (p->kind == kPlanScore && p->nq > 0 && !o0) ||
+        (p->kind == kPlanFamilies && p->n_jobs > 0 && !o0) ||
+        (p->kind == kPlanSupport && p->nq > 0 && !o0))
+        return fail(FC_ERR_ARG, "fc_plan_run: missing output buffer");
+    return run_plan(p, o0, o1, o2, (cudaStream_t)stream, true);
+}
+
+namespace fc {
+// Device resources of a plan (its graphs and buffers); the caller has made
+// the plan's device current.
+void release_plan(fc_plan *p)
+{
+    cudaStreamSynchronize(p->ctx->stream);
+    for (auto &gr : p->graphs) {
+        cudaStreamSynchronize(gr.s);
+        cudaGraphExecDestroy(gr.exec);
+    }
+    p->graphs.clear();
+    p->desc.release();
+    p->counters.release();
+    p->scratch_tables.release();
+    p->sort_mem.release();
+    p->pairs_C.release();
+    p->pairs_meta.release();
+    p->fam_tables.release();
+    p->fam_jobs.release();
+}
+}  // namespace fc
+
+extern "C" void fc_plan_free(fc_plan *p)
+{
+    if (!p) return;
+    if (p->ctx) {  // still attached: release here (an orphan was released by fc_free)
+        fc_ctx *c = p->ctx;
+        DevGuard g(c->device);
+        release_plan(p);
+        auto &lp = c->live_plans;
+        lp.erase(std::remove(lp.begin(), lp.end(), p), lp.end());
+    }
+    if (p->inner) fc_plan_free(p->inner);
+    delete p;
+}
+
+extern "C" int fc_sync(fc_ctx *c, void *stream)
+{
+    if (!c) return fail(FC_ERR_ARG, "fc_sync: null context");
+    DevGuard g(c->device);
+    if (stream) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    }
+    return read_status(c, c->stream);
+}
+
+// ------------------------------------------------------- host entry points
+
+extern "C" int fc_count(fc_ctx *c, const int32_t *vars, int32_t k, int32_t *table)
+{
+    if (!c || !table || (k > 0 && !vars)) return fail(FC_ERR_ARG, "fc_count: null argument");
+    int32_t off[2] = {0, k};
+    return fc_count_batch(c, 1, off, vars, nullptr, table);
+}
+
+extern "C" int fc_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int32_t *vars,
+                              const int64_t *table_off, int32_t *tables)
+{
+    if (!c || (nq > 0 && !tables)) return fail(FC_ERR_ARG, "fc_count_batch: null argument");
+    DevGuard g(c->device);
+    fc_plan *p = nullptr;
+    int rc;
+    {
+        BorrowScope b(c);
+        rc = fc_plan_count(c, nq, var_off, vars, table_off, &p);
+    }
+    if (rc != FC_OK) return rc;
+    rc = run_to_host(p, tables, sizeof(int32_t) * p->out_cells, nullptr, 0, nullptr, 0);
+    fc_plan_free(p);
+    return rc;
+}
+
+extern "C" int fc_score_batch(fc_ctx *c, int32_t nq, const int32_t *child, const int32_t *par_off,
+                              const int32_t *parents, int32_t kind, double ess, float *scores)
+{
+    if (!c || (nq > 0 && !scores)) return fail(FC_ERR_ARG, "fc_score_batch: null argument");
+    DevGuard g(c->device);
+    fc_plan *p = nullptr;
+    int rc;
+    {
+        BorrowScope b(c);
+        rc = fc_plan_score(c, nq, child, par_off, parents, kind, ess, &p);
+    }
+    if (rc != FC_OK) return rc;
+    rc = run_to_host(p, scores, sizeof(float) * nq, nullptr, 0, nullptr, 0);
+    fc_plan_free(p);
+    return rc;
+}
+
+extern "C" int fc_count_assignment(fc_ctx *c, const int32_t *vars, const int32_t *states, int32_t k,
+                                   int64_t *count)
+{
+    if (!c || !count || (k > 0 && (!vars || !states))) return fail(FC_ERR_ARG, "fc_count_assignment: null argument");
+    if (c->transactions) return fail(FC_ERR_STATE, "context holds transaction bitmaps");
+    if (k < 0 || k > c->n) return fail(FC_ERR_ARG, "bad k");
+    DevGuard g(c->device);
+    std::vector<int32_t> rows;
+    for (int t = 0; t < k; ++t) {
+        if (vars[t] < 0 || vars[t] >= c->n) return fail(FC_ERR_ARG, "variable %d out of range", vars[t]);
+        if (states[t] < 0 || states[t] >= c->arity[vars[t]]) {
+            *count = 0;
+            return FC_OK;
+        }
+        rows.push_back(c->soff[vars[t]] + states[t]);
+    }
+    if (k == 0) {
+        *count = c->m;
+        return FC_OK;
+    }
+    cudaError_t e = c->io[0].ensure(sizeof(unsigned long long) + sizeof(int32_t) * k + 64);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch");
+    unsigned long long *d_cnt = (unsigned long long *)c->io[0].p;
+    int32_t *d_rows = (int32_t *)((uint8_t *)c->io[0].p + 64);
+    cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), c->stream);
+    cudaMemcpyAsync(d_rows, rows.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, c->stream);
+    e = launch_assignment_count(c->d_bits, c->wstride, d_rows, k, c->words, d_cnt, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "assignment count");
+    unsigned long long h = 0;
+    e = cudaMemcpyAsync(&h, d_cnt, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "assignment count");
+    *count = (int64_t)h;
+    return FC_OK;
+}
+
