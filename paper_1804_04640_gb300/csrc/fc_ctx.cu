@@ -406,23 +406,32 @@ extern "C" int fc_append(fc_ctx *c, const uint8_t *D, int64_t m_new, int32_t lay
         if (e == cudaSuccess)
             e = launch_transpose_rows((const uint8_t *)c->io[2].p, m_new, c->n, c->d_D + m0, c->m_pad, c->stream);
     }
-    // states are checked before anything visible changes
+    // The repack of the bitmap words from m0 / 64 on also checks the states.
+    // A bad state appends nothing: the new rows of D are zeroed and the same
+    // words repacked over the old rows alone, before m or the marginals move.
     int32_t *bad = c->d_status + 1;
     int32_t bad_h = 0;
-    if (e == cudaSuccess) e = launch_check_states(c->d_D, c->m_pad, m0, m1, c->n, c->d_arity, bad, c->stream);
+    if (e == cudaSuccess)
+        e = launch_pack_bits(c->d_D, c->m_pad, m1, c->n, c->d_arity, c->d_soff, c->d_bits, c->wstride, 255, bad,
+                             c->stream, m0 / 64);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_h, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "fc_append");
     if (bad_h) {
-        cudaMemsetAsync(bad, 0, sizeof(int32_t), c->stream);
+        // D past m0 back to zero; the partial word at m0 / 64 repacked from
+        // the old rows alone; the words after it cleared in every bitmap row
+        const int64_t w_old = (m0 + 63) / 64, w_new = (m1 + 63) / 64;
         cudaMemset2DAsync(c->d_D + m0, c->m_pad, 0, m_new, c->n, c->stream);
+        if (m0 % 64) launch_pack_bits(c->d_D, c->m_pad, m0, c->n, c->d_arity, c->d_soff, c->d_bits, c->wstride,
+                                      255, bad, c->stream, m0 / 64);
+        if (w_new > w_old)
+            cudaMemset2DAsync(c->d_bits + w_old, sizeof(uint64_t) * c->wstride, 0, sizeof(uint64_t) * (w_new - w_old),
+                              c->R, c->stream);
+        cudaMemsetAsync(bad, 0, sizeof(int32_t), c->stream);
         cudaStreamSynchronize(c->stream);
         return fail(FC_ERR_RANGE, "fc_append: a state is >= its variable's arity; nothing was appended");
     }
-    e = launch_pack_bits(c->d_D, c->m_pad, m1, c->n, c->d_arity, c->d_soff, c->d_bits, c->wstride, 255, bad,
-                         c->stream, m0 / 64);
-    if (e == cudaSuccess)
-        e = launch_state_counts(c->d_D, c->m_pad, m0, m1, c->n, c->d_arity, c->d_soff, c->d_marg, c->stream);
+    e = launch_bit_popcounts_range(c->d_bits, c->R, c->wstride, m0, m1, c->d_marg, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "fc_append bitmaps");
     return finish_append(c, m1);
 }

@@ -9,30 +9,67 @@
 namespace fc {
 namespace {
 
-// One warp packs 64 consecutive instances of one variable: for every state s
-// the two ballots over (D_i[p] == s) are the low and high halves of word
-// p / 64 of bitmap (i, s).  A state >= r_i sets *bad_state.
-__global__ void pack_bits_kernel(const uint8_t *__restrict__ D, int64_t m_pad, int64_t m, int64_t w0,
-                                 const int32_t *__restrict__ arity,
-                                 const int32_t *__restrict__ soff, uint64_t *__restrict__ bits,
-                                 int64_t wstride, int32_t *bad_state)
+// One warp packs 32 consecutive words (2,048 instances) of one variable.  The
+// warp first copies those 2 KiB of the column to shared memory with 16-byte
+// loads.  In step j it reads instances 64 (w0 + j) + lane and + 32, and for
+// every state s the two ballots over (D_i[p] == s) form word w0 + j of bitmap
+// (i, s); lane j keeps that word, so after the 32 steps lane l holds word
+// w0 + l of every state and the stores are coalesced.  States are taken 16 at
+// a time (a register per state and lane).  A state >= r_i sets *bad_state;
+// such an instance sets no bit.  The copy starts 64-byte aligned (m_pad is a
+// multiple of 4096) and reads only vectors that start before m.
+constexpr int kPackWarps = 8;
+__global__ void __launch_bounds__(kPackWarps * 32) pack_bits_kernel(
+    const uint8_t *__restrict__ D, int64_t m_pad, int64_t m, int64_t w0, const int32_t *__restrict__ arity,
+    const int32_t *__restrict__ soff, uint64_t *__restrict__ bits, int64_t wstride, int32_t *bad_state)
 {
+    __shared__ __align__(16) uint8_t s_rows[kPackWarps][2048];
     const int i = blockIdx.y;
-    const int lane = threadIdx.x & 31;
-    const int64_t w = w0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w * 64 >= m) return;  // whole warp leaves together
-    const int64_t p0 = w * 64 + lane, p1 = p0 + 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t wb = w0 + ((int64_t)blockIdx.x * kPackWarps + warp) * 32;
+    const int64_t words = (m + 63) >> 6;
+    if (wb >= words) return;  // whole warp leaves together
     const uint8_t *col = D + (int64_t)i * m_pad;
     const int r = arity[i];
-    const int b0 = p0 < m ? (int)col[p0] : -1;
-    const int b1 = p1 < m ? (int)col[p1] : -1;
-    if (b0 >= r || b1 >= r) atomicOr(bad_state, 1);
-    uint64_t *row = bits + (int64_t)soff[i] * wstride + w;
-    for (int s = 0; s < r; ++s) {
-        const unsigned lo = __ballot_sync(0xffffffffu, b0 == s);
-        const unsigned hi = __ballot_sync(0xffffffffu, b1 == s);
-        if (lane == (s & 31)) row[(int64_t)s * wstride] = ((uint64_t)hi << 32) | lo;
+    uint8_t *buf = s_rows[warp];
+    {
+        // only vectors that start before m: such a vector ends by
+        // roundup(m, 16) <= m_pad, inside the column; instances past m are
+        // never read back from the buffer
+        const uint4 *src = reinterpret_cast<const uint4 *>(col + wb * 64);
+        uint4 *dst = reinterpret_cast<uint4 *>(buf);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (wb * 64 + 16 * (lane + 32 * k) < m) dst[lane + 32 * k] = __ldg(src + lane + 32 * k);
     }
+    __syncwarp();
+    uint64_t *row = bits + (int64_t)soff[i] * wstride + wb + lane;
+    const bool mine = wb + lane < words;
+    bool bad = false;
+    for (int s0 = 0; s0 < r; s0 += 16) {
+        uint64_t word[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) word[t] = 0ull;
+        for (int j = 0; j < 32 && wb + j < words; ++j) {
+            const int64_t p0 = (wb + j) * 64 + lane, p1 = p0 + 32;
+            const int b0 = p0 < m ? (int)buf[j * 64 + lane] : -1;
+            const int b1 = p1 < m ? (int)buf[j * 64 + 32 + lane] : -1;
+            if (s0 == 0) bad |= (b0 >= r) | (b1 >= r);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                if (s0 + t >= r) break;
+                const unsigned lo = __ballot_sync(0xffffffffu, b0 == s0 + t);
+                const unsigned hi = __ballot_sync(0xffffffffu, b1 == s0 + t);
+                if (lane == j) word[t] = ((uint64_t)hi << 32) | lo;
+            }
+        }
+        if (mine) {
+#pragma unroll
+            for (int t = 0; t < 16; ++t)
+                if (s0 + t < r) row[(int64_t)(s0 + t) * wstride] = word[t];
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(bad_state, 1);
 }
 
 __global__ void bit_popcount_kernel(const uint64_t *__restrict__ bits, int64_t wstride,
@@ -99,41 +136,25 @@ __global__ void assignment_count_kernel(const uint64_t *__restrict__ bits, int64
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
-// Appended instances [p0, p1) of every variable (blockIdx.y strides over the
-// n variables): any state >= its arity sets *bad_state.
-__global__ void check_states_kernel(const uint8_t *__restrict__ D, int64_t m_pad, int64_t p0, int64_t p1,
-                                    int32_t n, const int32_t *__restrict__ arity, int32_t *bad_state)
+// Marginal counts of appended instances from the repacked bitmaps: block r
+// adds to marg[r] the set bits of row r in words [w0, w1), ignoring the bits
+// below position `from` of word w0 (instances that were there before).
+__global__ void bit_popcount_range_kernel(const uint64_t *__restrict__ bits, int64_t wstride, int64_t w0,
+                                          int64_t w1, int from, unsigned long long *marg)
 {
-    bool bad = false;
-    for (int i = blockIdx.y; i < n; i += gridDim.y) {
-        const uint8_t *col = D + (int64_t)i * m_pad;
-        const int r = arity[i];
-        for (int64_t p = p0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < p1;
-             p += (int64_t)gridDim.x * blockDim.x)
-            bad |= col[p] >= r;
-    }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(bad_state, 1);
-}
-
-// Marginal counts of the appended instances [p0, p1) of every variable
-// (blockIdx.y strides over them), added to marg[soff + state] through a
-// shared-memory histogram per block.
-__global__ void state_counts_kernel(const uint8_t *__restrict__ D, int64_t m_pad, int64_t p0, int64_t p1,
-                                    int32_t n, const int32_t *__restrict__ arity, const int32_t *__restrict__ soff,
-                                    unsigned long long *marg)
-{
-    __shared__ unsigned int hist[256];
-    for (int i = blockIdx.y; i < n; i += gridDim.y) {
-        for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0u;
-        __syncthreads();
-        const uint8_t *col = D + (int64_t)i * m_pad;
-        for (int64_t p = p0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < p1;
-             p += (int64_t)gridDim.x * blockDim.x)
-            atomicAdd(&hist[col[p]], 1u);
-        __syncthreads();
-        for (int t = threadIdx.x; t < arity[i]; t += blockDim.x)
-            if (hist[t]) atomicAdd(marg + soff[i] + t, (unsigned long long)hist[t]);
-        __syncthreads();
+    const uint64_t *row = bits + (int64_t)blockIdx.x * wstride;
+    const uint64_t first_mask = (~0ull) << from;
+    unsigned long long c = 0;
+    for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x)
+        c += __popcll(w == w0 ? (row[w] & first_mask) : row[w]);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    __shared__ unsigned long long part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += part[j];
+        if (t) atomicAdd(marg + blockIdx.x, t);
     }
 }
 
@@ -186,11 +207,11 @@ cudaError_t launch_pack_bits(const uint8_t *D, int64_t m_pad, int64_t m, int32_t
                              int64_t wstride, int32_t /*max_arity*/, int32_t *bad_state,
                              cudaStream_t s, int64_t first_word)
 {
-    const int warps = 8;
     const int64_t words = (m + 63) / 64 - first_word;
     if (words <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((words + warps - 1) / warps), (unsigned)n);
-    pack_bits_kernel<<<grid, warps * 32, 0, s>>>(D, m_pad, m, first_word, d_arity, d_soff, bits, wstride,
+    const int64_t groups = (words + 31) / 32;  // 32 words per warp
+    dim3 grid((unsigned)((groups + kPackWarps - 1) / kPackWarps), (unsigned)n);
+    pack_bits_kernel<<<grid, kPackWarps * 32, 0, s>>>(D, m_pad, m, first_word, d_arity, d_soff, bits, wstride,
                                                  bad_state);
     return cudaGetLastError();
 }
@@ -204,21 +225,13 @@ unsigned append_grid(int64_t units, int threads)
 unsigned append_rows(int32_t n) { return (unsigned)std::max(1, std::min(n, 65535)); }
 }  // namespace
 
-cudaError_t launch_check_states(const uint8_t *D, int64_t m_pad, int64_t p0, int64_t p1, int32_t n,
-                                const int32_t *d_arity, int32_t *bad_state, cudaStream_t s)
+cudaError_t launch_bit_popcounts_range(const uint64_t *bits, int64_t rows, int64_t wstride, int64_t m_old,
+                                       int64_t m_new_total, int64_t *marg, cudaStream_t s)
 {
-    if (p1 <= p0) return cudaSuccess;
-    check_states_kernel<<<dim3(append_grid(p1 - p0, 256), append_rows(n)), 256, 0, s>>>(D, m_pad, p0, p1, n,
-                                                                                         d_arity, bad_state);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_state_counts(const uint8_t *D, int64_t m_pad, int64_t p0, int64_t p1, int32_t n,
-                                const int32_t *d_arity, const int32_t *d_soff, int64_t *marg, cudaStream_t s)
-{
-    if (p1 <= p0) return cudaSuccess;
-    state_counts_kernel<<<dim3(append_grid(p1 - p0, 256), append_rows(n)), 256, 0, s>>>(
-        D, m_pad, p0, p1, n, d_arity, d_soff, reinterpret_cast<unsigned long long *>(marg));
+    const int64_t w0 = m_old >> 6, w1 = (m_new_total + 63) >> 6;
+    if (rows <= 0 || w1 <= w0) return cudaSuccess;
+    bit_popcount_range_kernel<<<(unsigned)rows, 256, 0, s>>>(bits, wstride, w0, w1, (int)(m_old & 63),
+                                                            reinterpret_cast<unsigned long long *>(marg));
     return cudaGetLastError();
 }
 

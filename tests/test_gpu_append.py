@@ -151,6 +151,16 @@ def test_append_bad_state_changes_nothing():
         fc.fc_append(ctx, bad)
     assert e.value.code == fc.FC_ERR_RANGE
     assert fc.fc_info(ctx, 1) == 3000 and np.array_equal(fc.fc_marginals(ctx), marg0)
+    # the bitmaps hold the old rows only (the failed append was rolled back)
+    old = fc.fc_load(D[:, :3000], db.arities)
+    q_off, q_flat = fc.pack_lists([[4, 0], [1, 2, 3], [4]])
+    for c in (ctx, old):
+        fc.fc_set_option(c, "strategy", fc.FC_STRAT_BITMAP)
+    assert np.array_equal(fc.fc_count_batch(ctx, q_off, q_flat)[0], fc.fc_count_batch(old, q_off, q_flat)[0])
+    vo, vv = fc.pack_lists([[4, 0], [2]])
+    _, ss = fc.pack_lists([[1, 0], [2]])
+    assert np.array_equal(fc.fc_count_assignment_batch(ctx, vo, vv, ss), fc.fc_count_assignment_batch(old, vo, vv, ss))
+    fc.fc_set_option(ctx, "strategy", -1)
     fc.fc_append(ctx, D[:, 3000:])                       # the valid rows still go in cleanly
     full = fc.fc_load(D, db.arities)
     off, flat = fc.pack_lists([[4, 0], [4, 1, 2]])
