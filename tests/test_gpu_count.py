@@ -265,3 +265,36 @@ def test_assignment_batch(m):
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
         want = list(ex.map(lambda q: orc.count_assignment(*q), qs))
     assert got.tolist() == want
+
+
+def test_contexts_on_concurrent_host_threads():
+    """Two contexts driven from two host threads at once (ctypes drops the
+    GIL): the shared launch-attribute and occupancy caches are thread-safe and
+    every result matches a single-threaded run."""
+    import threading
+    dbs = [random_dag_database(14, 30_001 + 7 * t, 2, 5, 3, 1.0, seed=60 + t) for t in range(2)]
+    qs = [random_queries(14, 5000, 1, 5, seed=70 + t) for t in range(2)]
+    want = []
+    for db, q in zip(dbs, qs):
+        ctx = fc.fc_load(db.D, db.arities)
+        want.append(fc.fc_count_batch(ctx, *fc.pack_lists(q))[0])
+    got = [None, None]
+    errors = []
+
+    def run(t):
+        try:
+            ctx = fc.fc_load(dbs[t].D, dbs[t].arities)
+            off, flat = fc.pack_lists(qs[t])
+            for _ in range(3):
+                got[t] = fc.fc_count_batch(ctx, off, flat)[0]
+        except Exception as e:  # noqa: BLE001
+            errors.append(e)
+
+    th = [threading.Thread(target=run, args=(t,)) for t in range(2)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    assert not errors, errors
+    for t in range(2):
+        assert np.array_equal(got[t], want[t])
