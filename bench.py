@@ -416,7 +416,7 @@ def run_gpu(args, rank: int, world: int):
                 per_plans.append(p1)
                 pq_outs.append(torch.empty(max(fc.fc_plan_size(p1, 0), 1), dtype=torch.int32, device="cuda"))
             per_query = (per_plans, pq_outs)
-        strategies = np.bincount(fc.fc_plan_strategies(plan), minlength=5).tolist()
+        strategies = np.bincount(fc.fc_plan_strategies(plan), minlength=6).tolist()
     elif name == "scores":
         db = w["db"]
         ctx = fc.fc_load(db.D, db.arities)
@@ -435,7 +435,7 @@ def run_gpu(args, rank: int, world: int):
 
         def e2e_call():
             fc.fc_score_batch(ctx, w["child"], po, pa, "bdeu", 1.0, out=pinned)
-        strategies = np.bincount(fc.fc_plan_strategies(plan), minlength=5).tolist()
+        strategies = np.bincount(fc.fc_plan_strategies(plan), minlength=6).tolist()
     elif name == "families":
         db = w["db"]
         ctx = fc.fc_load(db.D, db.arities)
@@ -623,7 +623,7 @@ def run_gpu(args, rank: int, world: int):
         cfg = describe(name, w)
         cfg["l2"] = "flushed between timed steps (256 MiB write)"
         if strategies is not None:
-            cfg["strategies"] = dict(zip(["bitmap", "hist", "gatomic", "sort", "marginal"], strategies))
+            cfg["strategies"] = dict(zip(["bitmap", "hist", "gatomic", "sort", "marginal", "window"], strategies))
             cfg["cost_model_fs"] = {k: fc.fc_get_option(ctx, k) for k in
                                     ("bitmap_cost", "bitmap_chunk_cost", "small_cost", "hist_cost_row", "hist_cost_var")}
         cores = os.cpu_count() or 1

@@ -76,8 +76,11 @@ enum {
     FC_STRAT_HIST = 1,    /* mixed-radix key per instance into a shared-memory table (Sec. 3.3's partitions as keys) */
     FC_STRAT_GATOMIC = 2, /* mixed-radix key into the output table in global memory */
     FC_STRAT_SORT = 3,    /* mixed-radix key, device radix sort, run-length (Sec. 3.3: partitions are runs of equal keys) */
-    FC_STRAT_MARGINAL = 4 /* one variable: the per-state counts precomputed at load (Sec. 3.3, precomputed
-                             single-variable partitions); chosen automatically, never forced */
+    FC_STRAT_MARGINAL = 4, /* one variable: the per-state counts precomputed at load (Sec. 3.3, precomputed
+                              single-variable partitions); chosen automatically, never forced */
+    FC_STRAT_WINDOW = 5   /* tables beyond shared memory: the cell range cut into windows that fit, each
+                             counted in shared memory over all instances (Sec. 3.3's partitions grouped by
+                             their leading digits) */
 };
 
 typedef struct fc_ctx fc_ctx;
@@ -376,7 +379,7 @@ int fc_sync(fc_ctx *ctx, void *stream);
 /* Set a tuning option; returns FC_ERR_ARG for an unknown key or bad value.
  *   "strategy"          FC_STRAT_* forced for every query (default AUTO)
  *   "smem_cells"        int32 cells of the shared-memory table area per CTA
- *   "threads"           threads per CTA of the count kernel (multiple of 32)
+ *   "threads"           threads per CTA of the count kernel (multiple of 32, <= 512)
  *   "ctas_per_sm"       resident CTAs per SM the count kernel is sized for
  *   "hist_copies"       max copies of a shared-memory table (contention)
  *   "min_part_rows"     smallest row range one work item covers
@@ -384,6 +387,12 @@ int fc_sync(fc_ctx *ctx, void *stream);
  *                       all-pairs kernel moves the counts to int32
  *   "use_graph"         1 = capture plan runs in CUDA graphs (default), 0 = plain launches
  *   "wait_limit"        iteration limit of every device-side wait
+ *   "window_max"        most cell windows AUTO gives one query before it
+ *                       counts the table in global memory instead
+ *   "window_cells"      cap on the cells of one window (default: as many as
+ *                       the shared memory of an SM holds)
+ *   "window_wide"       1 = windows run in their own launch of one 1024-thread
+ *                       CTA per SM (default), 0 = inside the mixed launch
  *   "bitmap_cost", "hist_cost_row", "hist_cost_var", "flush_cost"
  *                       cost-model coefficients (x1000) used by AUTO. */
 int fc_set_option(fc_ctx *ctx, const char *key, int64_t value);

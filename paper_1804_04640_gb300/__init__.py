@@ -20,7 +20,8 @@ FC_OK, FC_ERR_ARG, FC_ERR_RANGE, FC_ERR_SIZE, FC_ERR_OOM, FC_ERR_CUDA, FC_ERR_TI
 FC_COL_MAJOR, FC_ROW_MAJOR = 0, 1
 FC_HOST, FC_DEVICE = 0, 1
 FC_LL, FC_MDL, FC_BDEU, FC_MI = 0, 1, 2, 3
-FC_STRAT_AUTO, FC_STRAT_BITMAP, FC_STRAT_HIST, FC_STRAT_GATOMIC, FC_STRAT_SORT, FC_STRAT_MARGINAL = -1, 0, 1, 2, 3, 4
+(FC_STRAT_AUTO, FC_STRAT_BITMAP, FC_STRAT_HIST, FC_STRAT_GATOMIC, FC_STRAT_SORT, FC_STRAT_MARGINAL,
+ FC_STRAT_WINDOW) = -1, 0, 1, 2, 3, 4, 5
 SCORE_KINDS = {"ll": FC_LL, "mdl": FC_MDL, "bdeu": FC_BDEU, "mi": FC_MI}
 
 # every entry point declared in include/fc.h

@@ -24,6 +24,13 @@
 //              lane never overflows and one multiply-add updates two keys.
 //     kGAtomic the same keys, counted straight into the table in global
 //              memory (tables too large for shared memory).
+//     kWindow  tables too large for shared memory cut into windows of
+//              consecutive cells (partitions that share their leading key
+//              digits); an item counts one window over its rows in shared
+//              memory, skipping keys outside it, and stores the window.  A
+//              table costs one pass over the rows per window but no global
+//              atomics, and windows run in a launch of one 1024-thread CTA
+//              per SM so that a window takes the SM's whole shared memory.
 //
 // When a query's counts feed a score, the reduction of Sec. 3.1 (Eq. 1,
 // Fig. 2) runs in the same launch: from shared memory when one item holds the
@@ -773,7 +780,78 @@ __device__ __forceinline__ void key_rows_global(const CountParams &P, const QVar
     }
 }
 
-__global__ void __launch_bounds__(512, 2) count_kernel(const CountParams P)
+// Scalar keys of which only those in the cell window [w0, w0 + wlen) are
+// counted, in shared memory.  K > 0 fixes the number of variables at compile
+// time (column pointers and strides in registers); K = 0 reads them per group.
+template <int K>
+__device__ __forceinline__ void key_rows_window(const CountParams &P, const QVar *vs, int kdyn, int64_t r0,
+                                                int64_t r1, uint32_t w0, uint32_t wlen, int32_t *win)
+{
+    constexpr int KR = K > 0 ? K : 1;
+    const uint4 *col[KR];
+    uint32_t st[KR];
+    if constexpr (K > 0) {
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            col[t] = reinterpret_cast<const uint4 *>(P.D + (int64_t)vs[t].var * P.m_pad + r0);
+            st[t] = (uint32_t)vs[t].stride;
+        }
+    }
+    const int64_t ngroups = (r1 - r0) >> 4;
+    for (int64_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
+        uint32_t key[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) key[j] = 0u - w0;
+        if constexpr (K > 0) {
+#pragma unroll
+            for (int t = 0; t < K; ++t) {
+                const uint4 x = __ldg(col[t] + g);
+                const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) key[4 * i + j] += ((w[i] >> (8 * j)) & 0xffu) * st[t];
+            }
+        } else {
+            for (int t = 0; t < kdyn; ++t) {
+                const QVar v = vs[t];
+                const uint4 x = __ldg(reinterpret_cast<const uint4 *>(P.D + (int64_t)v.var * P.m_pad + r0) + g);
+                const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) key[4 * i + j] += ((w[i] >> (8 * j)) & 0xffu) * (uint32_t)v.stride;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (key[j] < wlen) atomicAdd(&win[key[j]], 1);
+    }
+    for (int64_t p = r0 + (ngroups << 4) + threadIdx.x; p < r1; p += blockDim.x) {
+        uint32_t key = 0u - w0;
+        for (int t = 0; t < kdyn; ++t)
+            key += (uint32_t)P.D[(int64_t)vs[t].var * P.m_pad + p] * (uint32_t)vs[t].stride;
+        if (key < wlen) atomicAdd(&win[key], 1);
+    }
+}
+
+__device__ __forceinline__ void key_rows_window_dispatch(const CountParams &P, const QVar *vs, int k, int64_t r0,
+                                                         int64_t r1, uint32_t w0, uint32_t wlen, int32_t *win)
+{
+    switch (k) {
+    case 2: key_rows_window<2>(P, vs, k, r0, r1, w0, wlen, win); break;
+    case 3: key_rows_window<3>(P, vs, k, r0, r1, w0, wlen, win); break;
+    case 4: key_rows_window<4>(P, vs, k, r0, r1, w0, wlen, win); break;
+    case 5: key_rows_window<5>(P, vs, k, r0, r1, w0, wlen, win); break;
+    case 6: key_rows_window<6>(P, vs, k, r0, r1, w0, wlen, win); break;
+    default: key_rows_window<0>(P, vs, k, r0, r1, w0, wlen, win); break;
+    }
+}
+
+// kThreads x kBlocks: 512 x 2 for the mixed launch; 1024 x 1 for windowed
+// tables, whose window then takes the whole shared memory of an SM.
+template <int kThreads, int kBlocks>
+__global__ void __launch_bounds__(kThreads, kBlocks) count_kernel(const CountParams P)
 {
     extern __shared__ __align__(16) int32_t smem_tab[];
     __shared__ QVar s_vars[kMaxK];
@@ -792,11 +870,22 @@ __global__ void __launch_bounds__(512, 2) count_kernel(const CountParams P)
         const QHead h = P.qh[W.q];
         const int k = h.k;
         if (threadIdx.x < k) s_vars[threadIdx.x] = P.qv[h.var_off + threadIdx.x];
-        const int64_t c0 = nchunks * W.part / h.nparts;
-        const int64_t c1 = nchunks * (W.part + 1) / h.nparts;
+        // a windowed query's items are (row part, window) pairs, windows fastest
+        const bool windowed = h.strategy == kWindow;
+        const int nwin = windowed ? h.nwin : 1;
+        const int rpart = W.part / nwin, rparts = h.nparts / nwin;
+        const int64_t c0 = nchunks * rpart / rparts;
+        const int64_t c1 = nchunks * (rpart + 1) / rparts;
         const int64_t r0 = c0 * kChunkRows;
         const int64_t r1 = min(P.m, c1 * kChunkRows);
         const bool in_smem = h.strategy == kHist || h.strategy == kMarginal;
+        uint32_t w0 = 0, wlen = 0;  // the item's cell window
+        if (windowed) {
+            const uint32_t wsz = (uint32_t)((h.cells + nwin - 1) / nwin);
+            w0 = (uint32_t)(W.part % nwin) * wsz;
+            wlen = min(wsz, (uint32_t)h.cells - w0);
+            for (uint32_t c = threadIdx.x; c < wlen; c += blockDim.x) smem_tab[c] = 0;
+        }
         int copies = 1;   // per-warp copies (large tables, unscaled keys)
         int lshift = -1;  // log2 of the interleaved copies (tables of <= 16384 cells)
         if (h.strategy == kHist && h.cells <= 16384) {
@@ -826,6 +915,8 @@ __global__ void __launch_bounds__(512, 2) count_kernel(const CountParams P)
             const QVar v = s_vars[0];
             for (int s = threadIdx.x; s < v.arity; s += blockDim.x)
                 smem_tab[s * v.stride] = (int32_t)P.marg[v.soff + s];
+        } else if (windowed) {
+            key_rows_window_dispatch(P, s_vars, k, r0, r1, w0, wlen, smem_tab);
         } else if (lshift >= 0) {
             key_rows_swar_dispatch(P, s_vars, k, r0, r1, lshift, smem_tab);
         } else if (in_smem) {
@@ -860,6 +951,17 @@ __global__ void __launch_bounds__(512, 2) count_kernel(const CountParams P)
                 }
             }
             __syncthreads();
+        } else if (windowed) {
+            // a window over all rows stores its whole cell range (the table
+            // lives in global memory for scores too); split rows add
+            int32_t *dst = P.tables + h.table_off + w0;
+            for (uint32_t c = threadIdx.x; c < wlen; c += blockDim.x) {
+                const int32_t v = smem_tab[c];
+                if (rparts == 1)
+                    dst[c] = v;
+                else if (v)
+                    atomicAdd(dst + c, v);
+            }
         }
 
         if (h.score_kind != kNoScore) {
@@ -964,7 +1066,7 @@ __global__ void score_global_kernel(const QHead *__restrict__ qh, const int32_t 
 
 }  // namespace
 
-const void *count_kernel_ptr() { return (const void *)count_kernel; }
+const void *count_kernel_ptr() { return (const void *)count_kernel<512, 2>; }
 const void *bitmap_kernel_ptr() { return (const void *)bitmap_kernel; }
 
 size_t bitmap_smem_bytes(int threads, int stage_slots)
@@ -979,7 +1081,7 @@ size_t bitmap_smem_bytes(int threads, int stage_slots)
 namespace {
 std::mutex g_attr_mu;
 constexpr int kMaxDevices = 64;
-int g_count_smem[kMaxDevices], g_bitmap_smem[kMaxDevices];
+int g_count_smem[kMaxDevices], g_bitmap_smem[kMaxDevices], g_wide_smem[kMaxDevices];
 
 cudaError_t ensure_smem_attr(const void *fn, int *cache, size_t smem)
 {
@@ -1023,9 +1125,18 @@ int bitmap_ctas_per_sm(int threads, int stage_slots)
 
 cudaError_t launch_count(const CountParams &p, int grid, int threads, size_t smem, cudaStream_t s)
 {
-    cudaError_t e = ensure_smem_attr((const void *)count_kernel, g_count_smem, smem);
+    if (threads > 512) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_smem_attr((const void *)count_kernel<512, 2>, g_count_smem, smem);
     if (e != cudaSuccess) return e;
-    count_kernel<<<grid, threads, smem, s>>>(p);
+    count_kernel<512, 2><<<grid, threads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_wide(const CountParams &p, int grid, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = ensure_smem_attr((const void *)count_kernel<1024, 1>, g_wide_smem, smem);
+    if (e != cudaSuccess) return e;
+    count_kernel<1024, 1><<<grid, 1024, smem, s>>>(p);
     return cudaGetLastError();
 }
 

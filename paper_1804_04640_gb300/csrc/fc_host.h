@@ -89,6 +89,9 @@ struct Options {
     int32_t use_graph = 1;
     int64_t wait_limit = 1 << 22;
     int64_t sort_min_cells = 1 << 25;
+    int32_t window_max = 40;          // AUTO: most shared-memory windows per table
+    int32_t window_cells = 1 << 20;   // cap on the cells of one window
+    int32_t window_wide = 1;          // windows in a launch of one 1024-thread CTA per SM
     // cost model, femtoseconds: bitmap per DFS node per 4096-row chunk;
     // histogram per row and per row-variable; per table cell flushed
     int64_t bitmap_cost = 200000;
@@ -253,6 +256,10 @@ struct fc_plan {
     double ess = 1.0;
     int grid = 0, threads = 0, smem_cells = 0;
     size_t smem = 0;
+    // windowed tables in their own launch (1024 threads, one CTA per SM):
+    // items [n_items, n_items + n_witems) of d_items
+    int32_t n_witems = 0, wgrid = 0;
+    size_t wsmem = 0;
     // support
     fc::SupportParams sp{};
     int sup_grid = 0, sup_threads = 0;

@@ -15,7 +15,9 @@ constexpr int kMaxBitmapK = 8;     // deepest DFS the bitmap kernel is instantia
 constexpr int kChunkRows = 4096;   // row granule of work items (64 words of 64 bits)
 constexpr int kChunkWords = kChunkRows / 64;
 
-enum Strategy : int32_t { kBitmap = 0, kHist = 1, kGAtomic = 2, kSort = 3, kMarginal = 4 };
+enum Strategy : int32_t { kBitmap = 0, kHist = 1, kGAtomic = 2, kSort = 3, kMarginal = 4, kWindow = 5 };
+// most cell windows of one kWindow query (its work items stay below 2^15)
+constexpr int kMaxWindows = 4096;
 enum ScoreKind : int32_t { kNoScore = -1, kLL = 0, kMDL = 1, kBDeu = 2, kMI = 3 };
 
 // Status word values written by kernels (0 = fine).
@@ -33,7 +35,7 @@ struct QHead {
     int32_t r_child;     // arity of the child (score queries: child is the last, stride 1)
     int32_t child_soff;  // state offset of the child (marginals for MI)
     int32_t score_slot;  // index into the score output
-    int32_t pad;
+    int32_t nwin;        // kWindow: cell windows (items = nwin x row parts), else 1
 };
 
 // One variable of a query.  stride is the variable's weight in the cell index
@@ -110,6 +112,9 @@ cudaError_t launch_mask_tail_bits(uint64_t *bits, int64_t rows, int64_t wstride,
                                   cudaStream_t s);
 
 cudaError_t launch_count(const CountParams &p, int grid, int threads, size_t smem, cudaStream_t s);
+// count_kernel with 1024 threads and one CTA per SM (windowed tables); smem
+// is the window's bytes
+cudaError_t launch_count_wide(const CountParams &p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_bitmap(const CountParams &p, int grid, int threads, cudaStream_t s);
 size_t bitmap_smem_bytes(int threads, int stage_slots);
 int bitmap_ctas_per_sm(int threads, int stage_slots);

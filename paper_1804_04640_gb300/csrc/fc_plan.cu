@@ -117,7 +117,7 @@ bool bitmap_ok(const fc_ctx *c, const QVar *v, int k, QVar *o)
 
 // Strategy and cost of one query.  When the bitmap strategy is chosen, the
 // variables are left in v in entropy order (the order its kernel walks).
-QPlan choose(const fc_ctx *c, QVar *v, int k, int64_t cells, int32_t smem_cells, double chunks)
+QPlan choose(const fc_ctx *c, QVar *v, int k, int64_t cells, int32_t smem_cells, int32_t win_cells, double chunks)
 {
     const Options &o = c->opt;
     const double rows = (double)c->m;
@@ -131,18 +131,24 @@ QPlan choose(const fc_ctx *c, QVar *v, int k, int64_t cells, int32_t smem_cells,
     if (bm && o.bitmap_small && small_ok(ord, k))
         bitmap = chunks * ((double)o.bitmap_chunk_cost + small_units(ord, k) * o.small_cost) + flush;
     const double gatomic = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) * 2.0 + (double)cells * 4.0;
+    // one pass over the rows per window of the cell range, scalar keys
+    const double windows = (double)((cells + win_cells - 1) / win_cells);
+    const double window = windows * rows * (o.hist_cost_row + (double)k * o.hist_cost_var) * 2.0 + flush;
     int32_t s = o.strategy;
     if (k == 0) s = fits ? FC_STRAT_HIST : FC_STRAT_GATOMIC;
     if (k == 1 && fits && (s == FC_STRAT_AUTO || s == FC_STRAT_HIST)) return QPlan{FC_STRAT_MARGINAL, flush};
     if (s == FC_STRAT_BITMAP && !bm) s = FC_STRAT_AUTO;
     if (s == FC_STRAT_HIST && !fits) s = FC_STRAT_AUTO;
+    if (s == FC_STRAT_WINDOW && windows > kMaxWindows) s = FC_STRAT_AUTO;
     if (s == FC_STRAT_AUTO) {
         if (fits)
             s = bitmap < hist ? FC_STRAT_BITMAP : FC_STRAT_HIST;
+        else if (cells >= o.sort_min_cells)
+            s = FC_STRAT_SORT;
         else
-            s = cells >= o.sort_min_cells ? FC_STRAT_SORT : FC_STRAT_GATOMIC;
+            s = windows <= std::min<double>(o.window_max, kMaxWindows) ? FC_STRAT_WINDOW : FC_STRAT_GATOMIC;
     }
-    double cost = s == FC_STRAT_BITMAP ? bitmap : s == FC_STRAT_HIST ? hist : gatomic;
+    double cost = s == FC_STRAT_BITMAP ? bitmap : s == FC_STRAT_HIST ? hist : s == FC_STRAT_WINDOW ? window : gatomic;
     if (s == FC_STRAT_BITMAP) std::copy(ord, ord + k, v);
     return QPlan{s, cost};
 }
@@ -188,9 +194,13 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     p->score_kind = score_kind;
     p->ess = ess;
     const Options &o = c->opt;
-    p->threads = std::max(32, std::min(1024, o.threads / 32 * 32));
+    p->threads = std::max(32, std::min(512, o.threads / 32 * 32));
     const int max_cells = std::max(1, std::min<int>(o.smem_cells, (c->max_smem_optin - 4096) / 4));
     p->smem_cells = max_cells;
+    // cells of one window of a windowed table: the whole shared memory of an
+    // SM in the wide launch, else the mixed launch's table area
+    const bool wide = o.window_wide != 0;
+    const int win_cells = std::max(1, std::min<int>(o.window_cells, wide ? (c->max_smem_optin - 4096) / 4 : max_cells));
 
     const double chunks_d = (double)((c->m + kChunkRows - 1) / kChunkRows);
     std::vector<QHead> qh(nq);
@@ -235,7 +245,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
                 R.err_msg = g_err;
                 return;
             }
-            const QPlan ch = choose(c, R.qv.data() + first, k_eff, cells, max_cells, chunks_d);
+            const QPlan ch = choose(c, R.qv.data() + first, k_eff, cells, max_cells, win_cells, chunks_d);
             QHead &h = qh[q];
             h.cells = (int32_t)cells;
             h.var_off = (int32_t)first;  // within the range for now
@@ -299,14 +309,31 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     const int64_t nchunks = (c->m + kChunkRows - 1) / kChunkRows;
     const int64_t max_parts_rows = std::max<int64_t>(1, c->m / std::max<int64_t>(o.min_part_rows, kChunkRows));
     int32_t persistent = 0;
-    for (int32_t q = 0; q < nq; ++q)
-        if (qh[q].strategy == kHist || qh[q].strategy == kGAtomic) ++persistent;
+    int64_t window_items = 0;
+    for (int32_t q = 0; q < nq; ++q) {
+        QHead &h = qh[q];
+        h.nwin = 1;
+        if (h.strategy == kHist || h.strategy == kGAtomic) ++persistent;
+        if (h.strategy == kWindow) {
+            h.nwin = (int32_t)(((int64_t)h.cells + win_cells - 1) / win_cells);  // <= kMaxWindows
+            window_items += h.nwin;
+        }
+    }
     // (marginal items hold no rows, so they never split)
     const int64_t target = (int64_t)p->grid * 4;
     int64_t parts = 1;
     if (persistent > 0 && persistent < target)
         parts = std::min<int64_t>({nchunks, max_parts_rows, (target + persistent - 1) / persistent, 32767});
     parts = std::max<int64_t>(1, parts);
+    // windowed queries split their rows only when their windows alone would
+    // leave CTAs idle: a split window adds its nonzero cells to the table
+    // with atomics instead of storing every cell once
+    p->wgrid = wide ? c->num_sms : p->grid;
+    p->wsmem = (size_t)win_cells * 4;
+    int64_t wparts = 1;
+    if (window_items > 0 && window_items < p->wgrid)
+        wparts = std::min<int64_t>({nchunks, max_parts_rows, (2 * (int64_t)p->wgrid + window_items - 1) / window_items});
+    wparts = std::max<int64_t>(1, wparts);
     std::vector<Item> items;
     std::vector<int32_t> hq;  // queries that become work items of count_kernel
     std::vector<int32_t> qlist;
@@ -323,7 +350,9 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
             bmo.push_back({cost[q], q});
             continue;
         }
-        const int64_t qparts = h.strategy == kMarginal ? 1 : parts;
+        const int64_t qparts = h.strategy == kMarginal ? 1
+                               : h.strategy == kWindow ? std::max<int64_t>(1, std::min<int64_t>(wparts, 32767 / h.nwin)) * h.nwin
+                                                       : parts;
         h.nparts = (int16_t)qparts;
         hq.push_back(q);
         n_items += (size_t)qparts;
@@ -333,11 +362,15 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     std::vector<int32_t> perm;
     order_by_cost_desc(hq.size(), [&](size_t i) { return cost[hq[i]] / qh[hq[i]].nparts; }, perm);
     items.reserve(n_items);
+    std::vector<Item> witems;
     for (int32_t i : perm) {
         const int32_t q = hq[i];
-        for (int32_t part = 0; part < qh[q].nparts; ++part) items.push_back(Item{q, part});
+        std::vector<Item> &dst = wide && qh[q].strategy == kWindow ? witems : items;
+        for (int32_t part = 0; part < qh[q].nparts; ++part) dst.push_back(Item{q, part});
     }
     p->n_items = (int32_t)items.size();
+    p->n_witems = (int32_t)witems.size();
+    items.insert(items.end(), witems.begin(), witems.end());
     // bitmap queries: warp tasks of consecutive 4096-row chunks, heaviest
     // queries first.  A query gets tasks in proportion to its estimated cost
     // (about four tasks' worth of work per warp of the launch), each of at
@@ -405,7 +438,10 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     }
     for (int32_t q = 0; q < nq; ++q) {
         const QHead &h = qh[q];
-        if ((h.strategy != kHist && h.strategy != kMarginal) || h.nparts > 1) p->zero_tables = true;
+        // a window over all rows stores every cell of its range
+        const bool stores_all = h.strategy == kWindow ? h.nparts == h.nwin
+                                                      : (h.strategy == kHist || h.strategy == kMarginal) && h.nparts == 1;
+        if (!stores_all) p->zero_tables = true;
     }
     for (auto &j : p->sort_jobs) {
         j.table_off = qh[j.q].table_off;
@@ -436,7 +472,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     cudaError_t e = plan_buf(c, p->desc, 0, total);
     if (e == cudaSuccess) e = upload_stage(c, p->desc.p, total);
     p->upload_bytes = total;
-    p->n_counters = 2 + nq;
+    p->n_counters = 3 + nq;  // next item, next bitmap task, tickets, next wide item
     if (e == cudaSuccess) e = plan_buf(c, p->counters, 1, sizeof(int32_t) * p->n_counters);
     if (e == cudaSuccess && score_kind != kNoScore)
         e = plan_buf(c, p->scratch_tables, 2, sizeof(int32_t) * std::max<int64_t>(p->table_buf_cells, 1));
@@ -484,7 +520,7 @@ cudaError_t enqueue_count(fc_plan *p, int32_t *tables, float *scores, cudaStream
         e = cudaMemsetAsync(tab, 0, sizeof(int32_t) * p->table_buf_cells, s);
         if (e != cudaSuccess) return e;
     }
-    if (p->n_items > 0 || p->n_btasks > 0) {
+    if (p->n_items > 0 || p->n_witems > 0 || p->n_btasks > 0) {
         CountParams P{};
         P.D = c->d_D;
         P.m_pad = c->m_pad;
@@ -516,6 +552,15 @@ cudaError_t enqueue_count(fc_plan *p, int32_t *tables, float *scores, cudaStream
         if (p->n_items > 0) {
             const int grid = std::min<int64_t>(p->grid, std::max(p->n_items, 1));
             e = launch_count(P, grid, p->threads, p->smem, s);
+            if (e != cudaSuccess) return e;
+        }
+        if (p->n_witems > 0) {
+            CountParams W = P;
+            W.items = p->d_items + p->n_items;
+            W.n_items = p->n_witems;
+            W.next_item = (int32_t *)p->counters.p + 2 + p->nq;
+            W.smem_cells = (int32_t)(p->wsmem / 4);
+            e = launch_count_wide(W, std::min<int64_t>(p->wgrid, p->n_witems), p->wsmem, s);
             if (e != cudaSuccess) return e;
         }
     }
@@ -677,7 +722,7 @@ int64_t plan_launches(const fc_plan *p)
     switch (p->kind) {
     case kPlanCount:
     case kPlanScore:
-        return (p->n_btasks > 0) + (p->n_items > 0) + (int64_t)p->sort_jobs.size() +
+        return (p->n_btasks > 0) + (p->n_items > 0) + (p->n_witems > 0) + (int64_t)p->sort_jobs.size() +
                (p->kind == kPlanScore && p->n_qlist > 0);
     case kPlanSupport: return p->nq > 0 ? (p->sp.full_only ? 1 : 2) : 0;
     case kPlanPairs: return 2;

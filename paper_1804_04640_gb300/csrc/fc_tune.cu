@@ -20,9 +20,9 @@ struct OptDesc {
 };
 
 const OptDesc kOpts[] = {
-    {"strategy", nullptr, &Options::strategy, -1, 3},
+    {"strategy", nullptr, &Options::strategy, -1, 5},
     {"smem_cells", nullptr, &Options::smem_cells, 256, 1 << 20},
-    {"threads", nullptr, &Options::threads, 32, 1024},
+    {"threads", nullptr, &Options::threads, 32, 512},
     {"ctas_per_sm", nullptr, &Options::ctas_per_sm, 1, 32},
     {"hist_copies", nullptr, &Options::hist_copies, 1, 32},
     {"min_part_rows", &Options::min_part_rows, nullptr, kChunkRows, (int64_t)1 << 31},
@@ -30,6 +30,9 @@ const OptDesc kOpts[] = {
     {"use_graph", nullptr, &Options::use_graph, 0, 1},
     {"wait_limit", &Options::wait_limit, nullptr, 1, (int64_t)1 << 40},
     {"sort_min_cells", &Options::sort_min_cells, nullptr, 1, (int64_t)1 << 31},
+    {"window_max", nullptr, &Options::window_max, 0, kMaxWindows},
+    {"window_cells", nullptr, &Options::window_cells, 256, 1 << 20},
+    {"window_wide", nullptr, &Options::window_wide, 0, 1},
     {"bitmap_cost", &Options::bitmap_cost, nullptr, 0, (int64_t)1 << 40},
     {"bitmap_chunk_cost", &Options::bitmap_chunk_cost, nullptr, 0, (int64_t)1 << 40},
     {"hist_cost_row", &Options::hist_cost_row, nullptr, 0, (int64_t)1 << 40},
@@ -53,6 +56,8 @@ extern "C" int fc_set_option(fc_ctx *c, const char *key, int64_t value)
         if (std::strcmp(d.key, key) == 0) {
             if (value < d.lo || value > d.hi)
                 return fail(FC_ERR_ARG, "option %s must be in %lld..%lld", key, (long long)d.lo, (long long)d.hi);
+            if (d.p32 == &Options::strategy && value == FC_STRAT_MARGINAL)
+                return fail(FC_ERR_ARG, "the marginal strategy is chosen by the planner, never forced");
             if (d.p64) c->opt.*(d.p64) = value;
             else c->opt.*(d.p32) = (int32_t)value;
             return FC_OK;

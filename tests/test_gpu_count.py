@@ -16,7 +16,7 @@ from workloads import CONFIGS, config_database, random_dag_database, random_quer
 
 pytestmark = pytest.mark.gpu
 
-STRATS = [fc.FC_STRAT_BITMAP, fc.FC_STRAT_HIST, fc.FC_STRAT_GATOMIC, fc.FC_STRAT_SORT]
+STRATS = [fc.FC_STRAT_BITMAP, fc.FC_STRAT_HIST, fc.FC_STRAT_GATOMIC, fc.FC_STRAT_SORT, fc.FC_STRAT_WINDOW]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -106,7 +106,7 @@ def test_large_tables_sort_and_global_paths():
     queries = [[0, 1, 2, 3, 4], [5, 6, 7, 0], [1, 2, 3]]
     want = oracle_tables(orc, queries)
     check_batch(ctx, orc, queries, want)
-    for s in (fc.FC_STRAT_GATOMIC, fc.FC_STRAT_SORT):
+    for s in (fc.FC_STRAT_GATOMIC, fc.FC_STRAT_SORT, fc.FC_STRAT_WINDOW):
         fc.fc_set_option(ctx, "strategy", s)
         check_batch(ctx, orc, queries, want)
     fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_AUTO)
@@ -114,6 +114,48 @@ def test_large_tables_sort_and_global_paths():
     check_batch(ctx, orc, queries, want)
     fc.fc_set_option(ctx, "smem_cells", 256)           # everything leaves shared memory
     check_batch(ctx, orc, queries, want)
+
+
+def test_window_path_cuts_and_row_splits():
+    """Tables beyond shared memory counted window by window: the planner's
+    choice, uneven last windows, many windows per table, windows whose rows
+    are split over several CTAs (few queries), and scores over windowed
+    tables."""
+    db = random_dag_database(8, 250_003, 12, 16, 2, 0.3, seed=19)
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    queries = [[0, 1, 2, 3, 4], [5, 6, 7, 0], [1, 2, 3], [7, 6, 5, 4, 3]]
+    want = oracle_tables(orc, queries)
+    off, flat = fc.pack_lists(queries)
+    plan = fc.fc_plan_count(ctx, off, flat)
+    strat = fc.fc_plan_strategies(plan)
+    fc.fc_plan_free(plan)
+    cells = [int(np.prod([db.arities[v] for v in q])) for q in queries]
+    assert all(s == fc.FC_STRAT_WINDOW for s, n in zip(strat, cells) if 24576 < n <= 40 * 50_000)
+    check_batch(ctx, orc, queries, want)
+    fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_WINDOW)
+    for wide in (1, 0):                                # own launch / inside the mixed launch
+        fc.fc_set_option(ctx, "window_wide", wide)
+        for cells_per_window in (1 << 20, 7001, 1000):  # as many as fit .. ~1000 windows per table
+            fc.fc_set_option(ctx, "window_cells", cells_per_window)
+            check_batch(ctx, orc, queries, want)
+            check_batch(ctx, orc, queries[:1], want[:1])   # one query: rows split per window
+    # windowed and shared-memory queries in one plan (two launches)
+    fc.fc_set_option(ctx, "window_wide", 1)
+    fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_AUTO)
+    mixed = queries + [[0, 1], [2, 5, 6], [7]]
+    check_batch(ctx, orc, mixed, want + oracle_tables(orc, mixed[len(queries):]))
+    with pytest.raises(fc.FcError):
+        fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_MARGINAL)   # planner-only strategy
+    # a score over a windowed table (its table lives in global memory)
+    child, parents = 4, [0, 1, 2, 3]
+    fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_WINDOW)
+    fc.fc_set_option(ctx, "window_cells", 7001)
+    for kind in ("ll", "bdeu"):
+        po, pa = fc.pack_lists([parents])
+        got = fc.fc_score_batch(ctx, [child], po, pa, kind, ess=1.0)[0]
+        ref = orc.score(child, parents, kind, 1.0)
+        assert abs(got - ref) <= 1e-5 * max(1.0, abs(ref)), (kind, got, ref)
 
 
 def test_edge_cases():

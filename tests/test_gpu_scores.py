@@ -37,7 +37,7 @@ def assert_close(got, want, what):
 
 @pytest.mark.parametrize("kind", ["ll", "mdl", "bdeu", "mi"])
 @pytest.mark.parametrize("strategy", [fc.FC_STRAT_AUTO, fc.FC_STRAT_BITMAP, fc.FC_STRAT_HIST,
-                                      fc.FC_STRAT_GATOMIC, fc.FC_STRAT_SORT])
+                                      fc.FC_STRAT_GATOMIC, fc.FC_STRAT_SORT, fc.FC_STRAT_WINDOW])
 def test_scores_small_all_queries(kind, strategy):
     db = random_dag_database(16, 90_001, 2, 4, 4, 1.0, seed=31)
     ctx = fc.fc_load(db.D, db.arities)
