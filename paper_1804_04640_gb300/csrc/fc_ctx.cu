@@ -50,29 +50,43 @@ int cuda_fail(cudaError_t e, const char *what)
 // copy still reading it; nullptr on failure.
 uint8_t *stage_host(fc_ctx *c, size_t bytes)
 {
-    if (c->h_stage_ev && cudaEventSynchronize(c->h_stage_ev) != cudaSuccess) return nullptr;
-    if (bytes > c->h_stage_bytes) {
-        const size_t want = std::max(bytes, c->h_stage_bytes + c->h_stage_bytes / 2);
-        if (c->h_stage) cudaFreeHost(c->h_stage);
-        c->h_stage = nullptr;
-        c->h_stage_bytes = 0;
-        if (cudaHostAlloc((void **)&c->h_stage, want, cudaHostAllocDefault) != cudaSuccess) {
-            c->h_stage = nullptr;
+    fc_ctx::Stage &st = c->stage[c->bank];
+    if (st.ev && cudaEventSynchronize(st.ev) != cudaSuccess) return nullptr;
+    if (bytes > st.bytes) {
+        const size_t want = std::max(bytes, st.bytes + st.bytes / 2);
+        if (st.h) cudaFreeHost(st.h);
+        st.h = nullptr;
+        st.bytes = 0;
+        if (cudaHostAlloc((void **)&st.h, want, cudaHostAllocDefault) != cudaSuccess) {
+            st.h = nullptr;
             return nullptr;
         }
-        c->h_stage_bytes = want;
+        st.bytes = want;
     }
-    if (!c->h_stage_ev && cudaEventCreateWithFlags(&c->h_stage_ev, cudaEventDisableTiming) != cudaSuccess)
-        return nullptr;
-    return c->h_stage;
+    if (!st.ev && cudaEventCreateWithFlags(&st.ev, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    return st.h;
 }
-
-// Copies `bytes` of the staging buffer to dst on the context stream and
-// marks the staging buffer busy until the copy ends.
+uint8_t *stage_grow(fc_ctx *c, size_t bytes, size_t keep)
+{
+    fc_ctx::Stage &st = c->stage[c->bank];
+    if (bytes <= st.bytes) return st.h;
+    if (st.ev && cudaEventSynchronize(st.ev) != cudaSuccess) return nullptr;
+    const size_t want = std::max(bytes, st.bytes + st.bytes / 2);
+    uint8_t *h = nullptr;
+    if (cudaHostAlloc((void **)&h, want, cudaHostAllocDefault) != cudaSuccess) return nullptr;
+    if (st.h) {
+        std::memcpy(h, st.h, std::min(keep, st.bytes));
+        cudaFreeHost(st.h);
+    }
+    st.h = h;
+    st.bytes = want;
+    return h;
+}
 cudaError_t upload_stage(fc_ctx *c, void *dst, size_t bytes)
 {
-    cudaError_t e = cudaMemcpyAsync(dst, c->h_stage, bytes, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(c->h_stage_ev, c->stream);
+    fc_ctx::Stage &st = c->stage[c->bank];
+    cudaError_t e = cudaMemcpyAsync(dst, st.h, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(st.ev, c->stream);
     return e;
 }
 
@@ -268,6 +282,7 @@ extern "C" void fc_free(fc_ctx *c)
     if (!c) return;
     DevGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->out_stream) cudaStreamSynchronize(c->out_stream);
     // plans still alive keep their host struct for fc_plan_free but lose
     // their device memory and their context
     for (fc_plan *p : c->live_plans) {
@@ -275,10 +290,17 @@ extern "C" void fc_free(fc_ctx *c)
         p->ctx = nullptr;
     }
     c->live_plans.clear();
-    if (c->h_stage) cudaFreeHost(c->h_stage);
-    if (c->h_stage_ev) cudaEventDestroy(c->h_stage_ev);
+    for (auto &st : c->stage) {
+        if (st.h) cudaFreeHost(st.h);
+        if (st.ev) cudaEventDestroy(st.ev);
+    }
+    if (c->out_stream) cudaStreamDestroy(c->out_stream);
+    for (cudaEvent_t ev : c->half_done)
+        if (ev) cudaEventDestroy(ev);
     for (auto &b : c->io) b.release();
-    for (auto &b : c->pool) b.release();
+    for (auto &b : c->pipe_io) b.release();
+    for (auto &bank : c->pool)
+        for (auto &b : bank) b.release();
     cudaFree(c->d_D);
     cudaFree(c->d_bits);
     cudaFree(c->d_marg);

@@ -110,6 +110,19 @@ struct Options {
     int64_t support_part_words = 8192;
 };
 
+// Host arrays of the count planner, kept by the context between plan builds
+// so that a steady stream of batches allocates (and page-faults) nothing.
+struct PlanScratch {
+    std::vector<int64_t> base;      // first QVar slot of each query
+    std::vector<double> cost;       // cost-model estimate of each query
+    std::vector<int32_t> cells;     // table cells of each query
+    std::vector<uint32_t> cls;      // cost class of each query (descending order)
+    std::vector<uint8_t> passes;    // bitmap queries: first-variable passes (0 = none)
+    std::vector<int32_t> order, start, qlist;
+    std::vector<BTask> btasks;
+    size_t rest_bytes = 0;          // staging bytes past the QVars in the last plan
+};
+
 // Host worker threads of a context (the planner's per-query work).  run(n, f)
 // calls f(0) on the calling thread and f(1..n-1) on workers, and returns when
 // all have finished; workers sleep between runs.
@@ -193,18 +206,31 @@ struct fc_ctx {
     fc::Options opt;
     // scratch of the host-buffer entry points
     fc::DBuf io[3];
-    fc::DBuf pool[6];        // buffers lent to one-shot plans (descriptors, counters, tables, sort, pairs)
+    // buffers lent to one-shot plans (descriptors, counters, tables, sort,
+    // pairs), in two banks so that a synchronous call can have a plan
+    // running while it builds the next; `bank` selects the one in use
+    fc::DBuf pool[2][6];
+    fc::DBuf pipe_io[2];     // device outputs of the two halves of a pipelined call
+    int bank = 0;
+    int32_t q_base = 0;  // index of the plan's first query in the caller's batch (messages)
     bool borrow = false; // set while a synchronous entry point builds its plan
+    cudaStream_t out_stream = nullptr;  // device-to-host copies of pipelined calls
+    cudaEvent_t half_done[2] = {nullptr, nullptr};
     std::vector<uint32_t> mark;
     uint32_t epoch = 0;
     uint64_t generation = 0;  // bumped by every append; plans of older generations refuse to run
     std::vector<fc_plan *> live_plans;  // orphaned (device memory released) if the context goes first
     // pinned staging of plan descriptors: written on the host, copied by DMA;
     // the event marks the end of the last copy out of it
-    uint8_t *h_stage = nullptr;
-    size_t h_stage_bytes = 0;
-    cudaEvent_t h_stage_ev = nullptr;
+    // pinned staging of plan descriptors, one per bank; `ev` marks the end
+    // of the last upload from it
+    struct Stage {
+        uint8_t *h = nullptr;
+        size_t bytes = 0;
+        cudaEvent_t ev = nullptr;
+    } stage[2];
     std::unique_ptr<fc::PlanPool> pool_threads;  // started by the first large plan
+    std::unique_ptr<fc::PlanScratch> plan_scratch;
 };
 
 namespace fc {
@@ -286,23 +312,35 @@ namespace fc {
 inline cudaError_t plan_buf(fc_ctx *c, DBuf &b, int slot, size_t bytes)
 {
     if (!c->borrow) return b.ensure(bytes);
-    cudaError_t e = c->pool[slot].ensure(bytes);
+    DBuf &lent = c->pool[c->bank][slot];
+    cudaError_t e = lent.ensure(bytes);
     if (e != cudaSuccess) return e;
-    b.p = c->pool[slot].p;
-    b.bytes = c->pool[slot].bytes;
+    b.p = lent.p;
+    b.bytes = lent.bytes;
     b.owned = false;
     return cudaSuccess;
 }
 
 struct BorrowScope {
     fc_ctx *c;
-    explicit BorrowScope(fc_ctx *ctx) : c(ctx) { c->borrow = true; }
-    ~BorrowScope() { c->borrow = false; }
+    explicit BorrowScope(fc_ctx *ctx, int bank = 0) : c(ctx)
+    {
+        c->borrow = true;
+        c->bank = bank;
+    }
+    ~BorrowScope()
+    {
+        c->borrow = false;
+        c->bank = 0;
+    }
 };
 
-// Pinned host staging of at least `bytes` for plan descriptors, free of any
-// copy still reading it; nullptr on failure (fc_ctx.cu).
+// Pinned host staging (of the current bank) of at least `bytes` for plan
+// descriptors, free of any copy still reading it; nullptr on failure
+// (fc_ctx.cu).
 uint8_t *stage_host(fc_ctx *c, size_t bytes);
+// Grows the staging buffer to `bytes`, keeping its first `keep` bytes.
+uint8_t *stage_grow(fc_ctx *c, size_t bytes, size_t keep);
 // Copies `bytes` of the staging buffer to dst on the context stream and marks
 // the staging buffer busy until the copy ends (fc_ctx.cu).
 cudaError_t upload_stage(fc_ctx *c, void *dst, size_t bytes);

@@ -4,6 +4,7 @@
 // calls.
 #include "fc_host.h"
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <numeric>
@@ -14,11 +15,12 @@ using namespace fc;
 
 namespace fc {
 
-// Validates one query's variables and appends its QVars (arity-1 variables
-// dropped, strides of the caller's order, last fastest); returns the cells.
-// Reads the context only, so planner threads may call it concurrently (an
-// error's message goes to the calling thread's fc_last_error).
-int64_t describe(const fc_ctx *c, const int32_t *vars, int32_t k, std::vector<QVar> &qv, int32_t &k_eff)
+// Validates one query's variables and writes its QVars to out (room for k;
+// arity-1 variables dropped, strides of the caller's order, last fastest);
+// returns the cells.  Reads the context only, so planner threads may call it
+// concurrently (an error's message goes to the calling thread's
+// fc_last_error).
+int64_t describe_into(const fc_ctx *c, const int32_t *vars, int32_t k, QVar *out, int32_t &k_eff)
 {
     if (k < 0 || k > c->n) return fail(FC_ERR_ARG, "query has %d variables, n = %d", k, c->n);
     if (k > 0 && !vars) return fail(FC_ERR_ARG, "null variable list");
@@ -40,15 +42,26 @@ int64_t describe(const fc_ctx *c, const int32_t *vars, int32_t k, std::vector<QV
         for (int t = 1; t < k; ++t)
             if (sorted[t] == sorted[t - 1]) return fail(FC_ERR_ARG, "variable %d listed twice in one query", sorted[t]);
     }
+    // strides from the last variable; the kept variables are written from
+    // the back of their run and moved to its front
     int64_t stride = 1;
-    const size_t first = qv.size();
+    int32_t n_kept = 0;
     for (int t = k - 1; t >= 0; --t) {
         const int v = vars[t];
-        if (c->arity[v] > 1) qv.push_back(QVar{v, (int32_t)stride, c->arity[v], c->soff[v]});
+        if (c->arity[v] > 1) out[k - 1 - n_kept++] = QVar{v, (int32_t)stride, c->arity[v], c->soff[v]};
         stride *= c->arity[v];
     }
-    std::reverse(qv.begin() + first, qv.end());
-    k_eff = (int32_t)(qv.size() - first);
+    if (n_kept < k) std::memmove(out, out + (k - n_kept), sizeof(QVar) * n_kept);
+    k_eff = n_kept;
+    return cells;
+}
+
+int64_t describe(const fc_ctx *c, const int32_t *vars, int32_t k, std::vector<QVar> &qv, int32_t &k_eff)
+{
+    const size_t first = qv.size();
+    qv.resize(first + (size_t)std::max(k, 0));
+    const int64_t cells = describe_into(c, vars, k, qv.data() + first, k_eff);
+    qv.resize(cells < 0 ? first : first + (size_t)k_eff);
     return cells;
 }
 
@@ -153,37 +166,57 @@ QPlan choose(const fc_ctx *c, QVar *v, int k, int64_t cells, int32_t smem_cells,
     return QPlan{s, cost};
 }
 
-// Positions 0..n-1 ordered by decreasing key(i) (a positive cost), ties in
-// increasing position: a counting sort on the cost's exponent and top three
-// mantissa bits (1/8-octave classes), which is as much order as the
-// longest-processing-time-first assignment needs and avoids a comparison
-// sort's mispredicted branches on thousands of queries.
-template <class Key>
-void order_by_cost_desc(size_t n, Key key, std::vector<int32_t> &out)
+// Cost class of an estimate for the longest-first orders: its exponent and
+// top three mantissa bits (1/8-octave classes), complemented so that classes
+// ascend as costs descend.  Fewer than 2^14 classes exist.
+inline uint32_t cost_class(double v)
 {
-    constexpr int kBits = 14;  // 11 exponent + 3 mantissa bits of a positive double
-    std::vector<uint32_t> cls(n);
-    std::vector<int32_t> start((1 << kBits) + 1, 0);
-    for (size_t i = 0; i < n; ++i) {
-        double v = key(i);
-        if (!(v > 0.0)) v = 0.0;
-        uint64_t b;
-        std::memcpy(&b, &v, sizeof b);
-        cls[i] = ((1u << kBits) - 1u) - (uint32_t)(b >> (52 - 3));  // descending
-        ++start[cls[i] + 1];
-    }
-    for (int c = 0; c < (1 << kBits); ++c) start[c + 1] += start[c];
-    out.resize(n);
-    for (size_t i = 0; i < n; ++i) out[start[cls[i]]++] = (int32_t)i;
+    if (!(v > 0.0)) v = 0.0;
+    uint64_t b;
+    std::memcpy(&b, &v, sizeof b);
+    return ((1u << 14) - 1u) - (uint32_t)(b >> (52 - 3));
 }
 
-// Builds a count or score plan.  vars lists are read through `get`.
-template <class GetVars>
-int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off, int score_kind,
+// Queries q with want(q), ordered by ascending cls[q] (descending cost), ties
+// in increasing q: a counting sort over the class span [lo, hi] (longest-
+// processing-time-first needs no finer order, and it avoids a comparison
+// sort's mispredicted branches on thousands of queries).
+template <class Want>
+void order_by_class(int32_t nq, const std::vector<uint32_t> &cls, uint32_t lo, uint32_t hi, Want want,
+                    std::vector<int32_t> &out, std::vector<int32_t> &start)
+{
+    out.clear();
+    if (lo > hi) return;
+    const size_t span = (size_t)(hi - lo) + 1;
+    start.assign(span + 1, 0);
+    int32_t n = 0;
+    for (int32_t q = 0; q < nq; ++q)
+        if (want(q)) {
+            ++start[cls[q] - lo + 1];
+            ++n;
+        }
+    for (size_t c = 0; c < span; ++c) start[c + 1] += start[c];
+    out.resize(n);
+    for (int32_t q = 0; q < nq; ++q)
+        if (want(q)) out[start[cls[q] - lo]++] = q;
+}
+
+// Builds a count or score plan.  span(q) gives the length of query q's
+// variable list (or -1 after fail() for bad offsets); get(q, ...) the list.
+// The query heads and QVars are written straight into the pinned staging
+// buffer by the context's host threads, which take the queries in blocks and
+// also gather what the serial steps need (totals per strategy, compact
+// per-query cells, cost classes), so that those steps read small arrays and
+// touch the heads only where a value changes.
+template <class Span, class GetVars>
+int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_t *user_off, int score_kind,
                      double ess, fc_plan **out)
 {
     if (c->transactions) return fail(FC_ERR_STATE, "context holds transaction bitmaps; use the support calls");
     if (nq < 0) return fail(FC_ERR_ARG, "nq < 0");
+    if (!c->plan_scratch) c->plan_scratch.reset(new (std::nothrow) PlanScratch());
+    if (!c->plan_scratch) return fail(FC_ERR_OOM, "host allocation failed");
+    PlanScratch &S = *c->plan_scratch;
     fc_plan *p = new (std::nothrow) fc_plan();
     if (!p) return fail(FC_ERR_OOM, "host allocation failed");
     p->ctx = c;
@@ -201,124 +234,174 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     // SM in the wide launch, else the mixed launch's table area
     const bool wide = o.window_wide != 0;
     const int win_cells = std::max(1, std::min<int>(o.window_cells, wide ? (c->max_smem_optin - 4096) / 4 : max_cells));
-
     const double chunks_d = (double)((c->m + kChunkRows - 1) / kChunkRows);
-    std::vector<QHead> qh(nq);
-    std::vector<QVar> qv;
-    std::vector<double> cost(nq);
+    constexpr int32_t kThreadedQueries = 2048;  // smaller batches plan on the calling thread
+
+    // each query's QVars get slots of its list's length (arity-1 variables
+    // leave the end of a run unused)
+    S.base.resize((size_t)nq + 1);
+    S.base[0] = 0;
+    for (int32_t q = 0; q < nq; ++q) {
+        const int32_t k = span(q);
+        if (k < 0) {
+            fc_plan_free(p);
+            return FC_ERR_ARG;
+        }
+        S.base[q + 1] = S.base[q] + k;
+    }
+    const int64_t nvars = S.base[nq];
+    if (nvars > INT32_MAX) {
+        fc_plan_free(p);
+        return fail(FC_ERR_SIZE, "batch lists %lld variables", (long long)nvars);
+    }
+
+    // staging layout: [heads | QVars | items | score list | bitmap tasks]
+    const size_t o_qv = round_up(sizeof(QHead) * std::max(nq, 1), 256);
+    const size_t o_rest = o_qv + round_up(sizeof(QVar) * std::max<int64_t>(nvars, 1), 256);
+    uint8_t *host = stage_host(c, o_rest + S.rest_bytes);
+    if (!host) {
+        fc_plan_free(p);
+        return fail(FC_ERR_OOM, "pinned staging of %zu bytes", o_rest + S.rest_bytes);
+    }
+    QHead *qh = reinterpret_cast<QHead *>(host);
+    QVar *qv = reinterpret_cast<QVar *>(host + o_qv);
+    S.cost.resize(nq);
+    S.cells.resize(nq);
+    S.cls.resize(nq);
+    S.passes.resize(nq);
     p->strategy.resize(nq);
     p->table_off.assign(nq + 1, 0);
 
-    // Per query: validation, QVars and strategy.  Large batches split into
-    // contiguous query ranges on host threads (each query's work only reads
-    // the context); the ranges' QVars are concatenated in query order.
-    struct Range {
-        std::vector<QVar> qv;
-        int32_t err_q = -1;
-        int err_code = 0;
-        std::string err_msg;
-    };
+    // Per query: validation, QVars, strategy, heads.  Host threads take
+    // blocks of queries in order; the lowest failing query is reported
+    // (blocks past a failure are skipped, blocks before it all finish).
+    constexpr int32_t kBlock = 256;
     int nthreads = 1;
-    if (nq >= 4096) nthreads = (int)std::max<int64_t>(1, std::min<int64_t>(fc::host_threads(c), nq / 1024));
-    std::vector<Range> ranges(nthreads);
+    if (nq >= kThreadedQueries)
+        nthreads = (int)std::max<int64_t>(1, std::min<int64_t>(fc::host_threads(c), nq / 1024));
+    struct Tally {
+        int32_t fail_q = INT32_MAX;
+        int fail_code = 0;
+        std::string fail_msg;
+        int64_t n[6] = {0, 0, 0, 0, 0, 0};  // queries per strategy
+        int64_t window_items = 0;             // windows over all windowed queries
+        double bitmap_cost = 0.0;
+        uint32_t lo[2] = {UINT32_MAX, UINT32_MAX}, hi[2] = {0, 0};  // class spans: [0] items, [1] bitmap
+        std::vector<int32_t> sorts;
+    };
+    std::vector<Tally> tallies(nthreads);
+    std::atomic<int32_t> next_block{0}, first_bad{INT32_MAX};
     auto work = [&](int t) {
-        Range &R = ranges[t];
-        const int32_t q0 = (int32_t)((int64_t)nq * t / nthreads), q1 = (int32_t)((int64_t)nq * (t + 1) / nthreads);
-        R.qv.reserve((size_t)(q1 - q0) * 4);
         std::vector<int32_t> buf;
-        for (int32_t q = q0; q < q1; ++q) {
-            const int32_t *vars;
-            int32_t k;
-            int32_t child;
-            if (!get(q, vars, k, child, buf)) {
-                R.err_q = q;
-                R.err_code = FC_ERR_ARG;
-                R.err_msg = g_err;
-                return;
+        Tally &T = tallies[t];
+        auto failed = [&](int32_t q, int code) {
+            T.fail_q = q;
+            T.fail_code = code;
+            T.fail_msg = g_err;
+            int32_t cur = first_bad.load(std::memory_order_relaxed);
+            while (q < cur && !first_bad.compare_exchange_weak(cur, q, std::memory_order_relaxed)) {
             }
-            const size_t first = R.qv.size();
-            int32_t k_eff = 0;
-            const int64_t cells = describe(c, vars, k, R.qv, k_eff);
-            if (cells < 0) {
-                R.err_q = q;
-                R.err_code = (int)cells;
-                R.err_msg = g_err;
-                return;
+        };
+        for (;;) {
+            const int32_t q0 = next_block.fetch_add(kBlock, std::memory_order_relaxed);
+            if (q0 >= nq || q0 > first_bad.load(std::memory_order_relaxed)) return;
+            const int32_t q1 = std::min(nq, q0 + kBlock);
+            for (int32_t q = q0; q < q1; ++q) {
+                const int32_t *vars;
+                int32_t k, child, k_eff = 0;
+                int64_t cells = FC_ERR_ARG;
+                QVar *qq = qv + S.base[q];
+                if (get(q, vars, k, child, buf)) cells = describe_into(c, vars, k, qq, k_eff);
+                if (cells < 0) return failed(q, (int)cells);
+                int64_t toff = 0;
+                if (user_off) {
+                    if (user_off[q + 1] - user_off[q] < cells || user_off[q] < 0) {
+                        fail(FC_ERR_ARG, "table_off of query %d leaves %lld cells, it needs %lld", q + c->q_base,
+                             (long long)(user_off[q + 1] - user_off[q]), (long long)cells);
+                        return failed(q, FC_ERR_ARG);
+                    }
+                    toff = user_off[q];
+                    p->table_off[q] = toff;
+                }
+                const QPlan ch = choose(c, qq, k_eff, cells, max_cells, win_cells, chunks_d);
+                const int s = ch.strategy;
+                const int32_t nwin = s == kWindow ? (int32_t)((cells + win_cells - 1) / win_cells) : 1;  // <= kMaxWindows
+                QHead &h = qh[q];
+                h.table_off = toff;
+                h.cells = (int32_t)cells;
+                h.var_off = (int32_t)S.base[q];
+                h.k = (int16_t)k_eff;
+                h.strategy = (int16_t)s;
+                h.nparts = (int16_t)nwin;  // row splits and bitmap tasks are set later
+                h.score_kind = (int16_t)score_kind;
+                h.r_child = score_kind == kNoScore ? 1 : c->arity[child];
+                h.child_soff = score_kind == kNoScore ? 0 : c->soff[child];
+                h.score_slot = q;
+                h.nwin = nwin;
+                p->strategy[q] = s;
+                S.cost[q] = ch.cost;
+                S.cells[q] = (int32_t)cells;
+                const uint32_t cl = cost_class(ch.cost / nwin);
+                S.cls[q] = cl;
+                S.passes[q] = (uint8_t)((s == kBitmap && o.bitmap_small && k_eff == 3 && small_ok(qq, 3)) ? qq[0].arity : 0);
+                ++T.n[s];
+                if (s == kSort) {
+                    T.sorts.push_back(q);
+                } else {
+                    const int g = s == kBitmap ? 1 : 0;
+                    T.lo[g] = std::min(T.lo[g], cl);
+                    T.hi[g] = std::max(T.hi[g], cl);
+                    if (s == kBitmap) T.bitmap_cost += ch.cost;
+                    if (s == kWindow) T.window_items += nwin;
+                }
             }
-            const QPlan ch = choose(c, R.qv.data() + first, k_eff, cells, max_cells, win_cells, chunks_d);
-            QHead &h = qh[q];
-            h.cells = (int32_t)cells;
-            h.var_off = (int32_t)first;  // within the range for now
-            h.k = (int16_t)k_eff;
-            h.strategy = (int16_t)ch.strategy;
-            h.nparts = 1;
-            h.score_kind = (int16_t)score_kind;
-            h.r_child = score_kind == kNoScore ? 1 : c->arity[child];
-            h.child_soff = score_kind == kNoScore ? 0 : c->soff[child];
-            h.score_slot = q;
-            p->strategy[q] = ch.strategy;
-            cost[q] = ch.cost;
         }
     };
     fc::run_host_threads(c, nthreads, work);
-    for (const Range &R : ranges)
-        if (R.err_q >= 0) {  // the first failing range holds the lowest failing query
-            fc_plan_free(p);
-            return fail(R.err_code, "%s", R.err_msg.c_str());
-        }
+    Tally all;
     {
-        size_t total = 0;
-        for (const Range &R : ranges) total += R.qv.size();
-        qv.reserve(total);
-        for (int t = 0; t < nthreads; ++t) {
-            const int32_t base = (int32_t)qv.size();
-            const int32_t q0 = (int32_t)((int64_t)nq * t / nthreads), q1 = (int32_t)((int64_t)nq * (t + 1) / nthreads);
-            for (int32_t q = q0; q < q1; ++q) qh[q].var_off += base;
-            qv.insert(qv.end(), ranges[t].qv.begin(), ranges[t].qv.end());
+        const Tally *worst = nullptr;
+        for (const Tally &T : tallies)
+            if (T.fail_q != INT32_MAX && (!worst || T.fail_q < worst->fail_q)) worst = &T;
+        if (worst) {
+            fc_plan_free(p);
+            return fail(worst->fail_code, "%s", worst->fail_msg.c_str());
         }
+        for (const Tally &T : tallies) {
+            for (int s = 0; s < 6; ++s) all.n[s] += T.n[s];
+            all.window_items += T.window_items;
+            all.bitmap_cost += T.bitmap_cost;
+            for (int g = 0; g < 2; ++g) {
+                all.lo[g] = std::min(all.lo[g], T.lo[g]);
+                all.hi[g] = std::max(all.hi[g], T.hi[g]);
+            }
+            all.sorts.insert(all.sorts.end(), T.sorts.begin(), T.sorts.end());
+        }
+        std::sort(all.sorts.begin(), all.sorts.end());
     }
 
-    int64_t scratch = 0;
-    for (int32_t q = 0; q < nq; ++q) {
-        QHead &h = qh[q];
-        const int64_t cells = h.cells;
-        if (score_kind == kNoScore) {
-            if (user_off) {
-                if (user_off[q + 1] - user_off[q] < cells || user_off[q] < 0) {
-                    fc_plan_free(p);
-                    return fail(FC_ERR_ARG, "table_off of query %d leaves %lld cells, it needs %lld", q,
-                                (long long)(user_off[q + 1] - user_off[q]), (long long)cells);
-                }
-                p->table_off[q] = user_off[q];
-            } else {
-                p->table_off[q] = scratch;
-                scratch += cells;
+    // table offsets of count plans: the caller's, else dense in query order
+    if (score_kind == kNoScore) {
+        if (user_off) {
+            p->table_off[nq] = user_off[nq];
+        } else {
+            int64_t off = 0;
+            for (int32_t q = 0; q < nq; ++q) {
+                p->table_off[q] = off;
+                qh[q].table_off = off;
+                off += S.cells[q];
             }
-            h.table_off = p->table_off[q];
+            p->table_off[nq] = off;
         }
-        if (user_off) p->table_off[nq] = user_off[nq];
-        else p->table_off[nq] = scratch;
+        p->out_cells = p->table_off[nq];
     }
-    if (score_kind == kNoScore) p->out_cells = p->table_off[nq];
 
     // work items: split rows when the batch alone cannot fill the GPU
-    const size_t smem_bytes = (size_t)max_cells * 4;
-    int per_sm = std::max(1, o.ctas_per_sm);
-    p->grid = c->num_sms * per_sm;
-    p->smem = smem_bytes;
+    p->grid = c->num_sms * std::max(1, o.ctas_per_sm);
+    p->smem = (size_t)max_cells * 4;
     const int64_t nchunks = (c->m + kChunkRows - 1) / kChunkRows;
     const int64_t max_parts_rows = std::max<int64_t>(1, c->m / std::max<int64_t>(o.min_part_rows, kChunkRows));
-    int32_t persistent = 0;
-    int64_t window_items = 0;
-    for (int32_t q = 0; q < nq; ++q) {
-        QHead &h = qh[q];
-        h.nwin = 1;
-        if (h.strategy == kHist || h.strategy == kGAtomic) ++persistent;
-        if (h.strategy == kWindow) {
-            h.nwin = (int32_t)(((int64_t)h.cells + win_cells - 1) / win_cells);  // <= kMaxWindows
-            window_items += h.nwin;
-        }
-    }
+    const int64_t persistent = all.n[kHist] + all.n[kGAtomic];
     // (marginal items hold no rows, so they never split)
     const int64_t target = (int64_t)p->grid * 4;
     int64_t parts = 1;
@@ -331,84 +414,61 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     p->wgrid = wide ? c->num_sms : p->grid;
     p->wsmem = (size_t)win_cells * 4;
     int64_t wparts = 1;
-    if (window_items > 0 && window_items < p->wgrid)
-        wparts = std::min<int64_t>({nchunks, max_parts_rows, (2 * (int64_t)p->wgrid + window_items - 1) / window_items});
+    if (all.window_items > 0 && all.window_items < p->wgrid)
+        wparts = std::min<int64_t>(
+            {nchunks, max_parts_rows, (2 * (int64_t)p->wgrid + all.window_items - 1) / all.window_items});
     wparts = std::max<int64_t>(1, wparts);
-    std::vector<Item> items;
-    std::vector<int32_t> hq;  // queries that become work items of count_kernel
-    std::vector<int32_t> qlist;
-    std::vector<std::pair<double, int32_t>> bmo;
-    hq.reserve(nq);
-    size_t n_items = 0;
-    for (int32_t q = 0; q < nq; ++q) {
-        QHead &h = qh[q];
-        if (h.strategy == kSort) {
-            p->sort_jobs.push_back(SortJob{q, h.k, 0, h.cells, 0, nullptr});
-            continue;
+    int64_t window_parts = all.window_items;  // items of all windowed queries
+    if (parts > 1 || wparts > 1) {
+        window_parts = 0;
+        for (int32_t q = 0; q < nq; ++q) {
+            const int s = p->strategy[q];
+            if (s == kHist || s == kGAtomic) {
+                qh[q].nparts = (int16_t)parts;
+            } else if (s == kWindow) {
+                const int32_t nwin = qh[q].nwin;
+                qh[q].nparts = (int16_t)(std::max<int64_t>(1, std::min<int64_t>(wparts, 32767 / nwin)) * nwin);
+                window_parts += qh[q].nparts;
+            }
         }
-        if (h.strategy == kBitmap) {
-            bmo.push_back({cost[q], q});
-            continue;
-        }
-        const int64_t qparts = h.strategy == kMarginal ? 1
-                               : h.strategy == kWindow ? std::max<int64_t>(1, std::min<int64_t>(wparts, 32767 / h.nwin)) * h.nwin
-                                                       : parts;
-        h.nparts = (int16_t)qparts;
-        hq.push_back(q);
-        n_items += (size_t)qparts;
     }
-    // heaviest first by cost per part; a query's parts are consecutive, and
-    // within a cost class queries keep their order
-    std::vector<int32_t> perm;
-    order_by_cost_desc(hq.size(), [&](size_t i) { return cost[hq[i]] / qh[hq[i]].nparts; }, perm);
-    items.reserve(n_items);
-    std::vector<Item> witems;
-    for (int32_t i : perm) {
-        const int32_t q = hq[i];
-        std::vector<Item> &dst = wide && qh[q].strategy == kWindow ? witems : items;
-        for (int32_t part = 0; part < qh[q].nparts; ++part) dst.push_back(Item{q, part});
-    }
-    p->n_items = (int32_t)items.size();
-    p->n_witems = (int32_t)witems.size();
-    items.insert(items.end(), witems.begin(), witems.end());
+    const int64_t n_narrow = persistent * parts + all.n[kMarginal] + (wide ? 0 : window_parts);
+    p->n_items = (int32_t)n_narrow;
+    p->n_witems = (int32_t)(wide ? window_parts : 0);
+
     // bitmap queries: warp tasks of consecutive 4096-row chunks, heaviest
     // queries first.  A query gets tasks in proportion to its estimated cost
     // (about four tasks' worth of work per warp of the launch), each of at
     // least kMinTaskChunks chunks, so that light queries are not cut into
     // tasks whose fixed costs (dispatch, one reduction and atomic per cell)
     // outweigh their work.
-    {
-        order_by_cost_desc(bmo.size(), [&](size_t i) { return bmo[i].first; }, perm);
-        std::vector<std::pair<double, int32_t>> sorted;
-        sorted.reserve(bmo.size());
-        for (int32_t i : perm) sorted.push_back(bmo[i]);
-        bmo.swap(sorted);
-    }
-    std::vector<BTask> btasks;
-    btasks.reserve(bmo.size() * 4);
+    std::vector<BTask> &btasks = S.btasks;
+    btasks.clear();
     p->bm_threads = std::max(32, std::min(1024, o.bitmap_threads / 32 * 32));
     p->stage_slots = o.stage_slots;
     p->small_paths = o.bitmap_small;
-    if (!bmo.empty()) {
+    if (all.n[kBitmap] > 0) {
         constexpr int64_t kMinTaskChunks = 4;
+        std::vector<int32_t> &order = S.order;
+        order_by_class(nq, S.cls, all.lo[1], all.hi[1], [&](int32_t q) { return p->strategy[q] == kBitmap; },
+                       order, S.start);
         p->bm_grid = c->num_sms * bitmap_ctas_per_sm(p->bm_threads, p->stage_slots);
         const int64_t warps = (int64_t)p->bm_grid * (p->bm_threads / 32);
-        double total = 0.0;
-        for (auto &x : bmo) total += x.first;
-        const double unit = std::max(total / (4.0 * (double)warps), 1e-30);
+        const double unit = std::max(all.bitmap_cost / (4.0 * (double)warps), 1e-30);
         const int64_t max_tasks = std::max<int64_t>(1, std::min<int64_t>(nchunks / kMinTaskChunks, 32767));
-        for (auto &x : bmo) {
-            const int32_t q = x.second;
+        for (const int32_t q : order) {
             // a 3-variable register-blocked query splits by the first
-            // variable's state as well (one pass over the chunks per state)
-            const QVar *ov = qv.data() + qh[q].var_off;
-            const int32_t passes = (p->small_paths && qh[q].k == 3 && small_ok(ov, 3)) ? ov[0].arity : 0;
-            const double per = x.first / std::max(1, passes);
-            const int64_t t = std::max<int64_t>(1, std::min<int64_t>(max_tasks, (int64_t)std::ceil(per / unit)));
-            qh[q].nparts = (int16_t)std::min<int64_t>(t * std::max(1, passes), 32767);
+            // variable's state as well (one pass over the chunks per state);
+            // its tasks (the score ticket count) stay below 2^15
+            const int32_t passes = S.passes[q];
+            const int32_t pmul = std::max(1, passes);
+            const double per = S.cost[q] / pmul;
+            const int64_t t = std::max<int64_t>(
+                1, std::min<int64_t>({max_tasks, 32767 / pmul, (int64_t)std::ceil(per / unit)}));
+            qh[q].nparts = (int16_t)(t * pmul);
             // t balanced chunk ranges: the first nchunks % t get one extra chunk
             const int64_t base = nchunks / t, rem = nchunks % t;
-            for (int32_t s0 = passes > 0 ? 0 : -1; s0 < std::max(passes, 0); ++s0) {
+            for (int32_t s0 = passes > 0 ? 0 : -1; s0 < passes; ++s0) {
                 int64_t c0 = 0;
                 for (int64_t part = 0; part < t; ++part) {
                     const int64_t c1 = c0 + base + (part < rem ? 1 : 0);
@@ -420,53 +480,70 @@ int build_count_plan(fc_ctx *c, int32_t nq, GetVars get, const int64_t *user_off
     }
     p->n_btasks = (int32_t)btasks.size();
 
-    // tables that must exist in global memory for score plans
+    // tables that must exist in global memory for score plans: all but the
+    // shared-memory ones of a single item
     if (score_kind != kNoScore) {
+        int64_t off = 0;
         for (int32_t q = 0; q < nq; ++q) {
-            QHead &h = qh[q];
-            const bool global = (h.strategy != kHist && h.strategy != kMarginal) || h.nparts > 1;
+            const int s = p->strategy[q];
+            const bool global = s == kMarginal ? false : s == kHist ? parts > 1 : true;
             if (global) {
-                h.table_off = scratch;
-                scratch += h.cells;
-            } else {
-                h.table_off = 0;
+                qh[q].table_off = off;
+                off += S.cells[q];
             }
         }
-        p->table_buf_cells = scratch;
+        p->table_buf_cells = off;
     } else {
         p->table_buf_cells = p->out_cells;
     }
-    for (int32_t q = 0; q < nq; ++q) {
+    // tables some item adds to (rather than stores whole) start from zero
+    p->zero_tables = all.n[kBitmap] + all.n[kGAtomic] + all.n[kSort] > 0 || (all.n[kHist] > 0 && parts > 1) ||
+                     (all.n[kWindow] > 0 && wparts > 1);
+    std::vector<int32_t> &qlist = S.qlist;
+    qlist.clear();
+    for (const int32_t q : all.sorts) {
         const QHead &h = qh[q];
-        // a window over all rows stores every cell of its range
-        const bool stores_all = h.strategy == kWindow ? h.nparts == h.nwin
-                                                      : (h.strategy == kHist || h.strategy == kMarginal) && h.nparts == 1;
-        if (!stores_all) p->zero_tables = true;
-    }
-    for (auto &j : p->sort_jobs) {
-        j.table_off = qh[j.q].table_off;
+        SortJob j{q, h.k, 0, h.cells, 0, nullptr};
+        j.table_off = h.table_off;
         j.key_bits = j.cells > 1 ? 32 - __builtin_clz((uint32_t)(j.cells - 1)) : 0;
-        if (score_kind != kNoScore) qlist.push_back(j.q);
+        p->sort_jobs.push_back(j);
+        if (score_kind != kNoScore) qlist.push_back(q);
     }
     p->n_qlist = (int32_t)qlist.size();
 
-    // one device allocation for all descriptors
-    const size_t b_qh = sizeof(QHead) * std::max(nq, 1);
-    const size_t b_qv = sizeof(QVar) * std::max<size_t>(qv.size(), 1);
-    const size_t b_it = sizeof(Item) * std::max<size_t>(items.size(), 1);
+    // the rest of the staging buffer: items straight into it (heaviest
+    // first by cost per part, a query's parts consecutive, the windows of
+    // the wide launch after the mixed launch's items), then the score list
+    // and the bitmap tasks
+    const size_t n_all_items = (size_t)(n_narrow + p->n_witems);
+    const size_t b_it = sizeof(Item) * std::max<size_t>(n_all_items, 1);
     const size_t b_ql = sizeof(int32_t) * std::max<size_t>(qlist.size(), 1);
     const size_t b_bq = sizeof(BTask) * std::max<size_t>(btasks.size(), 1);
-    const size_t o_qv = round_up(b_qh, 256), o_it = o_qv + round_up(b_qv, 256), o_ql = o_it + round_up(b_it, 256);
-    const size_t o_bq = o_ql + round_up(b_ql, 256);
+    const size_t o_it = o_rest, o_ql = o_it + round_up(b_it, 256), o_bq = o_ql + round_up(b_ql, 256);
     const size_t total = o_bq + round_up(b_bq, 256);
-    uint8_t *host = stage_host(c, total);
+    S.rest_bytes = total - o_rest;
+    host = stage_grow(c, total, o_rest);
     if (!host) {
         fc_plan_free(p);
         return fail(FC_ERR_OOM, "pinned staging of %zu bytes", total);
     }
-    std::memcpy(host, qh.data(), sizeof(QHead) * nq);
-    std::memcpy(host + o_qv, qv.data(), sizeof(QVar) * qv.size());
-    std::memcpy(host + o_it, items.data(), sizeof(Item) * items.size());
+    qh = reinterpret_cast<QHead *>(host);
+    {
+        Item *it = reinterpret_cast<Item *>(host + o_it);
+        Item *wit = it + n_narrow;
+        auto item_query = [&](int32_t q) {
+            const int s = p->strategy[q];
+            return s == kHist || s == kGAtomic || s == kMarginal || s == kWindow;
+        };
+        std::vector<int32_t> &order = S.order;
+        order_by_class(nq, S.cls, all.lo[0], all.hi[0], item_query, order, S.start);
+        for (const int32_t q : order) {
+            const int s = p->strategy[q];
+            const int32_t np = s == kMarginal ? 1 : s == kWindow ? qh[q].nparts : (int32_t)parts;
+            Item *&dst = wide && s == kWindow ? wit : it;
+            for (int32_t part = 0; part < np; ++part) *dst++ = Item{q, part};
+        }
+    }
     std::memcpy(host + o_ql, qlist.data(), sizeof(int32_t) * qlist.size());
     std::memcpy(host + o_bq, btasks.data(), sizeof(BTask) * btasks.size());
     cudaError_t e = plan_buf(c, p->desc, 0, total);
@@ -683,7 +760,12 @@ extern "C" int fc_plan_count(fc_ctx *c, int32_t nq, const int32_t *var_off, cons
         child = -1;
         return true;
     };
-    return build_count_plan(c, nq, get, table_off, kNoScore, 1.0, out);
+    auto span = [&](int32_t q) -> int32_t {
+        const int32_t a = var_off[q], b = var_off[q + 1];
+        if (a < 0 || b < a) return fail(FC_ERR_ARG, "var_off must be non-decreasing and non-negative"), -1;
+        return b - a;
+    };
+    return build_count_plan(c, nq, span, get, table_off, kNoScore, 1.0, out);
 }
 
 extern "C" int fc_plan_score(fc_ctx *c, int32_t nq, const int32_t *child, const int32_t *par_off,
@@ -711,7 +793,14 @@ extern "C" int fc_plan_score(fc_ctx *c, int32_t nq, const int32_t *child, const 
         ch = child[q];
         return true;
     };
-    return build_count_plan(c, nq, get, nullptr, kind, ess, out);
+    auto span = [&](int32_t q) -> int32_t {
+        const int32_t a = par_off[q], b = par_off[q + 1];
+        if (a < 0 || b < a || (b > a && !parents))
+            return fail(FC_ERR_ARG, "par_off must be non-decreasing and non-negative"), -1;
+        if (b - a >= INT32_MAX) return fail(FC_ERR_ARG, "parent list too long"), -1;
+        return b - a + 1;
+    };
+    return build_count_plan(c, nq, span, get, nullptr, kind, ess, out);
 }
 
 namespace {
@@ -834,11 +923,97 @@ extern "C" int fc_count(fc_ctx *c, const int32_t *vars, int32_t k, int32_t *tabl
     return fc_count_batch(c, 1, off, vars, nullptr, table);
 }
 
+namespace {
+
+// Batches at least this large run a synchronous call in two halves.
+constexpr int32_t kPipelineQueries = 4096;
+
+// A synchronous call in two halves of its batch: the second half is planned
+// on the host while the first half's kernels run, and each half's output is
+// copied to the host on a second stream while the GPU goes on.  build(h, q0,
+// q1, &plan, &offset, &bytes) plans queries [q0, q1) with bank h lent to it
+// and says where its output goes in the host buffer.
+template <class Build>
+int run_in_halves(fc_ctx *c, int32_t nq, uint8_t *host, Build build)
+{
+    if (!c->out_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->out_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            c->out_stream = nullptr;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+    }
+    for (cudaEvent_t &ev : c->half_done)
+        if (!ev) {
+            cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) {
+                ev = nullptr;
+                return cuda_fail(e, "cudaEventCreate");
+            }
+        }
+    fc_plan *plans[2] = {nullptr, nullptr};
+    int rc = FC_OK;
+    const int32_t mid = nq / 2;
+    for (int h = 0; h < 2 && rc == FC_OK; ++h) {
+        const int32_t q0 = h ? mid : 0, q1 = h ? nq : mid;
+        size_t off = 0, bytes = 0;
+        {
+            BorrowScope b(c, h);
+            c->q_base = q0;
+            rc = build(h, q0, q1, &plans[h], &off, &bytes);
+            c->q_base = 0;
+        }
+        if (rc != FC_OK) break;
+        cudaError_t e = c->pipe_io[h].ensure(std::max<size_t>(bytes, 4));
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "output buffer");
+            break;
+        }
+        rc = run_plan(plans[h], c->pipe_io[h].p, nullptr, nullptr, c->stream, false);
+        if (rc != FC_OK) break;
+        e = cudaEventRecord(c->half_done[h], c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->out_stream, c->half_done[h], 0);
+        if (e == cudaSuccess && bytes > 0)
+            e = cudaMemcpyAsync(host + off, c->pipe_io[h].p, bytes, cudaMemcpyDeviceToHost, c->out_stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copy outputs");
+    }
+    const cudaError_t e = cudaStreamSynchronize(c->out_stream);
+    const int status = read_status(c, c->stream);
+    for (fc_plan *p : plans)
+        if (p) fc_plan_free(p);
+    if (rc != FC_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "copy outputs");
+    return status;
+}
+
+}  // namespace
+
 extern "C" int fc_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int32_t *vars,
                               const int64_t *table_off, int32_t *tables)
 {
     if (!c || (nq > 0 && !tables)) return fail(FC_ERR_ARG, "fc_count_batch: null argument");
     DevGuard g(c->device);
+    if (nq >= kPipelineQueries && var_off && vars && !c->transactions) {
+        if (table_off && table_off[0] < 0) return fail(FC_ERR_ARG, "table_off must be non-negative");
+        std::vector<int64_t> rel;
+        int64_t dense = 0;  // cells of the first half when the tables are packed
+        auto build = [&](int, int32_t q0, int32_t q1, fc_plan **p, size_t *off, size_t *bytes) -> int {
+            const int64_t *uo = nullptr;
+            if (table_off) {
+                rel.resize((size_t)(q1 - q0) + 1);
+                for (int32_t q = q0; q <= q1; ++q) rel[q - q0] = table_off[q] - table_off[q0];
+                uo = rel.data();
+            }
+            const int rc = fc_plan_count(c, q1 - q0, var_off + q0, vars, uo, p);
+            if (rc != FC_OK) return rc;
+            const int64_t base = table_off ? table_off[q0] : (q0 ? dense : 0);
+            if (!table_off && q0 == 0) dense = (*p)->out_cells;
+            *off = sizeof(int32_t) * (size_t)base;
+            *bytes = sizeof(int32_t) * (size_t)(*p)->out_cells;
+            return FC_OK;
+        };
+        return run_in_halves(c, nq, reinterpret_cast<uint8_t *>(tables), build);
+    }
     fc_plan *p = nullptr;
     int rc;
     {
@@ -856,6 +1031,15 @@ extern "C" int fc_score_batch(fc_ctx *c, int32_t nq, const int32_t *child, const
 {
     if (!c || (nq > 0 && !scores)) return fail(FC_ERR_ARG, "fc_score_batch: null argument");
     DevGuard g(c->device);
+    if (nq >= kPipelineQueries && child && par_off && !c->transactions) {
+        auto build = [&](int, int32_t q0, int32_t q1, fc_plan **p, size_t *off, size_t *bytes) -> int {
+            const int rc = fc_plan_score(c, q1 - q0, child + q0, par_off + q0, parents, kind, ess, p);
+            *off = sizeof(float) * (size_t)q0;
+            *bytes = sizeof(float) * (size_t)(q1 - q0);
+            return rc;
+        };
+        return run_in_halves(c, nq, reinterpret_cast<uint8_t *>(scores), build);
+    }
     fc_plan *p = nullptr;
     int rc;
     {

@@ -215,6 +215,38 @@ def test_large_batch_validation_errors():
         assert abs(float(s1[q]) - w) <= 1e-5 * abs(w) + 1e-12
 
 
+def test_two_half_batches_offsets_and_errors():
+    """Batches of 4096+ queries run in two halves (the second planned while
+    the first runs): padded caller offsets, packed offsets (table_off NULL
+    through the C ABI), and a bad offset in the second half reported with its
+    query's index in the whole batch."""
+    db = random_dag_database(14, 30_011, 2, 4, 3, 1.0, seed=23)
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    queries = random_queries(db.n, 6001, 1, 5, seed=24)
+    off, flat = fc.pack_lists(queries)
+    cells = np.array([int(np.prod([db.arities[v] for v in q])) for q in queries], dtype=np.int64)
+    padded = np.zeros(len(queries) + 1, dtype=np.int64)
+    padded[1:] = np.cumsum(cells + 3)
+    tables, _ = fc.fc_count_batch(ctx, off, flat, padded)
+    for q in range(0, len(queries), 37):
+        assert np.array_equal(tables[padded[q]:padded[q] + cells[q]].astype(np.int64), orc.table(queries[q]))
+    lib = fc.load_library()
+    packed = np.zeros(int(cells.sum()), dtype=np.int32)
+    rc = lib.fc_count_batch(ctx.ptr, len(queries), fc._ptr(off, fc._i32p), fc._ptr(flat, fc._i32p), None,
+                            fc._ptr(packed))
+    assert rc == fc.FC_OK, fc.fc_last_error()
+    dense = np.concatenate([[0], np.cumsum(cells)])
+    for q in range(3, len(queries), 41):
+        assert np.array_equal(packed[dense[q]:dense[q + 1]], tables[padded[q]:padded[q] + cells[q]])
+    short = padded.copy()
+    short[4001:] -= cells[4000] + 3 - 1                 # query 4000 gets one cell
+    if cells[4000] > 1:
+        with pytest.raises(fc.FcError) as e:
+            fc.fc_count_batch(ctx, off, flat, short)
+        assert e.value.code == fc.FC_ERR_ARG and "query 4000 " in str(e.value)
+
+
 def test_row_major_load_and_assignment_count():
     """fc_load with a row-major database; Count of a specific assignment
     (the worked example of Sec. 2 lives in tests/golden)."""
