@@ -1142,7 +1142,7 @@ cudaError_t launch_count_wide(const CountParams &p, int grid, size_t smem, cudaS
 
 cudaError_t launch_bitmap(const CountParams &p, int grid, int threads, cudaStream_t s)
 {
-    if (threads > kBitmapWarps * 32) return cudaErrorInvalidValue;
+    if (threads > 256) return cudaErrorInvalidValue;  // __launch_bounds__(256, 2)
     const size_t smem = bitmap_smem_bytes(threads, p.stage_slots);
     cudaError_t e = ensure_smem_attr((const void *)bitmap_kernel, g_bitmap_smem, smem);
     if (e != cudaSuccess) return e;

@@ -227,12 +227,16 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
     p->score_kind = score_kind;
     p->ess = ess;
     const Options &o = c->opt;
-    p->threads = std::max(32, std::min(512, o.threads / 32 * 32));
-    const int max_cells = std::max(1, std::min<int>(o.smem_cells, (c->max_smem_optin - 4096) / 4));
-    p->smem_cells = max_cells;
+    int threads = std::max(32, std::min(512, o.threads / 32 * 32));
+    int ctas_per_sm = std::max(1, o.ctas_per_sm);
+    int max_cells = std::max(1, std::min<int>(o.smem_cells, (c->max_smem_optin - 4096) / 4));
     // cells of one window of a windowed table: the whole shared memory of an
     // SM in the wide launch, else the mixed launch's table area
     const bool wide = o.window_wide != 0;
+    // the small launch shape (more, smaller CTAs: their per-item barriers and
+    // flushes overlap better) when few shared-memory tables need more room
+    constexpr int kSmallShapeThreads = 256, kSmallShapeCtas = 6, kSmallShapeCells = 8192;
+    const bool auto_shape = o.shape_auto != 0 && wide && max_cells > kSmallShapeCells;
     const int win_cells = std::max(1, std::min<int>(o.window_cells, wide ? (c->max_smem_optin - 4096) / 4 : max_cells));
     const double chunks_d = (double)((c->m + kChunkRows - 1) / kChunkRows);
     constexpr int32_t kThreadedQueries = 2048;  // smaller batches plan on the calling thread
@@ -285,6 +289,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
         std::string fail_msg;
         int64_t n[6] = {0, 0, 0, 0, 0, 0};  // queries per strategy
         int64_t window_items = 0;             // windows over all windowed queries
+        int64_t mid_hist = 0;                 // shared-memory tables beyond the small launch shape
         double bitmap_cost = 0.0;
         uint32_t lo[2] = {UINT32_MAX, UINT32_MAX}, hi[2] = {0, 0};  // class spans: [0] items, [1] bitmap
         std::vector<int32_t> sorts;
@@ -345,6 +350,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
                 S.cls[q] = cl;
                 S.passes[q] = (uint8_t)((s == kBitmap && o.bitmap_small && k_eff == 3 && small_ok(qq, 3)) ? qq[0].arity : 0);
                 ++T.n[s];
+                if (s == kHist && cells > kSmallShapeCells) ++T.mid_hist;
                 if (s == kSort) {
                     T.sorts.push_back(q);
                 } else {
@@ -370,6 +376,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
         for (const Tally &T : tallies) {
             for (int s = 0; s < 6; ++s) all.n[s] += T.n[s];
             all.window_items += T.window_items;
+            all.mid_hist += T.mid_hist;
             all.bitmap_cost += T.bitmap_cost;
             for (int g = 0; g < 2; ++g) {
                 all.lo[g] = std::min(all.lo[g], T.lo[g]);
@@ -379,6 +386,45 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
         }
         std::sort(all.sorts.begin(), all.sorts.end());
     }
+
+    // launch shape: the small one unless more than 1/64 of the queries are
+    // shared-memory tables that it cannot hold; those few are planned again
+    // with its table area
+    if (auto_shape && all.mid_hist * 64 <= nq) {
+        threads = kSmallShapeThreads;
+        ctas_per_sm = kSmallShapeCtas;
+        max_cells = kSmallShapeCells;
+        for (int32_t q = 0; q < nq && all.mid_hist > 0; ++q) {
+            if (p->strategy[q] != kHist || S.cells[q] <= max_cells) continue;
+            --all.mid_hist;
+            --all.n[kHist];
+            QHead &h = qh[q];
+            QVar *qq = qv + h.var_off;
+            const QPlan ch = choose(c, qq, h.k, S.cells[q], max_cells, win_cells, chunks_d);
+            const int s = ch.strategy;
+            const int32_t nwin = s == kWindow ? (int32_t)((S.cells[q] + win_cells - 1) / win_cells) : 1;
+            h.strategy = (int16_t)s;
+            h.nparts = (int16_t)nwin;
+            h.nwin = nwin;
+            p->strategy[q] = s;
+            S.cost[q] = ch.cost;
+            const uint32_t cl = cost_class(ch.cost / nwin);
+            S.cls[q] = cl;
+            S.passes[q] = (uint8_t)((s == kBitmap && o.bitmap_small && h.k == 3 && small_ok(qq, 3)) ? qq[0].arity : 0);
+            ++all.n[s];
+            if (s == kSort) {
+                all.sorts.insert(std::lower_bound(all.sorts.begin(), all.sorts.end(), q), q);
+            } else {
+                const int g = s == kBitmap ? 1 : 0;
+                all.lo[g] = std::min(all.lo[g], cl);
+                all.hi[g] = std::max(all.hi[g], cl);
+                if (s == kBitmap) all.bitmap_cost += ch.cost;
+                if (s == kWindow) all.window_items += nwin;
+            }
+        }
+    }
+    p->threads = threads;
+    p->smem_cells = max_cells;
 
     // table offsets of count plans: the caller's, else dense in query order
     if (score_kind == kNoScore) {
@@ -397,7 +443,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
     }
 
     // work items: split rows when the batch alone cannot fill the GPU
-    p->grid = c->num_sms * std::max(1, o.ctas_per_sm);
+    p->grid = c->num_sms * ctas_per_sm;
     p->smem = (size_t)max_cells * 4;
     const int64_t nchunks = (c->m + kChunkRows - 1) / kChunkRows;
     const int64_t max_parts_rows = std::max<int64_t>(1, c->m / std::max<int64_t>(o.min_part_rows, kChunkRows));
@@ -444,7 +490,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
     // outweigh their work.
     std::vector<BTask> &btasks = S.btasks;
     btasks.clear();
-    p->bm_threads = std::max(32, std::min(1024, o.bitmap_threads / 32 * 32));
+    p->bm_threads = std::max(32, std::min(256, o.bitmap_threads / 32 * 32));  // bitmap_kernel's launch bound
     p->stage_slots = o.stage_slots;
     p->small_paths = o.bitmap_small;
     if (all.n[kBitmap] > 0) {

@@ -33,6 +33,7 @@ const OptDesc kOpts[] = {
     {"window_max", nullptr, &Options::window_max, 0, kMaxWindows},
     {"window_cells", nullptr, &Options::window_cells, 256, 1 << 20},
     {"window_wide", nullptr, &Options::window_wide, 0, 1},
+    {"shape_auto", nullptr, &Options::shape_auto, 0, 1},
     {"bitmap_cost", &Options::bitmap_cost, nullptr, 0, (int64_t)1 << 40},
     {"bitmap_chunk_cost", &Options::bitmap_chunk_cost, nullptr, 0, (int64_t)1 << 40},
     {"hist_cost_row", &Options::hist_cost_row, nullptr, 0, (int64_t)1 << 40},
@@ -41,7 +42,7 @@ const OptDesc kOpts[] = {
     {"small_cost", &Options::small_cost, nullptr, 0, (int64_t)1 << 40},
     {"bitmap_small", nullptr, &Options::bitmap_small, 0, 1},
     {"stage_slots", nullptr, &Options::stage_slots, 1, 64},
-    {"bitmap_threads", nullptr, &Options::bitmap_threads, 32, 1024},
+    {"bitmap_threads", nullptr, &Options::bitmap_threads, 32, 256},
     {"support_warps", nullptr, &Options::support_warps, 1, 32},
     {"support_sets_per_warp", nullptr, &Options::support_sets_per_warp, 1, 64},
     {"support_part_words", &Options::support_part_words, nullptr, 64, (int64_t)1 << 40},
@@ -58,6 +59,8 @@ extern "C" int fc_set_option(fc_ctx *c, const char *key, int64_t value)
                 return fail(FC_ERR_ARG, "option %s must be in %lld..%lld", key, (long long)d.lo, (long long)d.hi);
             if (d.p32 == &Options::strategy && value == FC_STRAT_MARGINAL)
                 return fail(FC_ERR_ARG, "the marginal strategy is chosen by the planner, never forced");
+            if (d.p32 == &Options::threads || d.p32 == &Options::ctas_per_sm || d.p32 == &Options::smem_cells)
+                c->opt.shape_auto = 0;  // an explicit launch shape
             if (d.p64) c->opt.*(d.p64) = value;
             else c->opt.*(d.p32) = (int32_t)value;
             return FC_OK;

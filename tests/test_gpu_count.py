@@ -158,6 +158,32 @@ def test_window_path_cuts_and_row_splits():
         assert abs(got - ref) <= 1e-5 * max(1.0, abs(ref)), (kind, got, ref)
 
 
+def test_launch_shape_follows_table_sizes():
+    """The planner's two launch shapes: small CTAs unless enough tables need
+    more shared memory than they hold; tables beyond the small shape in a
+    batch that takes it are planned again (windows or bitmaps)."""
+    db = random_dag_database(12, 40_009, 5, 5, 3, 1.0, seed=29)
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    rng = np.random.default_rng(30)
+    big = [[int(x) for x in rng.choice(db.n, size=6, replace=False)] for _ in range(40)]   # 15,625 cells
+    small = random_queries(db.n, 4000, 1, 3, seed=31)
+    for queries, big_on_hist in ((big, True), (big + small, False)):
+        off, flat = fc.pack_lists(queries)
+        plan = fc.fc_plan_count(ctx, off, flat)
+        strat = fc.fc_plan_strategies(plan)[:len(big)]
+        fc.fc_plan_free(plan)
+        if big_on_hist:
+            assert (strat != fc.FC_STRAT_WINDOW).all()
+        else:
+            assert (strat != fc.FC_STRAT_HIST).all()
+        sample = big + queries[len(big)::97]
+        want = oracle_tables(orc, sample)
+        tables, toff = fc.fc_count_batch(ctx, off, flat)
+        for i, q in enumerate(list(range(len(big))) + list(range(len(big), len(queries), 97))):
+            assert np.array_equal(tables[toff[q]:toff[q + 1]].astype(np.int64), want[i]), q
+
+
 def test_edge_cases():
     D = np.array([[0, 1, 0, 1, 1], [0, 0, 0, 0, 0], [2, 1, 0, 2, 2]], dtype=np.uint8)
     ar = [2, 1, 3]
@@ -294,7 +320,10 @@ def test_plan_graph_replay_on_stream_is_deterministic():
     for q, w in enumerate(want):
         assert np.array_equal(results[0][toff[q]:toff[q + 1]].astype(np.int64), w)
     strat = fc.fc_plan_strategies(plan)
-    assert set(np.unique(strat)) <= {fc.FC_STRAT_BITMAP, fc.FC_STRAT_HIST}
+    assert set(np.unique(strat)) <= {fc.FC_STRAT_BITMAP, fc.FC_STRAT_HIST, fc.FC_STRAT_WINDOW}
+    # windows only for tables beyond the shared-memory table area of the launch
+    cells = np.array([int(np.prod([db.arities[v] for v in q])) for q in queries])
+    assert (cells[strat == fc.FC_STRAT_WINDOW] > 8192).all()
 
 
 def test_bounded_wait_reports_timeout_and_context_survives():
