@@ -122,6 +122,7 @@ struct PlanScratch {
     std::vector<int32_t> cells;     // table cells of each query
     std::vector<uint32_t> cls;      // cost class of each query (descending order)
     std::vector<uint8_t> passes;    // bitmap queries: first-variable passes (0 = none)
+    std::vector<uint8_t> mixed_win; // windowed queries counted in the mixed launch
     std::vector<int32_t> order, start, qlist;
     std::vector<BTask> btasks;
     size_t rest_bytes = 0;          // staging bytes past the QVars in the last plan

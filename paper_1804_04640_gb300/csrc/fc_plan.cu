@@ -288,7 +288,8 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
         int fail_code = 0;
         std::string fail_msg;
         int64_t n[6] = {0, 0, 0, 0, 0, 0};  // queries per strategy
-        int64_t window_items = 0;             // windows over all windowed queries
+        int64_t window_items = 0;             // windows of the wide launch's queries
+        int64_t mixed_windows = 0;            // windows counted in the mixed launch
         int64_t mid_hist = 0;                 // shared-memory tables beyond the small launch shape
         double bitmap_cost = 0.0;
         uint32_t lo[2] = {UINT32_MAX, UINT32_MAX}, hi[2] = {0, 0};  // class spans: [0] items, [1] bitmap
@@ -389,20 +390,22 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
 
     // launch shape: the small one unless more than 1/64 of the queries are
     // shared-memory tables that it cannot hold; those few are planned again
-    // with its table area
-    if (auto_shape && all.mid_hist * 64 <= nq) {
+    // with its table area (as windows of it they stay in the mixed launch)
+    const bool small_shape = auto_shape && all.mid_hist * 64 <= nq;
+    if (small_shape) {
         threads = kSmallShapeThreads;
         ctas_per_sm = kSmallShapeCtas;
         max_cells = kSmallShapeCells;
+        if (all.mid_hist > 0) S.mixed_win.assign(nq, 0);
         for (int32_t q = 0; q < nq && all.mid_hist > 0; ++q) {
             if (p->strategy[q] != kHist || S.cells[q] <= max_cells) continue;
             --all.mid_hist;
             --all.n[kHist];
             QHead &h = qh[q];
             QVar *qq = qv + h.var_off;
-            const QPlan ch = choose(c, qq, h.k, S.cells[q], max_cells, win_cells, chunks_d);
+            const QPlan ch = choose(c, qq, h.k, S.cells[q], max_cells, max_cells, chunks_d);
             const int s = ch.strategy;
-            const int32_t nwin = s == kWindow ? (int32_t)((S.cells[q] + win_cells - 1) / win_cells) : 1;
+            const int32_t nwin = s == kWindow ? (int32_t)((S.cells[q] + max_cells - 1) / max_cells) : 1;
             h.strategy = (int16_t)s;
             h.nparts = (int16_t)nwin;
             h.nwin = nwin;
@@ -419,10 +422,14 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
                 all.lo[g] = std::min(all.lo[g], cl);
                 all.hi[g] = std::max(all.hi[g], cl);
                 if (s == kBitmap) all.bitmap_cost += ch.cost;
-                if (s == kWindow) all.window_items += nwin;
+                if (s == kWindow) {
+                    all.mixed_windows += nwin;
+                    S.mixed_win[q] = 1;
+                }
             }
         }
     }
+    auto mixed_window = [&](int32_t q) { return all.mixed_windows > 0 && S.mixed_win[q]; };
     p->threads = threads;
     p->smem_cells = max_cells;
 
@@ -471,14 +478,14 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
             const int s = p->strategy[q];
             if (s == kHist || s == kGAtomic) {
                 qh[q].nparts = (int16_t)parts;
-            } else if (s == kWindow) {
+            } else if (s == kWindow && !mixed_window(q)) {
                 const int32_t nwin = qh[q].nwin;
                 qh[q].nparts = (int16_t)(std::max<int64_t>(1, std::min<int64_t>(wparts, 32767 / nwin)) * nwin);
                 window_parts += qh[q].nparts;
             }
         }
     }
-    const int64_t n_narrow = persistent * parts + all.n[kMarginal] + (wide ? 0 : window_parts);
+    const int64_t n_narrow = persistent * parts + all.n[kMarginal] + all.mixed_windows + (wide ? 0 : window_parts);
     p->n_items = (int32_t)n_narrow;
     p->n_witems = (int32_t)(wide ? window_parts : 0);
 
@@ -586,7 +593,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
         for (const int32_t q : order) {
             const int s = p->strategy[q];
             const int32_t np = s == kMarginal ? 1 : s == kWindow ? qh[q].nparts : (int32_t)parts;
-            Item *&dst = wide && s == kWindow ? wit : it;
+            Item *&dst = wide && s == kWindow && !mixed_window(q) ? wit : it;
             for (int32_t part = 0; part < np; ++part) *dst++ = Item{q, part};
         }
     }
