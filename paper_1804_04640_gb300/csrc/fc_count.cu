@@ -835,9 +835,85 @@ __device__ __forceinline__ void key_rows_window(const CountParams &P, const QVar
     }
 }
 
+// Windowed keys with variables combined in pairs: when r_t r_{t+1} <= 256 the
+// pair's joint state s_t r_{t+1} + s_{t+1} fits a byte, so one multiply-add
+// per 32-bit word forms it for four rows at once (no carries between bytes)
+// and the pair costs one byte extraction per row instead of two.  The pair
+// is a digit of the key with the second variable's stride.  Digit d is
+// dg[d] = (first variable, second variable, second's arity or 0 when the
+// digit has one variable, stride), in shared memory.
+template <int D>
+__device__ __forceinline__ void key_rows_window_digits(const CountParams &P, const int4 *dg, int64_t r0,
+                                                       int64_t r1, uint32_t w0, uint32_t wlen, int32_t *win)
+{
+    const int64_t ngroups = (r1 - r0) >> 4;
+    for (int64_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
+        uint32_t key[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) key[j] = 0u - w0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int4 q = dg[d];
+            uint4 x = __ldg(reinterpret_cast<const uint4 *>(P.D + (int64_t)q.x * P.m_pad + r0) + g);
+            const uint32_t mul = (uint32_t)q.z;
+            if (mul) {
+                const uint4 y = __ldg(reinterpret_cast<const uint4 *>(P.D + (int64_t)q.y * P.m_pad + r0) + g);
+                x.x = x.x * mul + y.x;
+                x.y = x.y * mul + y.y;
+                x.z = x.z * mul + y.z;
+                x.w = x.w * mul + y.w;
+            }
+            const uint32_t st = (uint32_t)q.w;
+            const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) key[4 * i + j] += ((w[i] >> (8 * j)) & 0xffu) * st;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (key[j] < wlen) atomicAdd(&win[key[j]], 1);
+    }
+    for (int64_t p = r0 + (ngroups << 4) + threadIdx.x; p < r1; p += blockDim.x) {
+        uint32_t key = 0u - w0;
+        for (int d = 0; d < D; ++d) {
+            const int4 q = dg[d];
+            uint32_t x = P.D[(int64_t)q.x * P.m_pad + p];
+            if (q.z) x = x * (uint32_t)q.z + P.D[(int64_t)q.y * P.m_pad + p];
+            key += x * (uint32_t)q.w;
+        }
+        if (key < wlen) atomicAdd(&win[key], 1);
+    }
+}
+
+template <bool kDigits>
 __device__ __forceinline__ void key_rows_window_dispatch(const CountParams &P, const QVar *vs, int k, int64_t r0,
                                                          int64_t r1, uint32_t w0, uint32_t wlen, int32_t *win)
 {
+    // digits after pairing neighbours whose joint state fits a byte (every
+    // thread derives the same count; thread 0 writes the table)
+    __shared__ int4 s_dig[kMaxK];
+    int digits = k;
+    if constexpr (kDigits)
+        for (int t = digits = 0; t < k; ++digits) t += (t + 1 < k && vs[t].arity * vs[t + 1].arity <= 256) ? 2 : 1;
+    if (kDigits && k <= 6 && digits < k) {
+        if (threadIdx.x == 0) {
+            for (int t = 0, d = 0; t < k; ++d) {
+                const bool pair = t + 1 < k && vs[t].arity * vs[t + 1].arity <= 256;
+                s_dig[d] = make_int4(vs[t].var, pair ? vs[t + 1].var : 0, pair ? vs[t + 1].arity : 0,
+                                     vs[pair ? t + 1 : t].stride);
+                t += pair ? 2 : 1;
+            }
+        }
+        __syncthreads();
+        switch (digits) {
+        case 1: key_rows_window_digits<1>(P, s_dig, r0, r1, w0, wlen, win); return;
+        case 2: key_rows_window_digits<2>(P, s_dig, r0, r1, w0, wlen, win); return;
+        case 3: key_rows_window_digits<3>(P, s_dig, r0, r1, w0, wlen, win); return;
+        case 4: key_rows_window_digits<4>(P, s_dig, r0, r1, w0, wlen, win); return;
+        default: key_rows_window_digits<5>(P, s_dig, r0, r1, w0, wlen, win); return;
+        }
+    }
     switch (k) {
     case 2: key_rows_window<2>(P, vs, k, r0, r1, w0, wlen, win); break;
     case 3: key_rows_window<3>(P, vs, k, r0, r1, w0, wlen, win); break;
@@ -849,10 +925,13 @@ __device__ __forceinline__ void key_rows_window_dispatch(const CountParams &P, c
 }
 
 // kThreads x kBlocks: 512 x 2 for the mixed launch; 1024 x 1 for windowed
-// tables, whose window then takes the whole shared memory of an SM.
+// tables, whose window then takes the whole shared memory of an SM (and
+// whose keys pair variables into byte digits, a path kept out of the mixed
+// launch's register allocation).
 template <int kThreads, int kBlocks>
 __global__ void __launch_bounds__(kThreads, kBlocks) count_kernel(const CountParams P)
 {
+    constexpr bool kWide = kThreads == 1024;
     extern __shared__ __align__(16) int32_t smem_tab[];
     __shared__ QVar s_vars[kMaxK];
     __shared__ int s_item;
@@ -916,13 +995,14 @@ __global__ void __launch_bounds__(kThreads, kBlocks) count_kernel(const CountPar
             for (int s = threadIdx.x; s < v.arity; s += blockDim.x)
                 smem_tab[s * v.stride] = (int32_t)P.marg[v.soff + s];
         } else if (windowed) {
-            key_rows_window_dispatch(P, s_vars, k, r0, r1, w0, wlen, smem_tab);
-        } else if (lshift >= 0) {
-            key_rows_swar_dispatch(P, s_vars, k, r0, r1, lshift, smem_tab);
-        } else if (in_smem) {
-            key_rows_swar(P, s_vars, k, r0, r1, smem_tab + (warp % copies) * h.cells);
-        } else {
-            key_rows_global(P, s_vars, k, r0, r1, P.tables + h.table_off);
+            key_rows_window_dispatch<kWide>(P, s_vars, k, r0, r1, w0, wlen, smem_tab);
+        } else if constexpr (!kWide) {  // the wide launch holds windows only
+            if (lshift >= 0)
+                key_rows_swar_dispatch(P, s_vars, k, r0, r1, lshift, smem_tab);
+            else if (in_smem)
+                key_rows_swar(P, s_vars, k, r0, r1, smem_tab + (warp % copies) * h.cells);
+            else
+                key_rows_global(P, s_vars, k, r0, r1, P.tables + h.table_off);
         }
         __syncthreads();
 

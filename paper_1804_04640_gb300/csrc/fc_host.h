@@ -93,7 +93,7 @@ struct Options {
     int32_t use_graph = 1;
     int64_t wait_limit = 1 << 22;
     int64_t sort_min_cells = 1 << 25;
-    int32_t window_max = 40;          // AUTO: most shared-memory windows per table
+    int32_t window_max = 16;          // AUTO: most shared-memory windows per table
     int32_t window_cells = 1 << 20;   // cap on the cells of one window
     int32_t window_wide = 1;          // windows in a launch of one 1024-thread CTA per SM
     // cost model, femtoseconds: bitmap per DFS node per 4096-row chunk;

@@ -131,7 +131,7 @@ def test_window_path_cuts_and_row_splits():
     strat = fc.fc_plan_strategies(plan)
     fc.fc_plan_free(plan)
     cells = [int(np.prod([db.arities[v] for v in q])) for q in queries]
-    assert all(s == fc.FC_STRAT_WINDOW for s, n in zip(strat, cells) if 24576 < n <= 40 * 50_000)
+    assert all(s == fc.FC_STRAT_WINDOW for s, n in zip(strat, cells) if 24576 < n <= 16 * 50_000)
     check_batch(ctx, orc, queries, want)
     fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_WINDOW)
     for wide in (1, 0):                                # own launch / inside the mixed launch
