@@ -298,6 +298,7 @@ extern "C" void fc_free(fc_ctx *c)
     for (cudaEvent_t ev : c->half_done)
         if (ev) cudaEventDestroy(ev);
     for (auto &b : c->io) b.release();
+    c->marg_delta.release();
     for (auto &b : c->pipe_io) b.release();
     for (auto &bank : c->pool)
         for (auto &b : bank) b.release();
@@ -373,15 +374,20 @@ int grow_storage(fc_ctx *c, int64_t m_need)
 }
 
 // New instance count, marginals and entropies after an append.
-int finish_append(fc_ctx *c, int64_t m_total)
+// New instance count, generation and entropies after an append; the host
+// copy of the marginals is read back from the device unless the caller has
+// already brought it up to date.
+int finish_append(fc_ctx *c, int64_t m_total, bool read_marginals = true)
 {
     c->m = m_total;
     c->words = (m_total + 63) / 64;
     c->generation += 1;
-    cudaError_t e = cudaMemcpyAsync(c->marg.data(), c->d_marg, sizeof(int64_t) * c->R, cudaMemcpyDeviceToHost,
-                                    c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "append marginals");
+    if (read_marginals) {
+        cudaError_t e = cudaMemcpyAsync(c->marg.data(), c->d_marg, sizeof(int64_t) * c->R,
+                                        cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "append marginals");
+    }
     if (!c->transactions)
         for (int i = 0; i < c->n; ++i) {
             double h = 0.0;
@@ -428,15 +434,23 @@ extern "C" int fc_append(fc_ctx *c, const uint8_t *D, int64_t m_new, int32_t lay
         if (e == cudaSuccess)
             e = launch_transpose_rows((const uint8_t *)c->io[2].p, m_new, c->n, c->d_D + m0, c->m_pad, c->stream);
     }
-    // The repack of the bitmap words from m0 / 64 on also checks the states.
-    // A bad state appends nothing: the new rows of D are zeroed and the same
-    // words repacked over the old rows alone, before m or the marginals move.
+    // The repack of the bitmap words from m0 / 64 on also checks the states
+    // and counts the new instances per state.  A bad state appends nothing:
+    // the new rows of D are zeroed and the same words repacked over the old
+    // rows alone, before m or the marginals move.
     int32_t *bad = c->d_status + 1;
     int32_t bad_h = 0;
+    c->h_marg_delta.assign(c->R, 0);
+    if (e == cudaSuccess) e = c->marg_delta.ensure(sizeof(int64_t) * c->R);
+    int64_t *delta = (int64_t *)c->marg_delta.p;
+    if (e == cudaSuccess) e = cudaMemsetAsync(delta, 0, sizeof(int64_t) * c->R, c->stream);
     if (e == cudaSuccess)
         e = launch_pack_bits(c->d_D, c->m_pad, m1, c->n, c->d_arity, c->d_soff, c->d_bits, c->wstride, 255, bad,
-                             c->stream, m0 / 64);
+                             c->stream, m0 / 64, delta, (int)(m0 % 64));
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_h, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->h_marg_delta.data(), delta, sizeof(int64_t) * c->R, cudaMemcpyDeviceToHost,
+                            c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "fc_append");
     if (bad_h) {
@@ -453,9 +467,10 @@ extern "C" int fc_append(fc_ctx *c, const uint8_t *D, int64_t m_new, int32_t lay
         cudaStreamSynchronize(c->stream);
         return fail(FC_ERR_RANGE, "fc_append: a state is >= its variable's arity; nothing was appended");
     }
-    e = launch_bit_popcounts_range(c->d_bits, c->R, c->wstride, m0, m1, c->d_marg, c->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "fc_append bitmaps");
-    return finish_append(c, m1);
+    for (int r = 0; r < c->R; ++r) c->marg[r] += c->h_marg_delta[r];
+    e = cudaMemcpyAsync(c->d_marg, c->marg.data(), sizeof(int64_t) * c->R, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fc_append marginals");
+    return finish_append(c, m1, false);
 }
 
 extern "C" int fc_append_bits(fc_ctx *c, const uint64_t *bitmaps, int64_t m_new, int32_t where)

@@ -211,6 +211,8 @@ struct fc_ctx {
     fc::Options opt;
     // scratch of the host-buffer entry points
     fc::DBuf io[3];
+    fc::DBuf marg_delta;     // marginal counts of the instances an append adds (R int64)
+    std::vector<int64_t> h_marg_delta;
     // buffers lent to one-shot plans (descriptors, counters, tables, sort,
     // pairs), in two banks so that a synchronous call can have a plan
     // running while it builds the next; `bank` selects the one in use

@@ -93,15 +93,15 @@ struct CountParams {
 
 // Launchers (each defined in the translation unit holding its kernel).
 // Bitmap words [first_word, ceil(m / 64)) of every (variable, state) row,
-// from the column-major D.
+// from the column-major D.  With delta set, delta[row] += the set bits of the
+// packed words at positions >= 64 first_word + first_from (the marginal
+// counts of appended instances, Sec. 6: a growing database updates the
+// bitmaps in place).
 cudaError_t launch_pack_bits(const uint8_t *D, int64_t m_pad, int64_t m, int32_t n,
                              const int32_t *d_arity, const int32_t *d_soff, uint64_t *bits,
                              int64_t wstride, int32_t max_arity, int32_t *bad_state,
-                             cudaStream_t s, int64_t first_word = 0);
-// Appends (Sec. 6: a growing database updates the bitmaps in place).
-// marg[r] += set bits of bitmap row r at positions [m_old, m_new_total).
-cudaError_t launch_bit_popcounts_range(const uint64_t *bits, int64_t rows, int64_t wstride, int64_t m_old,
-                                       int64_t m_new_total, int64_t *marg, cudaStream_t s);
+                             cudaStream_t s, int64_t first_word = 0, int64_t *delta = nullptr,
+                             int first_from = 0);
 cudaError_t launch_append_bits(uint64_t *bits, int64_t wstride, int32_t n_items, int64_t m_old,
                                const uint64_t *nb, int64_t n_in, int64_t m_new, int64_t *marg, cudaStream_t s);
 cudaError_t launch_bit_popcounts(const uint64_t *bits, int64_t rows, int64_t wstride,

@@ -11,17 +11,28 @@ namespace {
 
 // One warp packs 32 consecutive words (2,048 instances) of one variable.  The
 // warp first copies those 2 KiB of the column to shared memory with 16-byte
-// loads.  In step j it reads instances 64 (w0 + j) + lane and + 32, and for
-// every state s the two ballots over (D_i[p] == s) form word w0 + j of bitmap
-// (i, s); lane j keeps that word, so after the 32 steps lane l holds word
-// w0 + l of every state and the stores are coalesced.  States are taken 16 at
-// a time (a register per state and lane).  A state >= r_i sets *bad_state;
-// such an instance sets no bit.  The copy starts 64-byte aligned (m_pad is a
-// multiple of 4096) and reads only vectors that start before m.
+// loads.  In step j it reads instances 64 (w0 + j) + lane and + 32; ballots
+// over them form word w0 + j, which lane j keeps, so after the 32 steps lane
+// l holds word w0 + l and the stores are coalesced.
+//
+// Variables of at most 16 states are packed through bit planes: the ballots
+// take bit k of each state (k < ceil(log2 r)), and each lane then forms every
+// state's word as the AND of its planes or their complements, masked to the
+// instances below m.  Larger arities take two ballots per state and step
+// (states 16 at a time, a register per state and lane).
+//
+// A state >= r_i sets *bad_state (the caller then discards what was packed).
+// With `delta` set, the bits of each state's words, except the `first_from`
+// lowest bits of word first_word (instances that were there before), are
+// added to delta[state]: the marginal counts of the packed instances.  The
+// copy starts 64-byte aligned (m_pad is a multiple of 4096) and reads only
+// vectors that start before m.
 constexpr int kPackWarps = 8;
+constexpr int kPlaneMaxArity = 16;
 __global__ void __launch_bounds__(kPackWarps * 32) pack_bits_kernel(
     const uint8_t *__restrict__ D, int64_t m_pad, int64_t m, int64_t w0, const int32_t *__restrict__ arity,
-    const int32_t *__restrict__ soff, uint64_t *__restrict__ bits, int64_t wstride, int32_t *bad_state)
+    const int32_t *__restrict__ soff, uint64_t *__restrict__ bits, int64_t wstride, int32_t *bad_state,
+    unsigned long long *delta, int first_from)
 {
     __shared__ __align__(16) uint8_t s_rows[kPackWarps][2048];
     const int i = blockIdx.y;
@@ -43,30 +54,84 @@ __global__ void __launch_bounds__(kPackWarps * 32) pack_bits_kernel(
             if (wb * 64 + 16 * (lane + 32 * k) < m) dst[lane + 32 * k] = __ldg(src + lane + 32 * k);
     }
     __syncwarp();
-    uint64_t *row = bits + (int64_t)soff[i] * wstride + wb + lane;
-    const bool mine = wb + lane < words;
+    const int64_t my = wb + lane;  // the word this lane stores
+    uint64_t *row = bits + (int64_t)soff[i] * wstride + my;
+    const bool mine = my < words;
+    // instances of my word that exist (below m) and that are counted in delta
+    const int64_t left = m - 64 * my;
+    const uint64_t valid = left >= 64 ? ~0ull : left > 0 ? (~0ull >> (64 - left)) : 0ull;
+    const uint64_t counted = valid & ((my == w0 && first_from > 0) ? (~0ull << first_from) : ~0ull);
+    auto emit = [&](int st, uint64_t w) {
+        if (mine) row[(int64_t)st * wstride] = w;
+        if (delta) {
+            unsigned long long c = mine ? (unsigned long long)__popcll(w & counted) : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (lane == 0 && c) atomicAdd(delta + soff[i] + st, c);
+        }
+    };
     bool bad = false;
-    for (int s0 = 0; s0 < r; s0 += 16) {
-        uint64_t word[16];
+    if (r <= kPlaneMaxArity) {
+        const int nb = r > 1 ? 32 - __clz(r - 1) : 1;  // bit planes of a state
+        uint32_t plo[4] = {0u, 0u, 0u, 0u}, phi[4] = {0u, 0u, 0u, 0u};
+        int top = 0;  // the largest state seen
+        // step j: the ballots of bit k over instances 64 (wb + j) + lane and
+        // + 32 are plane k of word wb + j; lane j keeps them
+        auto step = [&](int j, int b0, int b1) {
+            top = max(top, max(b0, b1));
 #pragma unroll
-        for (int t = 0; t < 16; ++t) word[t] = 0ull;
-        for (int j = 0; j < 32 && wb + j < words; ++j) {
-            const int64_t p0 = (wb + j) * 64 + lane, p1 = p0 + 32;
-            const int b0 = p0 < m ? (int)buf[j * 64 + lane] : -1;
-            const int b1 = p1 < m ? (int)buf[j * 64 + 32 + lane] : -1;
-            if (s0 == 0) bad |= (b0 >= r) | (b1 >= r);
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                if (s0 + t >= r) break;
-                const unsigned lo = __ballot_sync(0xffffffffu, b0 == s0 + t);
-                const unsigned hi = __ballot_sync(0xffffffffu, b1 == s0 + t);
-                if (lane == j) word[t] = ((uint64_t)hi << 32) | lo;
+            for (int k = 0; k < 4; ++k) {
+                if (k >= nb) break;
+                const unsigned lo = __ballot_sync(0xffffffffu, b0 & (1 << k));
+                const unsigned hi = __ballot_sync(0xffffffffu, b1 & (1 << k));
+                if (lane == j) {
+                    plo[k] = lo;
+                    phi[k] = hi;
+                }
+            }
+        };
+        if ((wb + 32) * 64 <= m) {
+            // every instance of the warp's 32 words exists
+#pragma unroll 4
+            for (int j = 0; j < 32; ++j) step(j, buf[j * 64 + lane], buf[j * 64 + 32 + lane]);
+        } else {
+            for (int j = 0; j < 32 && wb + j < words; ++j) {
+                const int64_t p0 = (wb + j) * 64 + lane, p1 = p0 + 32;
+                step(j, p0 < m ? (int)buf[j * 64 + lane] : 0, p1 < m ? (int)buf[j * 64 + 32 + lane] : 0);
             }
         }
-        if (mine) {
+        bad = top >= r;
+        uint64_t plane[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) plane[k] = ((uint64_t)phi[k] << 32) | plo[k];
+        for (int st = 0; st < r; ++st) {
+            uint64_t w = valid;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < nb) w &= ((st >> k) & 1) ? plane[k] : ~plane[k];
+            emit(st, w);
+        }
+    } else {
+        for (int s0 = 0; s0 < r; s0 += 16) {
+            uint64_t word[16];
+#pragma unroll
+            for (int t = 0; t < 16; ++t) word[t] = 0ull;
+            for (int j = 0; j < 32 && wb + j < words; ++j) {
+                const int64_t p0 = (wb + j) * 64 + lane, p1 = p0 + 32;
+                const int b0 = p0 < m ? (int)buf[j * 64 + lane] : -1;
+                const int b1 = p1 < m ? (int)buf[j * 64 + 32 + lane] : -1;
+                if (s0 == 0) bad |= (b0 >= r) | (b1 >= r);
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    if (s0 + t >= r) break;
+                    const unsigned lo = __ballot_sync(0xffffffffu, b0 == s0 + t);
+                    const unsigned hi = __ballot_sync(0xffffffffu, b1 == s0 + t);
+                    if (lane == j) word[t] = ((uint64_t)hi << 32) | lo;
+                }
+            }
 #pragma unroll
             for (int t = 0; t < 16; ++t)
-                if (s0 + t < r) row[(int64_t)(s0 + t) * wstride] = word[t];
+                if (s0 + t < r) emit(s0 + t, word[t]);
         }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(bad_state, 1);
@@ -136,28 +201,6 @@ __global__ void assignment_count_kernel(const uint64_t *__restrict__ bits, int64
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
-// Marginal counts of appended instances from the repacked bitmaps: block r
-// adds to marg[r] the set bits of row r in words [w0, w1), ignoring the bits
-// below position `from` of word w0 (instances that were there before).
-__global__ void bit_popcount_range_kernel(const uint64_t *__restrict__ bits, int64_t wstride, int64_t w0,
-                                          int64_t w1, int from, unsigned long long *marg)
-{
-    const uint64_t *row = bits + (int64_t)blockIdx.x * wstride;
-    const uint64_t first_mask = (~0ull) << from;
-    unsigned long long c = 0;
-    for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x)
-        c += __popcll(w == w0 ? (row[w] & first_mask) : row[w]);
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    __shared__ unsigned long long part[32];
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += part[j];
-        if (t) atomicAdd(marg + blockIdx.x, t);
-    }
-}
-
 // Transactions [m_old, m_old + m_new) of each item (blockIdx.y strides over
 // the items) from `nb` (n_in
 // words per item, bit p of word j = new transaction 64 j + p) merged into the
@@ -205,14 +248,15 @@ __global__ void append_bits_kernel(uint64_t *__restrict__ bits, int64_t wstride,
 cudaError_t launch_pack_bits(const uint8_t *D, int64_t m_pad, int64_t m, int32_t n,
                              const int32_t *d_arity, const int32_t *d_soff, uint64_t *bits,
                              int64_t wstride, int32_t /*max_arity*/, int32_t *bad_state,
-                             cudaStream_t s, int64_t first_word)
+                             cudaStream_t s, int64_t first_word, int64_t *delta, int first_from)
 {
     const int64_t words = (m + 63) / 64 - first_word;
     if (words <= 0) return cudaSuccess;
     const int64_t groups = (words + 31) / 32;  // 32 words per warp
     dim3 grid((unsigned)((groups + kPackWarps - 1) / kPackWarps), (unsigned)n);
     pack_bits_kernel<<<grid, kPackWarps * 32, 0, s>>>(D, m_pad, m, first_word, d_arity, d_soff, bits, wstride,
-                                                 bad_state);
+                                                 bad_state, reinterpret_cast<unsigned long long *>(delta),
+                                                 first_from);
     return cudaGetLastError();
 }
 
@@ -224,16 +268,6 @@ unsigned append_grid(int64_t units, int threads)
 }
 unsigned append_rows(int32_t n) { return (unsigned)std::max(1, std::min(n, 65535)); }
 }  // namespace
-
-cudaError_t launch_bit_popcounts_range(const uint64_t *bits, int64_t rows, int64_t wstride, int64_t m_old,
-                                       int64_t m_new_total, int64_t *marg, cudaStream_t s)
-{
-    const int64_t w0 = m_old >> 6, w1 = (m_new_total + 63) >> 6;
-    if (rows <= 0 || w1 <= w0) return cudaSuccess;
-    bit_popcount_range_kernel<<<(unsigned)rows, 256, 0, s>>>(bits, wstride, w0, w1, (int)(m_old & 63),
-                                                            reinterpret_cast<unsigned long long *>(marg));
-    return cudaGetLastError();
-}
 
 cudaError_t launch_append_bits(uint64_t *bits, int64_t wstride, int32_t n_items, int64_t m_old,
                                const uint64_t *nb, int64_t n_in, int64_t m_new, int64_t *marg, cudaStream_t s)
