@@ -1090,7 +1090,7 @@ struct FamilyRows {
     __device__ __forceinline__ int64_t step() const { return cstep; }
 };
 
-// One block per family (child, parents): the score of the child given the
+// One warp per family (child, parents): the score of the child given the
 // other variables of a joint table counted once for the whole variable set
 // (Sec. 4.2: every family of the parent-set lattice is a (child, rest) split
 // of some variable set).
