@@ -383,7 +383,13 @@ int fc_sync(fc_ctx *ctx, void *stream);
 /* ------------------------------------------------------- options, errors */
 
 /* Set a tuning option; returns FC_ERR_ARG for an unknown key or bad value.
- *   "strategy"          FC_STRAT_* forced for every query (default AUTO)
+ *   "strategy"          FC_STRAT_* forced for every query (default AUTO;
+ *                       FC_STRAT_MARGINAL cannot be forced)
+ *   "shape_auto"        1 = the planner picks the count kernel's launch shape
+ *                       per batch (default): 256 threads x 8192-cell tables,
+ *                       or the three options below when more than 1/64 of the
+ *                       batch are shared-memory tables beyond 8192 cells.
+ *                       Setting any of the three sets it to 0.
  *   "smem_cells"        int32 cells of the shared-memory table area per CTA
  *   "threads"           threads per CTA of the count kernel (multiple of 32, <= 512)
  *   "ctas_per_sm"       resident CTAs per SM the count kernel is sized for
@@ -399,8 +405,15 @@ int fc_sync(fc_ctx *ctx, void *stream);
  *                       the shared memory of an SM holds)
  *   "window_wide"       1 = windows run in their own launch of one 1024-thread
  *                       CTA per SM (default), 0 = inside the mixed launch
- *   "bitmap_cost", "hist_cost_row", "hist_cost_var", "flush_cost"
- *                       cost-model coefficients (x1000) used by AUTO. */
+ *   "bitmap_threads"    threads per CTA of the bitmap kernel (<= 256)
+ *   "stage_slots"       bitmap rows a warp of the bitmap kernel stages per chunk
+ *   "bitmap_small"      1 = register-blocked bitmap path for 2-3 small variables
+ *   "sort_min_cells"    tables at least this large take the sort strategy
+ *   "bitmap_cost", "bitmap_chunk_cost", "small_cost", "hist_cost_row",
+ *   "hist_cost_var", "flush_cost"
+ *                       cost-model coefficients (femtoseconds) used by AUTO
+ *   "support_warps", "support_sets_per_warp", "support_part_words"
+ *                       launch shape of the itemset-support kernels. */
 int fc_set_option(fc_ctx *ctx, const char *key, int64_t value);
 
 /* Current value of an option (or -1 for an unknown key). */

@@ -118,6 +118,15 @@ double small_units(const QVar *o, int k)
     return (double)o[0].arity * (1.0 + rb + rc + rb * rc);
 }
 
+// Threads per CTA of the bitmap kernel (its launch bound is 256) and the
+// state rows a warp stages per chunk (16 bytes per row and thread, within one
+// CTA's shared memory).
+int bitmap_threads(const fc_ctx *c) { return std::max(32, std::min(256, c->opt.bitmap_threads / 32 * 32)); }
+int stage_slots(const fc_ctx *c)
+{
+    return std::max(1, std::min(c->opt.stage_slots, (c->max_smem_optin - 1024) / (16 * bitmap_threads(c))));
+}
+
 bool bitmap_ok(const fc_ctx *c, const QVar *v, int k, QVar *o)
 {
     if (k < 1 || k > kMaxBitmapK) return false;
@@ -125,7 +134,7 @@ bool bitmap_ok(const fc_ctx *c, const QVar *v, int k, QVar *o)
     entropy_order(c, o, k);
     int slots = 0;
     for (int t = 1; t < k; ++t) slots += o[t].arity;
-    return slots <= c->opt.stage_slots;
+    return slots <= stage_slots(c);
 }
 
 // Strategy and cost of one query.  When the bitmap strategy is chosen, the
@@ -497,8 +506,8 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
     // outweigh their work.
     std::vector<BTask> &btasks = S.btasks;
     btasks.clear();
-    p->bm_threads = std::max(32, std::min(256, o.bitmap_threads / 32 * 32));  // bitmap_kernel's launch bound
-    p->stage_slots = o.stage_slots;
+    p->bm_threads = bitmap_threads(c);
+    p->stage_slots = stage_slots(c);
     p->small_paths = o.bitmap_small;
     if (all.n[kBitmap] > 0) {
         constexpr int64_t kMinTaskChunks = 4;
