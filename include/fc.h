@@ -388,8 +388,10 @@ int fc_sync(fc_ctx *ctx, void *stream);
  *   "shape_auto"        1 = the planner picks the count kernel's launch shape
  *                       per batch (default): 256 threads x 8192-cell tables,
  *                       or the three options below when more than 1/64 of the
- *                       batch are shared-memory tables beyond 8192 cells.
- *                       Setting any of the three sets it to 0.
+ *                       batch are shared-memory tables beyond 8192 cells or
+ *                       when, with m >= 2^19, most histogram work is on tables
+ *                       of 256 cells or more.  Setting any of the three sets
+ *                       it to 0.
  *   "smem_cells"        int32 cells of the shared-memory table area per CTA
  *   "threads"           threads per CTA of the count kernel (multiple of 32, <= 512)
  *   "ctas_per_sm"       resident CTAs per SM the count kernel is sized for

@@ -81,9 +81,9 @@ struct DBuf {
 struct Options {
     int32_t strategy = FC_STRAT_AUTO;
     // launch shape of the mixed count launch; with shape_auto the planner
-    // takes 256 threads x 6 CTAs x 8192 cells per SM unless the batch has
-    // enough shared-memory tables between 8192 and smem_cells cells
-    int32_t smem_cells = 24576;       // 96 KiB of tables per CTA
+    // takes 256 threads x 6 CTAs x 8192 cells per SM unless the batch needs
+    // the larger table area below (its rule is in the planner)
+    int32_t smem_cells = 16384;       // 64 KiB of tables per CTA
     int32_t threads = 512;
     int32_t ctas_per_sm = 2;
     int32_t shape_auto = 1;           // cleared by setting any of the three above

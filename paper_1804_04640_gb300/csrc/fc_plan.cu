@@ -300,6 +300,7 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
         int64_t window_items = 0;             // windows of the wide launch's queries
         int64_t mixed_windows = 0;            // windows counted in the mixed launch
         int64_t mid_hist = 0;                 // shared-memory tables beyond the small launch shape
+        double hist_cost = 0.0, hist_cost_256 = 0.0;  // histogram work, and that on tables of >= 256 cells
         double bitmap_cost = 0.0;
         uint32_t lo[2] = {UINT32_MAX, UINT32_MAX}, hi[2] = {0, 0};  // class spans: [0] items, [1] bitmap
         std::vector<int32_t> sorts;
@@ -361,6 +362,10 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
                 S.passes[q] = (uint8_t)((s == kBitmap && o.bitmap_small && k_eff == 3 && small_ok(qq, 3)) ? qq[0].arity : 0);
                 ++T.n[s];
                 if (s == kHist && cells > kSmallShapeCells) ++T.mid_hist;
+                if (s == kHist) {
+                    T.hist_cost += ch.cost;
+                    if (cells >= 256) T.hist_cost_256 += ch.cost;
+                }
                 if (s == kSort) {
                     T.sorts.push_back(q);
                 } else {
@@ -387,6 +392,8 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
             for (int s = 0; s < 6; ++s) all.n[s] += T.n[s];
             all.window_items += T.window_items;
             all.mid_hist += T.mid_hist;
+            all.hist_cost += T.hist_cost;
+            all.hist_cost_256 += T.hist_cost_256;
             all.bitmap_cost += T.bitmap_cost;
             for (int g = 0; g < 2; ++g) {
                 all.lo[g] = std::min(all.lo[g], T.lo[g]);
@@ -398,9 +405,14 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
     }
 
     // launch shape: the small one unless more than 1/64 of the queries are
-    // shared-memory tables that it cannot hold; those few are planned again
-    // with its table area (as windows of it they stay in the mixed launch)
-    const bool small_shape = auto_shape && all.mid_hist * 64 <= nq;
+    // shared-memory tables that it cannot hold, or long row ranges (items of
+    // >= 2^19 rows, whose per-item fixed costs the small CTAs save little of)
+    // go mostly into tables of >= 256 cells, which get 2-8x more interleaved
+    // copies (less atomic contention) in the large shape's table area.  The
+    // few tables beyond the small shape's area are planned again with it (as
+    // windows of it they stay in the mixed launch).
+    const bool long_rows_big_tables = c->m >= (1 << 19) && all.hist_cost_256 > 0.45 * all.hist_cost;
+    const bool small_shape = auto_shape && all.mid_hist * 64 <= nq && !long_rows_big_tables;
     if (small_shape) {
         threads = kSmallShapeThreads;
         ctas_per_sm = kSmallShapeCtas;
