@@ -604,18 +604,30 @@ int build_count_plan(fc_ctx *c, int32_t nq, Span span, GetVars get, const int64_
     qh = reinterpret_cast<QHead *>(host);
     {
         Item *it = reinterpret_cast<Item *>(host + o_it);
-        Item *wit = it + n_narrow;
+        Item *const it_end = it + n_narrow;
+        Item *wit = it_end;
+        Item *const wit_end = wit + p->n_witems;
         auto item_query = [&](int32_t q) {
             const int s = p->strategy[q];
             return s == kHist || s == kGAtomic || s == kMarginal || s == kWindow;
         };
         std::vector<int32_t> &order = S.order;
         order_by_class(nq, S.cls, all.lo[0], all.hi[0], item_query, order, S.start);
+        bool fits = true;  // the counts taken above size both regions exactly
         for (const int32_t q : order) {
             const int s = p->strategy[q];
             const int32_t np = s == kMarginal ? 1 : s == kWindow ? qh[q].nparts : (int32_t)parts;
-            Item *&dst = wide && s == kWindow && !mixed_window(q) ? wit : it;
+            const bool to_wide = wide && s == kWindow && !mixed_window(q);
+            Item *&dst = to_wide ? wit : it;
+            if (dst + np > (to_wide ? wit_end : it_end)) {
+                fits = false;
+                break;
+            }
             for (int32_t part = 0; part < np; ++part) *dst++ = Item{q, part};
+        }
+        if (!fits || it != it_end || wit != wit_end) {
+            fc_plan_free(p);
+            return fail(FC_ERR_STATE, "planner: work items do not match their count");
         }
     }
     std::memcpy(host + o_ql, qlist.data(), sizeof(int32_t) * qlist.size());
