@@ -75,6 +75,23 @@ def test_append_categorical_matches_single_load(cuts):
     assert np.array_equal(got[2], marg)
 
 
+@pytest.mark.parametrize("arity", [(1, 2), (14, 16), (17, 40)])
+def test_append_marginals_every_pack_path(arity):
+    """Appended marginals come from the pack: bit planes (up to 16 states,
+    arity-1 variables included) and two ballots per state (more states), at
+    cuts inside and at the start of a bitmap word."""
+    db = random_dag_database(7, 150_031, arity[0], arity[1], 2, 0.5, seed=17 + arity[1])
+    D = np.ascontiguousarray(db.D)
+    ctx = fc.fc_load(D[:, :40_001], db.arities)
+    fc.fc_append(ctx, D[:, 40_001:40_064])          # up to a word boundary
+    fc.fc_append(ctx, D[:, 40_064:150_031])
+    marg = np.concatenate([np.bincount(D[v], minlength=int(db.arities[v])) for v in range(db.n)])
+    assert np.array_equal(fc.fc_marginals(ctx), marg)
+    orc = oracle.DB(D, db.arities)
+    for q in ([0], [1, 2], [3, 0, 6]):
+        assert np.array_equal(fc.fc_count(ctx, q).astype(np.int64), orc.table(q)), q
+
+
 def test_append_all_paths_after_growth():
     """Bitmap DFS, histogram, sort, pairs, assignments and rules on a context
     grown past its first allocation, against a single load."""

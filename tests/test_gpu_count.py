@@ -184,6 +184,27 @@ def test_launch_shape_follows_table_sizes():
             assert np.array_equal(tables[toff[q]:toff[q + 1]].astype(np.int64), want[i]), q
 
 
+def test_window_digits_paired_and_single():
+    """Windowed keys with neighbouring variables paired into byte digits
+    (joint arity <= 256), left single (joint arity > 256), and mixed."""
+    db = random_dag_database(8, 90_017, 12, 40, 2, 0.5, seed=37)
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    ar = db.arities
+    small = [v for v in range(db.n) if ar[v] <= 16]
+    big = [v for v in range(db.n) if ar[v] > 16]
+    queries = [list(range(db.n))[:3], list(range(db.n))[3:6], list(range(db.n))[5:8]]
+    if len(small) >= 2 and big:
+        queries += [small[:2] + big[:1], big[:1] + small[:2]]
+    if len(big) >= 3:
+        queries.append(big[:3])
+    want = oracle_tables(orc, queries)
+    fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_WINDOW)
+    for cells_per_window in (1 << 20, 5003):
+        fc.fc_set_option(ctx, "window_cells", cells_per_window)
+        check_batch(ctx, orc, queries, want)
+
+
 def test_edge_cases():
     D = np.array([[0, 1, 0, 1, 1], [0, 0, 0, 0, 0], [2, 1, 0, 2, 2]], dtype=np.uint8)
     ar = [2, 1, 3]
