@@ -88,7 +88,7 @@ struct Options {
     int32_t ctas_per_sm = 2;
     int32_t shape_auto = 1;           // cleared by setting any of the three above
     int32_t hist_copies = 4;
-    int64_t min_part_rows = 65536;
+    int64_t min_part_rows = 8192;
     int64_t pair_chunk_rows = 1 << 16;
     int32_t use_graph = 1;
     int64_t wait_limit = 1 << 22;
