@@ -801,9 +801,9 @@ def run_append_gpu(args, rank, world, fc, torch, barrier, dist, dev):
 
     R = int(db.arities.sum())
     # algorithmic bytes per appended instance: read the new states and write
-    # them behind D (2 n), read them once to check and pack them (n), write
-    # R bits and read them back for the marginals (R / 4)
-    per_row = 3 * db.n + R / 4
+    # them behind D (2 n), read them once to check, pack and count them (n),
+    # write R bits (R / 8)
+    per_row = 3 * db.n + R / 8
     line = None
     if rank == 0:
         cores = os.cpu_count() or 1
@@ -820,10 +820,12 @@ def run_append_gpu(args, rank, world, fc, torch, barrier, dist, dev):
             "config": dict(describe(name, w), l2="flushed between timed steps (256 MiB write)"),
             "e2e": {"value": B / e2e_s, "unit": UNITS[name], "h2d_bytes_per_step": int(db.n * B),
                     "d2h_bytes_per_step": int(8 * R + 4)},
-            "gpu_launches": steps * 3,
+            "gpu_launches": steps,  # the pack; the copy behind D is a driver memcpy
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
-                         "duration": "whole append call (copy, pack with the state check, marginals, host syncs)",
+                         "frac": achieved / hbm, "traffic": measured_traffic(name),
+                         "peak_source": f"{peak_src} hbm_gbs",
+                         "duration": "whole append call (copy, pack with the state check and marginal counts, "
+                                     "host syncs); traffic is the pack's",
                          "note": f"algorithmic {per_row:.0f} B per appended instance"},
             "cpu_baseline": cpu, "clocks": clk.summary(),
         }
