@@ -311,15 +311,17 @@ def _table_offsets(ar, vo, vv) -> np.ndarray:
     if nq == 0:
         return to
     ar = np.asarray(ar, dtype=np.float64)
-    k = np.diff(np.asarray(vo, dtype=np.int64))
+    vo = np.asarray(vo, dtype=np.int64)
+    k = np.diff(vo)
     cells = np.ones(nq, dtype=np.float64)
     nz = k > 0
-    if len(vv):
-        # out-of-range ids count as arity 1 here; the library rejects them
-        ids = np.asarray(vv, dtype=np.int64)
+    if nz.any() and len(vv) >= vo[-1] and (k >= 0).all():
+        # out-of-range ids count as arity 1 here; the library rejects them.
+        # Segments start only at non-empty lists: an empty list's start is
+        # the next list's, and each segment ends where the next one starts.
+        ids = np.asarray(vv, dtype=np.int64)[:vo[-1]]
         ids = np.where((ids >= 0) & (ids < len(ar)), ids, len(ar))
-        prods = np.multiply.reduceat(np.append(ar, 1.0)[ids], np.minimum(vo[:-1], len(vv) - 1))
-        cells[nz] = prods[nz]
+        cells[nz] = np.multiply.reduceat(np.append(ar, 1.0)[ids], vo[:-1][nz])
     # tables past 2^31 cells are refused by the library (FC_ERR_SIZE); clamp
     # them so the offsets stay representable
     to[1:] = np.cumsum(np.minimum(cells, 2.0 ** 40).astype(np.int64))
