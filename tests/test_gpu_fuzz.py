@@ -30,7 +30,7 @@ def _lib():
     fc.load_library(build_if_missing=True)
 
 
-@pytest.mark.parametrize("case", range(24))
+@pytest.mark.parametrize("case", range(64))
 def test_random_planner_configurations(case):
     rng = np.random.default_rng(9000 + case)
     n = int(rng.integers(2, 11))
@@ -59,3 +59,34 @@ def test_random_planner_configurations(case):
         want = orc.table(queries[q])
         got = tables[toff[q]:toff[q + 1]].astype(np.int64)
         assert np.array_equal(got, want), (case, q, queries[q])
+
+
+@pytest.mark.parametrize("case", range(16))
+def test_random_score_configurations(case):
+    """Score plans under the same random options: every (child, parents)
+    score within 1e-5 of the oracle's FP64 value (plus 1e-6 absolute for MI,
+    whose value can be near zero)."""
+    rng = np.random.default_rng(7000 + case)
+    n = int(rng.integers(3, 12))
+    m = int(rng.choice([17, 4097, 60_013, 200_003]))
+    db = random_dag_database(n, m, int(rng.choice([1, 2])), int(rng.choice([3, 5, 9])), 3, 1.0, seed=50 + case)
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    for key, vals in OPTION_CHOICES.items():
+        fc.fc_set_option(ctx, key, int(vals[int(rng.integers(0, len(vals)))]))
+    nq = int(rng.choice([1, 40, 5000]))
+    child, parents = [], []
+    for _ in range(nq):
+        c = int(rng.integers(0, n))
+        others = [v for v in range(n) if v != c]
+        k = int(rng.integers(0, min(5, len(others)) + 1))
+        child.append(c)
+        parents.append([int(x) for x in rng.choice(others, size=k, replace=False)])
+    po, pa = fc.pack_lists(parents)
+    kind = ["ll", "mdl", "bdeu", "mi"][case % 4]
+    got = fc.fc_score_batch(ctx, child, po, pa, kind, 1.0)
+    check = range(nq) if nq <= 40 else range(0, nq, 53)
+    for q in check:
+        want = orc.score(child[q], parents[q], kind, 1.0)
+        tol = 1e-5 * abs(want) + (1e-6 if kind == "mi" else 1e-12)
+        assert abs(float(got[q]) - want) <= tol, (case, kind, q, child[q], parents[q], float(got[q]), want)
