@@ -295,7 +295,9 @@ extern "C" void fc_free(fc_ctx *c)
         if (st.ev) cudaEventDestroy(st.ev);
     }
     if (c->out_stream) cudaStreamDestroy(c->out_stream);
-    for (cudaEvent_t ev : c->half_done)
+    for (cudaEvent_t ev : c->part_done)
+        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : c->copy_done)
         if (ev) cudaEventDestroy(ev);
     for (auto &b : c->io) b.release();
     c->marg_delta.release();

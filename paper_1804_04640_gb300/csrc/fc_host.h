@@ -217,12 +217,13 @@ struct fc_ctx {
     // pairs), in two banks so that a synchronous call can have a plan
     // running while it builds the next; `bank` selects the one in use
     fc::DBuf pool[2][6];
-    fc::DBuf pipe_io[2];     // device outputs of the two halves of a pipelined call
+    fc::DBuf pipe_io[2];     // device outputs of the parts of a pipelined call, per bank
     int bank = 0;
     int32_t q_base = 0;  // index of the plan's first query in the caller's batch (messages)
     bool borrow = false; // set while a synchronous entry point builds its plan
     cudaStream_t out_stream = nullptr;  // device-to-host copies of pipelined calls
-    cudaEvent_t half_done[2] = {nullptr, nullptr};
+    cudaEvent_t part_done[2] = {nullptr, nullptr};   // a bank's part: kernels done
+    cudaEvent_t copy_done[2] = {nullptr, nullptr};   // a bank's part: output copied out
     std::vector<uint32_t> mark;
     uint32_t epoch = 0;
     uint64_t generation = 0;  // bumped by every append; plans of older generations refuse to run
