@@ -186,16 +186,16 @@ int fc_count_assignment_batch(fc_ctx *ctx, int32_t nq, const int32_t *var_off, c
  * of `tables`; table_off is non-decreasing with
  * table_off[q+1] - table_off[q] >= cells of query q.  Pass table_off = NULL
  * to pack the tables back to back in query order.  A batch of 4096 queries
- * or more runs in two halves: the second half is planned while the first
- * one's kernels run, and each half's tables are copied back while the GPU
- * goes on (a bad query in the second half is reported after the first half
+ * or more runs in two parts: the second part is planned while the first
+ * one's kernels run, and each part's tables are copied back while the GPU
+ * goes on (a bad query in the second part is reported after the first part
  * ran).  `tables` is best in pinned memory (cudaHostAlloc), which the copies
  * can overlap. */
 int fc_count_batch(fc_ctx *ctx, int32_t nq, const int32_t *var_off, const int32_t *vars,
                    const int64_t *table_off, int32_t *tables);
 
 /* Scores of nq (child, parents) queries (Sec. 3.1, Eq. 1; kinds above);
- * batches of 4096 or more run in two halves as in fc_count_batch.
+ * batches of 4096 or more run in two parts as in fc_count_batch.
  * Query q scores child[q] given parents[par_off[q] .. par_off[q+1]); the
  * child must not be among its parents.  ess is the BDeu equivalent sample
  * size (ignored by the other kinds).  scores: nq float (FP32 result; BDeu is
