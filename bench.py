@@ -345,7 +345,7 @@ def run_reference(args, rank: int, world: int):
         steps.append(oracle_rate(args.workload, w, max(0.5, args.ref_seconds / 4), cores)[0])
     value = statistics.median(steps[args.warmup:]) if args.steps else rate
     unit = UNITS[args.workload]
-    line = {"impl": "reference", "metric": METRIC if args.workload == "random" else f"{args.workload} {unit}",
+    line = {"impl": "reference", "metric": METRIC if args.workload == "random" else f"{args.workload}: {unit}",
             "value": value, "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64/f64",
             "data": "synthetic (seeded)", "config": describe(args.workload, w),
