@@ -440,6 +440,32 @@ const char *fc_last_error(void);
  * Exercises the bounded-wait error path without faulting the GPU. */
 int fc_selftest_wait_timeout(fc_ctx *ctx, int64_t wait_limit);
 
+/* ------------------------------------------------- throughput probes
+ *
+ * The paper has no counterpart to this call: it measures the rates of the
+ * on-chip units that bound the counting kernels on databases that stay in L2,
+ * the denominators of their rooflines (HBM bandwidth bounds none of them
+ * there).  Each probe runs one kernel that does nothing but the measured
+ * operation, with every lane busy, on the current device:
+ *   FC_PROBE_L2_READ      16-byte loads that bypass L1 over a `size`-byte
+ *                         buffer (a power of two from 1 MiB to 64 MiB) that
+ *                         stays in L2: bytes/s.  The histogram strategy reads
+ *                         its columns this way (Sec. 3.3's partition pass).
+ *   FC_PROBE_SMEM_ATOMIC  conflict-free atomicAdd(+1) to shared memory, every
+ *                         lane of a warp on its own bank: atomics/s.  The
+ *                         histogram strategy issues one per instance.
+ *   FC_PROBE_AND_POPC     c += popcount(a & b) on 64-bit words held in
+ *                         registers: words/s.  The bitmap strategy (Sec. 3.2)
+ *                         and itemset supports (Sec. 4.3) do one per word of
+ *                         every intersection.
+ * `size` is ignored by the last two.  The call allocates a small buffer (and
+ * the probe buffer), launches one untimed and five timed kernels on `stream`
+ * (NULL = legacy default stream), waits for them and writes the best rate to
+ * *rate.  Errors: FC_ERR_ARG (unknown kind, bad size, null rate), FC_ERR_OOM,
+ * FC_ERR_CUDA. */
+enum { FC_PROBE_L2_READ = 0, FC_PROBE_SMEM_ATOMIC = 1, FC_PROBE_AND_POPC = 2 };
+int fc_probe_rate(int32_t kind, int64_t size, double *rate, void *stream);
+
 /* ------------------------------------------------- allocation-free variant
  *
  * The paper has no counterpart to this call; it exists for callers that
@@ -465,8 +491,10 @@ int fc_selftest_wait_timeout(fc_ctx *ctx, int64_t wait_limit);
  *   stream  cudaStream_t the work is enqueued on (NULL = the legacy default
  *           stream).  The call returns once the work is enqueued.
  * The first call on a device looks up the scratch array's device address
- * (once per device, with that device current); make that first call before
- * any stream capture begins.  All calls share the one scratch array and it
+ * (once per device, with that device current) and keeps it for the life of
+ * the process; make that first call before any stream capture begins, and do
+ * not use the call across a cudaDeviceReset (the kept address would be
+ * stale).  D may be NULL when m is 0; the table is then all zeros.  All calls share the one scratch array and it
  * keeps the last call's contents, so calls whose work overlaps on the GPU
  * (other streams, other host threads) race and give wrong counts: serialise
  * them.  No call allocates or frees memory.

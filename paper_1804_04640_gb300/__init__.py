@@ -35,7 +35,7 @@ EXPORTS = (
     "fc_count_assignment_batch", "fc_plan_assignments", "fc_families_count", "fc_score_families",
     "fc_plan_families", "fc_mine_rules", "fc_rules_size", "fc_rules_itemsets", "fc_rules_list",
     "fc_rules_free", "fc_append", "fc_append_bits", "fc_reserve", "fc_support_splits_batch",
-    "fc_plan_support_splits",
+    "fc_plan_support_splits", "fc_probe_rate",
 )
 
 
@@ -88,6 +88,7 @@ def load_library(build_if_missing: bool = False):
                                          ctypes.c_double, ctypes.POINTER(_vp)]),
         "fc_plan_support": (ctypes.c_int, [_vp, ctypes.c_int32, _i32p, _i32p, ctypes.POINTER(_vp)]),
         "fc_plan_pairs": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
+        "fc_probe_rate": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), _vp]),
         "fc_plan_size": (ctypes.c_int64, [_vp, ctypes.c_int32]),
         "fc_plan_table_offsets": (ctypes.c_int, [_vp, _i64p]),
         "fc_plan_strategies": (ctypes.c_int, [_vp, _i32p]),
@@ -578,16 +579,46 @@ def fc_selftest_wait_timeout(ctx: Handle, wait_limit: int) -> int:
     return int(load_library().fc_selftest_wait_timeout(ctx.ptr, int(wait_limit)))
 
 
+FC_PROBE_L2_READ, FC_PROBE_SMEM_ATOMIC, FC_PROBE_AND_POPC = 0, 1, 2
+
+
+def fc_probe_rate(kind: int, size: int = 0, stream=None) -> float:
+    """Rate of one on-chip unit on the current device (fc_probe_rate in
+    include/fc.h): bytes/s, atomics/s or words/s."""
+    out = ctypes.c_double(0.0)
+    _check(load_library().fc_probe_rate(int(kind), int(size), ctypes.byref(out), _stream_ptr(stream)))
+    return float(out.value)
+
+
 def fc_count_sorted_noalloc(D, arities, vars_, table, stream=None):
     """One table by sort + run-length with the library's fixed scratch (no
     allocation).  D: CUDA uint8 tensor (n, ld) column-major, rows of at least
     m instances; table: CUDA int32 tensor of prod(arities[vars]) cells.  The
-    call is asynchronous on `stream`."""
+    call is asynchronous on `stream`.  Arguments the C call cannot check
+    (device buffer sizes, dtypes, devices, the length of `arities`) are
+    checked here before anything is enqueued."""
     if not (_is_cuda(D) and _is_cuda(table)):
         raise FcError(FC_ERR_ARG, "fc_count_sorted_noalloc needs CUDA tensors for D and table")
+    import torch
+    if D.dtype != torch.uint8 or D.dim() != 2 or (D.shape[1] > 1 and D.stride(1) != 1):
+        raise FcError(FC_ERR_ARG, "D must be a 2-D uint8 tensor whose instances are contiguous (stride(1) == 1)")
+    if table.dtype != torch.int32 or not table.is_contiguous():
+        raise FcError(FC_ERR_ARG, "table must be a contiguous int32 tensor")
+    cur = torch.cuda.current_device()
+    if D.device.index != cur or table.device.index != cur:
+        raise FcError(FC_ERR_ARG, f"D and table must be on the current device (cuda:{cur})")
     ar, v = _host(arities, np.int32), _host(vars_, np.int32)
-    n, ld = int(D.shape[0]), int(D.stride(0))
-    m = int(D.shape[1])
+    n, m = int(D.shape[0]), int(D.shape[1])
+    ld = int(D.stride(0)) if n > 1 else m
+    if ar.ndim != 1 or len(ar) < n:
+        raise FcError(FC_ERR_ARG, f"arities holds {ar.size} values for {n} variables")
+    if v.ndim != 1 or np.any(v < 0) or np.any(v >= n):
+        raise FcError(FC_ERR_ARG, "a variable id is outside 0..n-1")
+    cells = 1
+    for x in v:
+        cells *= int(ar[x])
+    if table.numel() < cells:
+        raise FcError(FC_ERR_SIZE, f"table holds {table.numel()} cells, the query needs {cells}")
     _check(load_library().fc_count_sorted_noalloc(_ptr(D), n, m, ld, _ptr(ar, _i32p), _ptr(v, _i32p), len(v),
                                                   _ptr(table), _stream_ptr(stream)))
 

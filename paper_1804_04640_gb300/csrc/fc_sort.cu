@@ -256,7 +256,7 @@ extern "C" int fc_count_sorted_noalloc(const uint8_t *D, int32_t n, int64_t m, i
                                        int32_t *table, void *stream)
 {
     using namespace fc;
-    if (!D || !arities || !table || (k > 0 && !vars))
+    if ((!D && m > 0) || !arities || !table || (k > 0 && !vars))
         return set_error(FC_ERR_ARG, "fc_count_sorted_noalloc: null argument");
     if (n < 1 || m < 0 || ld < m || k < 0 || k > kMaxK)
         return set_error(FC_ERR_ARG, "fc_count_sorted_noalloc: bad n, m, ld or k");

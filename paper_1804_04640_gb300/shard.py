@@ -33,6 +33,14 @@ def query_range(nq: int, rank: int, world: int) -> tuple[int, int]:
     return nq * rank // world, nq * (rank + 1) // world
 
 
+def split_batch(batch, rank: int, world: int):
+    """The part of a batch of independent queries that `rank` answers: the
+    contiguous slice query_range(len(batch), rank, world).  The parts of all
+    ranks tile the batch, so every query is answered exactly once."""
+    lo, hi = query_range(len(batch), rank, world)
+    return batch[lo:hi]
+
+
 def allreduce_tables(tables: np.ndarray, group=None) -> np.ndarray:
     """Exact sum of the ranks' partial tables (int64, through torch.distributed)."""
     import torch
