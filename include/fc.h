@@ -415,7 +415,14 @@ int fc_sync(fc_ctx *ctx, void *stream);
  *   "hist_cost_var", "flush_cost"
  *                       cost-model coefficients (femtoseconds) used by AUTO
  *   "support_warps", "support_sets_per_warp", "support_part_words"
- *                       launch shape of the itemset-support kernels. */
+ *                       launch shape of the itemset-support kernels
+ *   "zero_copy"         1 (default) = when the output buffer of fc_count,
+ *                       fc_count_batch or fc_score_batch is page-locked host
+ *                       memory (cudaHostAlloc, or cudaHostRegister with
+ *                       mapping) and no output cell is accumulated, the
+ *                       kernels store the outputs into it directly instead
+ *                       of into a device buffer that is copied afterwards;
+ *                       0 = always copy. */
 int fc_set_option(fc_ctx *ctx, const char *key, int64_t value);
 
 /* Current value of an option (or -1 for an unknown key). */

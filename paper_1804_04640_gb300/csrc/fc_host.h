@@ -90,6 +90,7 @@ struct Options {
     int32_t hist_copies = 4;
     int64_t min_part_rows = 8192;
     int64_t pair_chunk_rows = 1 << 16;
+    int32_t pair_producer_warps = 16; // warps of the all-pairs kernel that build operands (16, 24, 31)
     int32_t use_graph = 1;
     int64_t wait_limit = 1 << 22;
     int64_t sort_min_cells = 1 << 25;
@@ -112,6 +113,10 @@ struct Options {
     int32_t support_warps = 16;
     int32_t support_sets_per_warp = 4;
     int64_t support_part_words = 8192;
+    // synchronous count / score calls whose output buffer is page-locked
+    // host memory let the kernels store into it directly (no device buffer,
+    // no copy) when no output cell is accumulated
+    int32_t zero_copy = 1;
 };
 
 // Host arrays of the count planner, kept by the context between plan builds

@@ -182,6 +182,9 @@ struct SupportParams {
     const int64_t *split_off;
     int32_t all_splits;
     int32_t pad;
+    // marginal count of every item (one-item subsets are not counted by the
+    // kernels: the finishing pass copies these)
+    const int64_t *marg;
 };
 constexpr int kMaxSplitK = 16;  // itemset size limit of the all-splits mode
 cudaError_t launch_support(const SupportParams &p, int grid, int threads, size_t smem,
@@ -190,6 +193,22 @@ cudaError_t launch_support_confidence(const SupportParams &p, cudaStream_t s);
 const void *support_kernel_ptr(int mode);  // 0 leave-one-out, 1 full only, 2 all splits
 
 // All-pairs one-hot co-occurrence on tcgen05 tensor cores.
+//
+// One 256 x 256 region of C on or above its diagonal: rows ra*256.. (the A
+// operand, two halves of 128 rows, one accumulator each) against columns
+// rb*256.. (the B operand).  Only the cells on or above the diagonal of C and
+// inside the R x R matrix are needed, so each accumulator multiplies only the
+// columns it needs: n0 / n1 columns (multiples of 16, 0 = skipped), the
+// second half starting coff1 columns into B (128 on the diagonal, whose
+// lower-left quarter lies below the diagonal).  Its rows are split over
+// ksplit CTAs from cta0 on.
+struct PairsRegion {
+    int32_t ra, rb;
+    int32_t n0, n1, coff1;
+    int32_t real_b;      // B rows inside the R x R matrix (the rest are zero)
+    int32_t cta0, ksplit;
+};
+
 struct PairsParams {
     const uint64_t *bits;    // R rows of wstride words (one row per (variable, state))
     int64_t wstride;
@@ -198,12 +217,14 @@ struct PairsParams {
     int32_t R_pad;           // padded to the tile size
     int32_t *C;              // R_pad x R_pad int32 co-occurrence (upper tiles), zeroed
     int32_t chunk_words;     // words accumulated in FP32 before the move to int32
-    int32_t ksplit;          // row splits per tile
+    int32_t nregions;
+    const PairsRegion *regions;  // device array, cta0 ascending
+    int32_t grid;            // CTAs of the launch (sum of the regions' ksplit)
+    int32_t producer_warps;  // warps expanding operands: 16, 24 or 31
     int32_t *status;
     int64_t wait_limit;
 };
 cudaError_t launch_pairs_gemm(const PairsParams &p, cudaStream_t s);
-int pairs_tile_count(int32_t R_pad);
 cudaError_t launch_pairs_extract(const int32_t *C, int32_t R_pad, int32_t n, const int32_t *d_arity,
                                  const int32_t *d_soff, const int64_t *d_pair_off, int64_t m,
                                  int32_t *pair_tables, float *mi, cudaStream_t s);

@@ -13,14 +13,20 @@
 //     shared memory with the 128-byte swizzle the MMA descriptors describe;
 //   * a CTA owns a 256 x 256 region of C and one range of rows (split K):
 //     two tcgen05.mma.cta_group::1.kind::f8f6f4 accumulators (M = 128,
-//     N = 256, K = 32, FP32 in tensor memory, 512 columns) share one B
-//     operand of 256 rows; on diagonal regions both A halves are slices of B,
-//     so only B is built.  Every product is 0 or 2^-12 and every partial sum
-//     is 2^-12 times an integer no larger than the rows of one split, which
-//     the planner keeps far below 2^24, so the FP32 sums are exact; the
-//     result is read with tcgen05.ld, scaled by 2^12, converted to int32 and
-//     added to C;
-//   * only regions on or above the diagonal of C are computed.
+//     N <= 256, K = 32, FP32 in tensor memory, 512 columns) share one B
+//     operand; on diagonal regions both A halves are slices of B, so only B
+//     is built.  Every product is 0 or 2^-12 and every partial sum is 2^-12
+//     times an integer no larger than the rows of one split, which the
+//     planner keeps far below 2^24, so the FP32 sums are exact; the result is
+//     read with tcgen05.ld, scaled by 2^12, converted to int32 and added to C;
+//   * only regions on or above the diagonal of C are computed, and in each
+//     an accumulator multiplies only the columns it needs: those inside the
+//     R x R matrix (rounded up to 16, the MMA's N granule), and on the
+//     diagonal the second half skips the quarter below the diagonal.  Rows
+//     of B past R are zero, filled once per stage buffer; the planner splits
+//     each region's rows over CTAs in proportion to its shared-memory
+//     traffic, so that every CTA of the one wave finishes at about the same
+//     time.
 //
 // Pipeline per CTA: 16 producer warps fill kStages shared-memory stages
 // (loading the bitmap words three stages ahead of the one they expand) and
@@ -39,9 +45,6 @@ constexpr int kN = 256;                      // columns of one MMA
 constexpr int kRegion = 256;                 // a CTA's region of C is kRegion x kRegion
 constexpr int kKStage = 128;                 // instances per stage = bytes per operand row
 constexpr int kStages = 3;
-constexpr int kProducerWarps = 16;
-constexpr int kProducers = kProducerWarps * 32;
-constexpr int kThreads = kProducers + 32;    // + the MMA / TMEM warp
 constexpr int kABytes = kRegion * kKStage;   // two A halves of 128 rows, 32 KiB
 constexpr int kBBytes = kN * kKStage;        // 32 KiB
 constexpr int kStageBytes = kABytes + kBBytes;
@@ -50,7 +53,10 @@ constexpr uint32_t kTmemCols = 512;          // two 128 x 256 FP32 accumulators
 
 // Instruction descriptor of kind::f8f6f4: D = F32 (bits 4-5 = 1), A = B = E4M3
 // (format 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+__device__ __forceinline__ uint32_t idesc_n(int n)
+{
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -97,12 +103,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int64_t l
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+__device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -137,37 +144,34 @@ __device__ __forceinline__ void store_row_word(uint8_t *tile, int row, int half,
     }
 }
 
-// Region idx in the order (ra, rb), ra <= rb, rb-major.
-__device__ __forceinline__ void region_of(int idx, int R_pad, int &ra, int &rb)
+// PW producer warps expand the operands; warp PW issues the MMAs and owns
+// the tensor memory; warps 0..3 also read the accumulators back.
+template <int PW>
+__global__ void __launch_bounds__(PW * 32 + 32, 1) pairs_gemm_kernel(const PairsParams P)
 {
-    const int nb = R_pad / kRegion;
-    for (int b = 0; b < nb; ++b)
-        for (int a = 0; a <= b; ++a) {
-            if (idx == 0) {
-                ra = a;
-                rb = b;
-                return;
-            }
-            --idx;
-        }
-    ra = rb = 0;
-}
-
-__global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsParams P)
-{
+    constexpr int kProducerWarps = PW;
+    constexpr int kProducers = kProducerWarps * 32;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = (uint64_t *)(smem + kStages * kStageBytes);  // full[S], empty[S], acc
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int region = blockIdx.x / P.ksplit, split = blockIdx.x % P.ksplit;
-    int ra, rb;
-    region_of(region, P.R_pad, ra, rb);
-    const bool diag = ra == rb;  // both A halves are slices of B
+    // this CTA's region: the last one whose first CTA is at or before it
+    int lo = 0, hi = P.nregions - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.regions[mid].cta0 <= (int)blockIdx.x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const PairsRegion G = P.regions[lo];
+    const int split = (int)blockIdx.x - G.cta0;
+    const bool diag = G.ra == G.rb;  // both A halves are slices of B
     const int64_t total_stages = (P.words + 1) / 2;
-    const int64_t st0 = total_stages * split / P.ksplit;
-    const int64_t st1 = total_stages * (split + 1) / P.ksplit;
+    const int64_t st0 = total_stages * split / G.ksplit;
+    const int64_t st1 = total_stages * (split + 1) / G.ksplit;
     const int64_t nst = st1 - st0;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kStages), accb = smem_u32(bars + 2 * kStages);
 
@@ -193,21 +197,31 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
 
     if (warp < kProducerWarps) {
         // ---------------------------------------------------------- producers
-        // tasks: (operand row, half of the stage's two 64-bit words); rows
-        // 0..255 are the A halves, 256..511 are B
+        // B rows past the matrix that the MMAs read (up to N's 16-row granule,
+        // and on the diagonal the rows the A halves take from B) are zero in
+        // every stage buffer, written once
+        const int bread = diag ? max((G.real_b + 15) & ~15, G.n1 > 0 ? kRegion : kM) : (G.real_b + 15) & ~15;
+        for (int u = threadIdx.x; u < kStages * (bread - G.real_b) * 8; u += kProducers) {
+            const int slot = u / ((bread - G.real_b) * 8), r = u % ((bread - G.real_b) * 8);
+            uint8_t *b_tile = smem + slot * kStageBytes + kABytes;
+            *reinterpret_cast<uint4 *>(b_tile + (G.real_b + (r >> 3)) * 128 + ((r & 7) << 4)) = make_uint4(0, 0, 0, 0);
+        }
+        // tasks: (operand row, half of the stage's two 64-bit words); off the
+        // diagonal rows 0..255 are the A halves and 256.. are B, on it all
+        // rows are B
         constexpr int kTasksMax = ((kRegion + kN) * 2 + kProducers - 1) / kProducers;
-        const int first = diag ? kRegion * 2 : 0;  // skip the A rows when A comes from B
-        const int ntask = (kRegion + kN) * 2 - first;
+        const int a_rows = diag ? 0 : kRegion;
+        const int ntask = (a_rows + G.real_b) * 2;
         // words of stages st + 1, st + 2, st + 3 in flight while stage st is expanded
         uint64_t p1[kTasksMax], p2[kTasksMax], p3[kTasksMax];
         auto load = [&](int64_t st, uint64_t (&dst)[kTasksMax]) {
             const int64_t kw = (st0 + st) * 2;  // first 64-bit word of that stage
 #pragma unroll
             for (int j = 0; j < kTasksMax; ++j) {
-                const int u = first + threadIdx.x + j * kProducers;
+                const int u = threadIdx.x + j * kProducers;
                 const int i = u >> 1, half = u & 1;
-                const int grow = i < kRegion ? ra * kRegion + i : rb * kRegion + (i - kRegion);
-                dst[j] = (st < nst && u < first + ntask && grow < P.R)
+                const int grow = i < a_rows ? G.ra * kRegion + i : G.rb * kRegion + (i - a_rows);
+                dst[j] = (st < nst && u < ntask && grow < P.R)
                              ? __ldg(P.bits + (int64_t)grow * P.wstride + kw + half)
                              : 0ull;
             }
@@ -236,13 +250,13 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
             uint8_t *b_tile = a_tile + kABytes;
 #pragma unroll
             for (int j = 0; j < kTasksMax; ++j) {
-                const int u = first + threadIdx.x + j * kProducers;
-                if (u < first + ntask) {
+                const int u = threadIdx.x + j * kProducers;
+                if (u < ntask) {
                     const int i = u >> 1, half = u & 1;
-                    if (i < kRegion)
+                    if (i < a_rows)
                         store_row_word(a_tile, i, half, cur[j]);
                     else
-                        store_row_word(b_tile, i - kRegion, half, cur[j]);
+                        store_row_word(b_tile, i - a_rows, half, cur[j]);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -250,6 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
         }
     } else if (lane == 0) {
         // ------------------------------------------------------ MMA issuer
+        const uint32_t id0 = G.n0 > 0 ? idesc_n(G.n0) : 0u, id1 = G.n1 > 0 ? idesc_n(G.n1) : 0u;
         for (int64_t st = 0; st < nst; ++st) {
             const int slot = (int)(st % kStages);
             if (!mbar_wait(full0 + 8 * slot, (uint32_t)((st / kStages) & 1), P.wait_limit) ||
@@ -260,12 +275,15 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
             tc_fence_after();
             const uint32_t b_addr = smem_u32(smem + slot * kStageBytes) + kABytes;
             const uint32_t a_addr = diag ? b_addr : b_addr - kABytes;
+            const uint32_t b1_addr = b_addr + (uint32_t)G.coff1 * kKStage;  // B rows from coff1 on
 #pragma unroll
             for (int kk = 0; kk < kKStage / 32; ++kk) {
-                const uint64_t bd = smem_desc(b_addr + 32 * kk);
                 const uint32_t acc = (st > 0 || kk > 0) ? 1u : 0u;
-                mma_f8(tmem, smem_desc(a_addr + 32 * kk), bd, acc);                          // rows 0..127
-                mma_f8(tmem + kN, smem_desc(a_addr + kM * kKStage + 32 * kk), bd, acc);     // rows 128..255
+                if (G.n0 > 0)  // rows 0..127
+                    mma_f8(tmem, smem_desc(a_addr + 32 * kk), smem_desc(b_addr + 32 * kk), id0, acc);
+                if (G.n1 > 0)  // rows 128..255
+                    mma_f8(tmem + kN, smem_desc(a_addr + kM * kKStage + 32 * kk), smem_desc(b1_addr + 32 * kk), id1,
+                           acc);
             }
             mma_commit(empty0 + 8 * slot);
         }
@@ -281,10 +299,12 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
         if (__all_sync(kFull, done && !*(volatile int *)&s_abort)) {
 #pragma unroll 1
           for (int half = 0; half < 2; ++half) {
-            const int row = ra * kRegion + half * kM + warp * 32 + lane;
-            int32_t *crow = P.C + (int64_t)row * P.R_pad + rb * kRegion;
+            const int n = half ? G.n1 : G.n0;
+            const int coff = half ? G.coff1 : 0;
+            const int row = G.ra * kRegion + half * kM + warp * 32 + lane;
+            int32_t *crow = P.C + (int64_t)row * P.R_pad + G.rb * kRegion + coff;
 #pragma unroll 1
-            for (int c0 = 0; c0 < kN; c0 += 32) {
+            for (int c0 = 0; c0 < n; c0 += 32) {
                 uint32_t r[32];
                 const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(half * kN + c0);
                 asm volatile(
@@ -301,9 +321,10 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
                 if (row < P.R) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int col = rb * kRegion + c0 + j;  // the lower triangle is never read
+                        // columns of the accumulator only; the lower triangle is never read
+                        const int col = G.rb * kRegion + coff + c0 + j;
                         const int v = __float2int_rn(__uint_as_float(r[j]) * kOneHotScale);
-                        if (v && col < P.R && row <= col) atomicAdd(crow + c0 + j, v);
+                        if (c0 + j < n && v && col < P.R && row <= col) atomicAdd(crow + c0 + j, v);
                     }
                 }
             }
@@ -372,20 +393,24 @@ __global__ void wait_selftest_kernel(int32_t *status, int64_t limit)
 
 }  // namespace
 
-int pairs_tile_count(int32_t R_pad)
+template <int PW>
+cudaError_t launch_pairs_pw(const PairsParams &p, cudaStream_t s)
 {
-    const int nb = R_pad / kRegion;
-    return nb * (nb + 1) / 2;
+    cudaError_t e = cudaFuncSetAttribute(pairs_gemm_kernel<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemBytes);
+    if (e != cudaSuccess) return e;
+    pairs_gemm_kernel<PW><<<p.grid, PW * 32 + 32, kSmemBytes, s>>>(p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pairs_gemm(const PairsParams &p, cudaStream_t s)
 {
-    if (p.R_pad % kRegion != 0) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(pairs_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    const int grid = pairs_tile_count(p.R_pad) * p.ksplit;
-    pairs_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(p);
-    return cudaGetLastError();
+    if (p.R_pad % kRegion != 0 || p.nregions < 1 || p.grid < 1) return cudaErrorInvalidValue;
+    switch (p.producer_warps) {
+    case 24: return launch_pairs_pw<24>(p, s);
+    case 31: return launch_pairs_pw<31>(p, s);
+    default: return launch_pairs_pw<16>(p, s);
+    }
 }
 
 cudaError_t launch_pairs_extract(const int32_t *C, int32_t R_pad, int32_t n, const int32_t *d_arity,

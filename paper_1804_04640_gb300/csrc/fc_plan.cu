@@ -798,14 +798,52 @@ int read_status(fc_ctx *c, cudaStream_t s)
     return FC_OK;
 }
 
+// Device address of a caller's host output buffer [h, h + bytes) when the
+// whole buffer is page-locked host memory the GPU can store to (cudaHostAlloc,
+// or cudaHostRegister with mapping; on a GB300 node such stores travel over
+// the CPU-GPU link while the kernel runs), else nullptr.
+void *device_view(const void *h, size_t bytes)
+{
+    if (!h || bytes == 0) return nullptr;
+    const uint8_t *first = (const uint8_t *)h, *last = first + bytes - 1;
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, first) != cudaSuccess || cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+        return nullptr;
+    if ((const uint8_t *)b.devicePointer - (const uint8_t *)a.devicePointer != (ptrdiff_t)(bytes - 1)) return nullptr;
+    return a.devicePointer;
+}
+
+// A count or score plan whose kernels only store to the output (no output
+// cell is accumulated, so nothing must be zeroed first) can write straight
+// into a caller's page-locked host buffer instead of a device buffer that is
+// copied afterwards.
+bool stores_only(const fc_plan *p)
+{
+    if (p->kind == kPlanScore) return true;
+    return p->kind == kPlanCount && !p->zero_tables && p->sort_jobs.empty();
+}
+
 // Runs a plan on the context stream with runtime-owned device outputs and
-// copies them to the caller's host buffers.
+// copies them to the caller's host buffers (or, for a plan that only stores
+// its outputs, has the kernels write page-locked host buffers directly).
 int run_to_host(fc_plan *p, void *h0, size_t b0, void *h1, size_t b1, void *h2, size_t b2)
 {
     fc_ctx *c = p->ctx;
     void *hs[3] = {h0, h1, h2};
     size_t bs[3] = {b0, b1, b2};
     void *ds[3] = {nullptr, nullptr, nullptr};
+    if (c->opt.zero_copy && stores_only(p) && b1 == 0 && b2 == 0) {
+        void *dv = device_view(h0, b0);
+        if (dv) {
+            int rc = run_plan(p, dv, nullptr, nullptr, c->stream, false);
+            if (rc != FC_OK) return rc;
+            return read_status(c, c->stream);
+        }
+    }
     for (int i = 0; i < 3; ++i) {
         if (!hs[i] || bs[i] == 0) continue;
         cudaError_t e = c->io[i].ensure(bs[i]);
@@ -1057,6 +1095,14 @@ int run_in_parts(fc_ctx *c, int32_t nq, uint8_t *host, Build build)
             c->q_base = 0;
         }
         if (rc != FC_OK) break;
+        // a part whose kernels only store their outputs writes the caller's
+        // page-locked buffer directly: no device buffer, no copy
+        void *direct = c->opt.zero_copy && stores_only(plans[i]) ? device_view(host + off, bytes) : nullptr;
+        if (direct) {
+            rc = run_plan(plans[i], direct, nullptr, nullptr, c->stream, false);
+            if (rc != FC_OK) break;
+            continue;
+        }
         cudaError_t e = c->pipe_io[bank].ensure(std::max<size_t>(bytes, 4));
         // the bank's output buffer is free once the earlier part's copy ends
         if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(c->stream, c->copy_done[bank], 0);

@@ -29,7 +29,9 @@ cudaError_t enqueue_support(fc_plan *p, int32_t *support, int32_t *sub, float *c
     if (p->nq == 0) return cudaSuccess;
     e = launch_support(P, p->sup_grid, p->sup_threads, 0, s);
     if (e != cudaSuccess) return e;
-    if (conf) e = launch_support_confidence(P, s);
+    // the finishing pass fills one-item subsets from the marginals (and the
+    // confidences, when asked for)
+    if (!P.full_only) e = launch_support_confidence(P, s);
     return e;
 }
 
@@ -171,6 +173,7 @@ int build_set_plan(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t 
     SupportParams &P = p->sp;
     uint8_t *d = (uint8_t *)p->desc.p;
     P.bits = c->d_bits;
+    P.marg = c->d_marg;
     P.wstride = c->wstride;
     P.words = c->words;
     P.set_off = (const int32_t *)d;

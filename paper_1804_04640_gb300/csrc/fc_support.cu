@@ -51,30 +51,40 @@ __device__ __forceinline__ void support_set(const SupportParams &P, const int32_
             pre[1] = x[0];
 #pragma unroll
             for (int t = 2; t <= K; ++t) pre[t] = pre[t - 1] & x[t - 1];
-            uint64_t suf = x[K - 1];  // AND of x[t+1..K-1] for t = K-2
-            loo[K - 1] += (unsigned)__popcll(pre[K - 1]);
-#pragma unroll
-            for (int t = K - 2; t >= 1; --t) {
-                loo[t] += (unsigned)__popcll(pre[t] & suf);
-                suf &= x[t];
-            }
-            loo[0] += (unsigned)__popcll(suf);
             full += (unsigned)__popcll(pre[K]);
+            // two items: each leave-one-out set is one item, whose count is
+            // its marginal (filled in by the finishing kernel)
+            if constexpr (K > 2) {
+                uint64_t suf = x[K - 1];  // AND of x[t+1..K-1] for t = K-2
+                loo[K - 1] += (unsigned)__popcll(pre[K - 1]);
+#pragma unroll
+                for (int t = K - 2; t >= 1; --t) {
+                    loo[t] += (unsigned)__popcll(pre[t] & suf);
+                    suf &= x[t];
+                }
+                loo[0] += (unsigned)__popcll(suf);
+            }
         }
     }
     full = __reduce_add_sync(kFullMask, full);
+    if constexpr (K > 2) {
 #pragma unroll
-    for (int t = 0; t < K; ++t) loo[t] = __reduce_add_sync(kFullMask, loo[t]);
+        for (int t = 0; t < K; ++t) loo[t] = __reduce_add_sync(kFullMask, loo[t]);
+    }
     if (lane == 0) {
         if (atomic) {
             if (full) atomicAdd(supp, (int)full);
+            if constexpr (K > 2) {
 #pragma unroll
-            for (int t = 0; t < K; ++t)
-                if (loo[t]) atomicAdd(sub + t, (int)loo[t]);
+                for (int t = 0; t < K; ++t)
+                    if (loo[t]) atomicAdd(sub + t, (int)loo[t]);
+            }
         } else {
             *supp = (int)full;
+            if constexpr (K > 2) {
 #pragma unroll
-            for (int t = 0; t < K; ++t) sub[t] = (int)loo[t];
+                for (int t = 0; t < K; ++t) sub[t] = (int)loo[t];
+            }
         }
     }
 }
@@ -246,6 +256,11 @@ __global__ void __launch_bounds__(512, 2) assign_kernel(const SupportParams P)
 // With k fixed at compile time the walk unrolls completely and the 2^k - 1
 // counters (subset masks 1 .. 2^k - 1) sit in registers.
 
+// A one-item subset's support is that item's marginal count, taken when the
+// bitmaps were loaded (Sec. 3.3 precomputes single-variable partitions), so
+// the walk counts only subsets of two or more items; the finishing kernel
+// fills in the one-item entries.
+
 template <int K, int T, int MASK>
 struct SubsetWalk {
     // subsets MASK | {some items >= T}; acc is the AND of MASK's words
@@ -253,7 +268,7 @@ struct SubsetWalk {
     {
         if constexpr (T < K) {
             const uint64_t a = MASK == 0 ? x[T] : (acc & x[T]);
-            cnt[MASK | (1 << T)] += (unsigned)__popcll(a);
+            if constexpr (MASK != 0) cnt[MASK | (1 << T)] += (unsigned)__popcll(a);
             SubsetWalk<K, T + 1, MASK | (1 << T)>::run(x, a, cnt);
             SubsetWalk<K, T + 1, MASK>::run(x, acc, cnt);
         }
@@ -286,6 +301,7 @@ __device__ __forceinline__ void splits_set(const SupportParams &P, const int32_t
     constexpr int kFull = (1 << K) - 1;
 #pragma unroll
     for (int i = 1; i <= kFull; ++i) {
+        if ((i & (i - 1)) == 0) continue;  // one item: filled from its marginal count
         const unsigned v = __reduce_add_sync(kFullMask, cnt[i]);
         if (lane == 0) {
             int32_t *dst = i == kFull ? supp : sub + (i - 1);
@@ -363,12 +379,21 @@ __global__ void __launch_bounds__(256, 2) splits_kernel(const SupportParams P)
     }
 }
 
-// conf(A => S \ A) = supp(S) / supp(A) for every split, 0 when supp(A) = 0.
+// Finishing pass of the all-splits mode: the one-item antecedents of the
+// unrolled sizes (2..6 items) take their item's marginal count, then
+// conf(A => S \ A) = supp(S) / supp(A) for every split, 0 when supp(A) = 0
+// (confidences only when asked for).
 __global__ void splits_confidence_kernel(const SupportParams P)
 {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < P.nq;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t a = P.split_off[q], b = P.split_off[q + 1];
+        const int32_t i0 = P.set_off[q], k = P.set_off[q + 1] - i0;
+        if (k >= 2 && k <= 6) {
+            for (int t = 0; t < k; ++t)
+                P.sub_support[a + (1 << t) - 1] = (int32_t)P.marg[P.items[i0 + t]];
+        }
+        if (!P.confidence) continue;
         const float s = (float)P.support[q];
         for (int64_t t = a; t < b; ++t) {
             const int32_t d = P.sub_support[t];
@@ -377,13 +402,20 @@ __global__ void splits_confidence_kernel(const SupportParams P)
     }
 }
 
-// conf((S without item t) => item t) = supp(S) / supp(S without item t), 0 when
-// the denominator is 0 (then supp(S) is 0 as well).
+// Finishing pass of the leave-one-out mode: an itemset of two items has
+// one-item leave-one-out sets, whose counts are the items' marginals; then
+// conf((S without item t) => item t) = supp(S) / supp(S without item t), 0
+// when the denominator is 0 (then supp(S) is 0 as well), when asked for.
 __global__ void confidence_kernel(const SupportParams P)
 {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < P.nq;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int32_t a = P.set_off[q], b = P.set_off[q + 1];
+        if (b - a == 2) {
+            P.sub_support[a] = (int32_t)P.marg[P.items[a + 1]];
+            P.sub_support[a + 1] = (int32_t)P.marg[P.items[a]];
+        }
+        if (!P.confidence) continue;
         const float s = (float)P.support[q];
         for (int32_t t = a; t < b; ++t) {
             const int32_t d = P.sub_support[t];

@@ -422,3 +422,52 @@ def test_contexts_on_concurrent_host_threads():
     assert not errors, errors
     for t in range(2):
         assert np.array_equal(got[t], want[t])
+
+
+@pytest.mark.parametrize("nq", [300, 6001])
+def test_pinned_outputs_are_written_by_the_kernels(nq):
+    """A page-locked output buffer whose plan only stores its cells is written
+    by the kernels directly (zero_copy); the tables and scores equal those of
+    the copied path (a numpy buffer, and zero_copy off), padded caller
+    offsets keep the gaps untouched, and a batch that accumulates (forced
+    bitmap strategy) falls back to the copy.  Both the one-part and the
+    two-part (>= 4096 queries) calls are covered."""
+    torch = pytest.importorskip("torch")
+    db = random_dag_database(16, 50_003, 2, 5, 3, 0.5, seed=61)
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    queries = random_queries(db.n, nq, 1, 5, seed=62)
+    off, flat = fc.pack_lists(queries)
+    copied, toff = fc.fc_count_batch(ctx, off, flat)
+    for q in range(0, nq, max(1, nq // 60)):
+        assert np.array_equal(copied[toff[q]:toff[q + 1]].astype(np.int64), orc.table(queries[q]))
+    pinned = torch.full((int(toff[-1]),), -9, dtype=torch.int32).pin_memory()
+    fc.fc_count_batch(ctx, off, flat, toff, out=pinned)
+    assert np.array_equal(pinned.numpy(), copied[: int(toff[-1])])
+    # padded offsets: the cells between tables keep the caller's values
+    cells = np.diff(toff)
+    padded = np.zeros(nq + 1, dtype=np.int64)
+    padded[1:] = np.cumsum(cells + 2)
+    pad_out = torch.full((int(padded[-1]),), -9, dtype=torch.int32).pin_memory()
+    fc.fc_count_batch(ctx, off, flat, padded, out=pad_out)
+    got = pad_out.numpy()
+    for q in range(nq):
+        assert np.array_equal(got[padded[q]:padded[q] + cells[q]], copied[toff[q]:toff[q + 1]])
+        assert np.all(got[padded[q] + cells[q]:padded[q + 1]] == -9)
+    # scores into a page-locked buffer equal the copied ones
+    child = [q[0] for q in queries]
+    po, pa = fc.pack_lists([q[1:] for q in queries])
+    s_copy = fc.fc_score_batch(ctx, child, po, pa, "bdeu", 1.0)
+    s_pin = torch.zeros(nq, dtype=torch.float32).pin_memory()
+    fc.fc_score_batch(ctx, child, po, pa, "bdeu", 1.0, out=s_pin)
+    assert np.array_equal(s_pin.numpy(), s_copy[:nq])
+    # zero_copy off, and an accumulating plan, take the copy path
+    fc.fc_set_option(ctx, "zero_copy", 0)
+    off_out = torch.full((int(toff[-1]),), -9, dtype=torch.int32).pin_memory()
+    fc.fc_count_batch(ctx, off, flat, toff, out=off_out)
+    assert np.array_equal(off_out.numpy(), copied[: int(toff[-1])])
+    fc.fc_set_option(ctx, "zero_copy", 1)
+    fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_BITMAP)
+    bm_out = torch.full((int(toff[-1]),), -9, dtype=torch.int32).pin_memory()
+    fc.fc_count_batch(ctx, off, flat, toff, out=bm_out)
+    assert np.array_equal(bm_out.numpy(), copied[: int(toff[-1])])
