@@ -454,8 +454,10 @@ def roofline(name: str, ms: float, work: dict, pk: dict, resident_bytes: int, pl
              "traffic": traffic,
              "peak_source": "measured by fc_probe_rate(FC_PROBE_AND_POPC) on this GPU: 64-bit AND + popcount + add",
              "work": "one 64-bit AND + popcount per word of every set counted "
-                     + ("(2^k - 1 subsets per itemset)" if name == "splits" else
-                        "(k + 1 sets per itemset: the itemset and its k leave-one-out sets)" if name == "support"
+                     + ("(the 2^k - 1 - k subsets of >= 2 items of each itemset; one-item subsets are the "
+                        "marginals counted at load)" if name == "splits" else
+                        "(the itemset and its k leave-one-out sets; for k = 2 those are single items, whose "
+                        "counts are the marginals counted at load)" if name == "support"
                         else "(the AND of the conditions' state bitmaps)"),
              "duration": "whole step"}
         if resident_bytes > L2_BYTES:
@@ -654,7 +656,10 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
         units = len(w["sets"])
         words = (w["m"] + 63) // 64
         ks = np.diff(so).astype(np.int64)
-        sets_per = (2 ** ks - 1) if splits else (ks + 1)
+        # sets counted per word: one-item sets are the load-time marginals,
+        # so every subset of >= 2 items (splits), or the itemset and its k
+        # leave-one-out sets when those have >= 2 items (supports)
+        sets_per = (2 ** ks - 1 - ks) if splits else np.where(ks == 2, 1, ks + 1)
         work = {"alg_bytes": int(len(it)) * (w["m"] // 8), "popc_words": int(sets_per.sum()) * words}
         pins = tuple(torch.empty(o.numel(), dtype=o.dtype).pin_memory() for o in outs)
         h2d = fc.fc_plan_size(plan, 5)

@@ -189,8 +189,11 @@ int fc_count_assignment_batch(fc_ctx *ctx, int32_t nq, const int32_t *var_off, c
  * or more runs in two parts: the second part is planned while the first
  * one's kernels run, and each part's tables are copied back while the GPU
  * goes on (a bad query in the second part is reported after the first part
- * ran).  `tables` is best in pinned memory (cudaHostAlloc), which the copies
- * can overlap. */
+ * ran).  `tables` is best in pinned memory (cudaHostAlloc): the copies can
+ * overlap it, and a part whose kernels store every cell of its tables (no
+ * cell accumulated; option "zero_copy") writes it directly, with no copy.
+ * Cells between tables (when table_off leaves gaps) are unspecified after
+ * the call. */
 int fc_count_batch(fc_ctx *ctx, int32_t nq, const int32_t *var_off, const int32_t *vars,
                    const int64_t *table_off, int32_t *tables);
 
@@ -198,8 +201,9 @@ int fc_count_batch(fc_ctx *ctx, int32_t nq, const int32_t *var_off, const int32_
  * batches of 4096 or more run in two parts as in fc_count_batch.
  * Query q scores child[q] given parents[par_off[q] .. par_off[q+1]); the
  * child must not be among its parents.  ess is the BDeu equivalent sample
- * size (ignored by the other kinds).  scores: nq float (FP32 result; BDeu is
- * accumulated in FP64 on the device). */
+ * size (ignored by the other kinds).  scores: nq float (FP32 result with
+ * cancellation-free FP32 terms; BDeu's per-query constants, and its terms
+ * for priors of 1 or more, in FP64). */
 int fc_score_batch(fc_ctx *ctx, int32_t nq, const int32_t *child, const int32_t *par_off,
                    const int32_t *parents, int32_t kind, double ess, float *scores);
 

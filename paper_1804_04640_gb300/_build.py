@@ -13,7 +13,7 @@ LIB = os.path.join(OUT_DIR, "libfc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["fc_ctx.cu", "fc_plan.cu", "fc_sets.cu", "fc_pairs_host.cu", "fc_tune.cu", "fc_families.cu",
-           "fc_rules.cu", "fc_count.cu", "fc_sort.cu", "fc_pack.cu", "fc_support.cu", "fc_pairs.cu", "fc_probe.cu"]
+           "fc_rules.cu", "fc_count.cu", "fc_sort.cu", "fc_pack.cu", "fc_support.cu", "fc_pairs.cu", "fc_probe.cu", "fc_dplan.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

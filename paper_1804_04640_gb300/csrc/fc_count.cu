@@ -939,12 +939,13 @@ __global__ void __launch_bounds__(kThreads, kBlocks) count_kernel(const CountPar
     __shared__ ScoreAcc s_red[32];
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int64_t nchunks = (P.m + kChunkRows - 1) / kChunkRows;
+    const int n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
 
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(P.next_item, 1);
         __syncthreads();
         const int it = s_item;
-        if (it >= P.n_items) break;
+        if (it >= n_items) break;
         const Item W = P.items[it];
         const QHead h = P.qh[W.q];
         const int k = h.k;

@@ -301,6 +301,7 @@ extern "C" void fc_free(fc_ctx *c)
         if (ev) cudaEventDestroy(ev);
     for (auto &b : c->io) b.release();
     c->marg_delta.release();
+    c->dplan_buf.release();
     for (auto &b : c->pipe_io) b.release();
     for (auto &bank : c->pool)
         for (auto &b : bank) b.release();

@@ -1,0 +1,441 @@
+// fc_dplan.cu -- planning a large count batch on the device.
+//
+// A synchronous fc_count_batch of thousands of queries spends as long on the
+// host planner (validation, per-query descriptors, strategy choice, work
+// items in longest-first order) as the GPU spends counting.  When every query
+// of a batch is counted in shared memory -- a histogram, a precomputed
+// marginal, or windows of the mixed launch (Sec. 3.3's partitions, keyed and
+// counted on chip) -- the plan is simple enough to build on the device:
+//
+//   dplan_describe   one thread per query: validates it, writes its QVars
+//                    (strides in the caller's order, arity-1 variables
+//                    dropped) and head, picks the strategy with the same cost
+//                    model as the host planner, and counts its work items
+//                    per cost class;
+//   dplan_finish     one CTA: checks the batch-wide conditions of the fast
+//                    path (the small launch shape, no row splits), turns the
+//                    class counts into positions (longest first) and packs
+//                    the table offsets when the caller gave none;
+//   dplan_items      one thread per query: writes its items at its class's
+//                    next positions;
+//
+// then the count kernel runs with its item count read from device memory.
+// A query the fast path does not handle (one the cost model sends to the
+// bitmap strategy, a table beyond the mixed launch's windows, an invalid
+// query) leaves the item count at zero, so nothing is counted, and the host
+// runs the regular planner, which also produces the error messages.
+#include "fc_host.h"
+
+#include <cstring>
+
+namespace fc {
+
+// Result of a device plan, read by the host after the batch ran.
+struct DPlanSummary {
+    int32_t bad;        // nonzero: a query the fast path does not take (or an invalid one)
+    int32_t n_items;    // work items of the count launch (0 when bad)
+    int32_t mid;        // tables the planner's large shape would hold whole (8192 < cells <= 16384)
+    int32_t hist;       // histogram queries
+    int64_t out_cells;  // cells of the packed tables (no caller offsets)
+    int32_t pad[2];
+};
+
+namespace {
+
+constexpr int kClasses = 1 << 14;  // 1/8-octave cost classes (see cost_class)
+
+struct DPlanParams {
+    const int32_t *var_off;   // nq + 1
+    const int32_t *vars;      // the lists from var_off[0] on
+    int32_t base0;            // var_off[0]
+    const int64_t *user_off;  // nq + 1, or null (tables packed in query order)
+    const int32_t *arity, *soff;
+    const double *entropy;
+    int32_t n, nq;
+    double rows, chunks;
+    // cost model (femtoseconds) and the planner's limits
+    double hist_row, hist_var, flush, bitmap_node, bitmap_chunk, small_unit;
+    int32_t bitmap_small, stage_slots, force_hist, window_max;
+    int32_t small_cells;  // table area of the small launch shape
+    int32_t max_cells;    // table area of the large shape
+    int32_t min_hist;     // histogram queries needed for one item per query
+    QHead *qh;
+    QVar *qv;
+    Item *items;
+    uint32_t *cls;
+    int32_t *class_count;  // kClasses
+    int32_t *n_items_eff;  // the count launch's item count
+    DPlanSummary *sum;
+};
+
+__device__ __forceinline__ uint32_t cost_class_dev(double v)
+{
+    if (!(v > 0.0)) v = 0.0;
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    return ((1u << 14) - 1u) - (uint32_t)(b >> (52 - 3));
+}
+
+// Cost of the bitmap strategy for a query of k <= kMaxBitmapK variables (its
+// variables in ascending entropy, as its kernel walks them), or a huge value
+// when the bitmap kernel cannot take it.  Mirrors the host planner's model.
+__device__ double bitmap_cost(const DPlanParams &P, const QVar *v, int k)
+{
+    if (k < 1 || k > kMaxBitmapK) return 1e300;
+    QVar o[kMaxBitmapK];
+    for (int t = 0; t < k; ++t) o[t] = v[t];
+    for (int i = 1; i < k; ++i) {  // stable insertion sort by entropy
+        const QVar x = o[i];
+        const double h = P.entropy[x.var];
+        int j = i - 1;
+        while (j >= 0 && P.entropy[o[j].var] > h) {
+            o[j + 1] = o[j];
+            --j;
+        }
+        o[j + 1] = x;
+    }
+    int slots = 0;
+    for (int t = 1; t < k; ++t) slots += o[t].arity;
+    if (slots > P.stage_slots) return 1e300;
+    auto ok = [](int r) { return r >= 2 && r <= 5; };
+    const bool small = P.bitmap_small && ((k == 2 && ok(o[0].arity) && ok(o[1].arity)) ||
+                                          (k == 3 && ok(o[1].arity) && ok(o[2].arity)));
+    if (small) {
+        const double units = k == 2 ? (double)o[0].arity * o[1].arity + o[0].arity + o[1].arity
+                                    : (double)o[0].arity * (1.0 + o[1].arity + o[2].arity +
+                                                            (double)o[1].arity * o[2].arity);
+        return P.chunks * (P.bitmap_chunk + units * P.small_unit);
+    }
+    double nodes = 0.0, level = 1.0;
+    for (int t = 0; t < k; ++t) {
+        level *= o[t].arity;
+        nodes += level;
+    }
+    return P.chunks * (P.bitmap_chunk + nodes * P.bitmap_node);
+}
+
+__global__ void dplan_describe(const DPlanParams P)
+{
+    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < P.nq; q += gridDim.x * blockDim.x) {
+        const int32_t a = P.var_off[q], b = P.var_off[q + 1];
+        const int32_t k = b - a;
+        // the host planner reports every invalid query; here it only stops the fast path
+        if (a < P.base0 || b > P.var_off[P.nq] || k < 0 || k > P.n || k > 48) {
+            atomicOr(&P.sum->bad, 1);
+            continue;
+        }
+        const int32_t *vars = P.vars + (a - P.base0);
+        int64_t cells = 1;
+        bool bad = false;
+        for (int t = 0; t < k && !bad; ++t) {
+            const int v = vars[t];
+            if (v < 0 || v >= P.n) {
+                bad = true;
+                break;
+            }
+            cells *= P.arity[v];
+            if (cells > INT32_MAX) bad = true;
+            for (int u = 0; u < t; ++u)
+                if (vars[u] == v) bad = true;
+        }
+        const int64_t base = (int64_t)a - P.base0;
+        if (!bad && P.user_off && (P.user_off[q] < 0 || P.user_off[q + 1] - P.user_off[q] < cells)) bad = true;
+        if (bad) {
+            atomicOr(&P.sum->bad, 1);
+            continue;
+        }
+        // QVars: strides of the caller's order (last fastest), arity-1 variables dropped
+        QVar *out = P.qv + base;
+        int64_t stride = 1;
+        int k_eff = 0;
+        for (int t = k - 1; t >= 0; --t)
+            if (P.arity[vars[t]] > 1) ++k_eff;
+        int w = k_eff;
+        for (int t = k - 1; t >= 0; --t) {
+            const int v = vars[t];
+            if (P.arity[v] > 1) out[--w] = QVar{v, (int32_t)stride, P.arity[v], P.soff[v]};
+            stride *= P.arity[v];
+        }
+        // strategy: the cost model of the host planner, in the small launch
+        // shape; only the shared-memory strategies are taken here
+        const double hist = P.rows * (P.hist_row + (double)k_eff * P.hist_var) + (double)cells * P.flush;
+        int s;
+        double cost;
+        int32_t nwin = 1;
+        if (k_eff == 0) {
+            s = kHist;
+            cost = hist;
+        } else if (k_eff == 1 && cells <= P.max_cells) {
+            s = kMarginal;
+            cost = (double)cells * P.flush;
+        } else if (cells <= P.max_cells) {
+            if (!P.force_hist && bitmap_cost(P, out, k_eff) + (double)cells * P.flush < hist) {
+                atomicOr(&P.sum->bad, 2);  // the bitmap strategy: host planner
+                continue;
+            }
+            if (cells <= P.small_cells) {
+                s = kHist;
+                cost = hist;
+            } else {
+                // beyond the small shape's area: windows of it in the same launch
+                atomicAdd(&P.sum->mid, 1);
+                nwin = (int32_t)((cells + P.small_cells - 1) / P.small_cells);
+                if (nwin > P.window_max) {
+                    atomicOr(&P.sum->bad, 4);
+                    continue;
+                }
+                s = kWindow;
+                cost = (double)nwin * P.rows * (P.hist_row + (double)k_eff * P.hist_var) * 2.0 +
+                       (double)cells * P.flush;
+            }
+        } else {
+            atomicOr(&P.sum->bad, 4);  // wide windows, global atomics, sort: host planner
+            continue;
+        }
+        if (s == kHist) atomicAdd(&P.sum->hist, 1);
+        QHead h;
+        h.table_off = P.user_off ? P.user_off[q] : 0;
+        h.cells = (int32_t)cells;
+        h.var_off = (int32_t)base;
+        h.k = (int16_t)k_eff;
+        h.strategy = (int16_t)s;
+        h.nparts = (int16_t)nwin;
+        h.score_kind = (int16_t)kNoScore;
+        h.r_child = 1;
+        h.child_soff = 0;
+        h.score_slot = q;
+        h.nwin = nwin;
+        P.qh[q] = h;
+        const uint32_t cl = cost_class_dev(cost / nwin);
+        P.cls[q] = cl;
+        atomicAdd(&P.class_count[cl], nwin);
+    }
+}
+
+// Exclusive prefix sum of x[0..n) in place by one CTA, each thread a
+// contiguous run, sums in 64 bits; returns the total to every thread.
+template <class T>
+__device__ int64_t block_scan(T *x, int64_t n, int64_t *red)
+{
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = min(n, per * threadIdx.x), hi = min(n, lo + per);
+    int64_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += x[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {  // Hillis-Steele over the run sums
+        const int64_t v = threadIdx.x >= (unsigned)off ? red[threadIdx.x - off] : 0;
+        __syncthreads();
+        red[threadIdx.x] += v;
+        __syncthreads();
+    }
+    const int64_t total = red[blockDim.x - 1];
+    int64_t run = red[threadIdx.x] - s;
+    for (int64_t i = lo; i < hi; ++i) {
+        const int64_t v = x[i];
+        x[i] = (T)run;
+        run += v;
+    }
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(1024) dplan_finish(const DPlanParams P, int64_t *cells_scan)
+{
+    __shared__ int64_t red[1024];
+    __shared__ int s_bad;
+    // the small launch shape holds the batch only when few tables would fit
+    // the large shape whole, and one item per query fills the GPU only with
+    // enough histogram queries (the host planner splits rows otherwise)
+    if (threadIdx.x == 0)
+        s_bad = P.sum->bad || (int64_t)P.sum->mid * 64 > P.nq || P.sum->hist < P.min_hist;
+    __syncthreads();
+    if (s_bad) {
+        if (threadIdx.x == 0) {
+            P.sum->bad |= 8;
+            P.sum->n_items = 0;
+            *P.n_items_eff = 0;
+        }
+        return;
+    }
+    // positions of the classes' items: ascending class = descending cost
+    const int64_t n_items = block_scan<int32_t>(P.class_count, kClasses, red);
+    if (threadIdx.x == 0) {
+        P.sum->n_items = (int32_t)n_items;
+        *P.n_items_eff = (int32_t)n_items;
+    }
+    // packed table offsets in query order when the caller gave none
+    if (!P.user_off) {
+        for (int64_t q = threadIdx.x; q < P.nq; q += blockDim.x) cells_scan[q] = P.qh[q].cells;
+        __syncthreads();
+        const int64_t total = block_scan<int64_t>(cells_scan, P.nq, red);
+        for (int64_t q = threadIdx.x; q < P.nq; q += blockDim.x) P.qh[q].table_off = cells_scan[q];
+        if (threadIdx.x == 0) P.sum->out_cells = total;
+    }
+}
+
+__global__ void dplan_items(const DPlanParams P)
+{
+    if (*P.n_items_eff == 0) return;
+    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < P.nq; q += gridDim.x * blockDim.x) {
+        const int32_t nwin = P.qh[q].nwin;
+        const int32_t pos = atomicAdd(&P.class_count[P.cls[q]], nwin);
+        for (int32_t part = 0; part < nwin; ++part) P.items[pos + part] = Item{q, part};
+    }
+}
+
+}  // namespace
+
+// Plans and runs a count batch on the device (see the top of this file).
+// Returns FC_OK with *done set when the batch was counted, FC_OK with *done
+// clear when the host planner must take it (nothing was written), or an
+// error code.
+int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int32_t *vars,
+                       const int64_t *table_off, int32_t *tables, bool *done)
+{
+    *done = false;
+    const Options &o = c->opt;
+    constexpr int kSmallThreads = 256, kSmallCtas = 6, kSmallCells = 8192;
+    if (!o.device_plan || (o.strategy != FC_STRAT_AUTO && o.strategy != FC_STRAT_HIST) || !o.shape_auto ||
+        !o.window_wide || c->m >= (1 << 19) || c->transactions || nq < 1)
+        return FC_OK;
+    const int32_t nvars = var_off[nq] - var_off[0];
+    if (var_off[0] < 0 || nvars < 0) return FC_OK;
+    const int max_cells = std::max(1, std::min<int>(o.smem_cells, (c->max_smem_optin - 4096) / 4));
+    if (max_cells <= kSmallCells) return FC_OK;
+    const int grid = c->num_sms * kSmallCtas;
+
+    // host inputs into the pinned staging buffer, one upload
+    const size_t b_off = round_up(sizeof(int32_t) * (nq + 1), 256);
+    const size_t b_vars = round_up(sizeof(int32_t) * std::max(nvars, 1), 256);
+    const size_t b_user = table_off ? round_up(sizeof(int64_t) * (nq + 1), 256) : 0;
+    const size_t b_ent = round_up(sizeof(double) * c->n, 256);
+    const size_t in_bytes = b_off + b_vars + b_user + b_ent;
+    uint8_t *h = stage_host(c, in_bytes);
+    if (!h) return FC_OK;
+    std::memcpy(h, var_off, sizeof(int32_t) * (nq + 1));
+    std::memcpy(h + b_off, vars + var_off[0], sizeof(int32_t) * nvars);
+    if (table_off) std::memcpy(h + b_off + b_vars, table_off, sizeof(int64_t) * (nq + 1));
+    std::memcpy(h + b_off + b_vars + b_user, c->entropy.data(), sizeof(double) * c->n);
+
+    // device layout: inputs | heads | QVars | items | classes | class counts |
+    // packed offsets | item count | counter | summary
+    const int64_t max_items = (int64_t)nq * std::min(o.window_max, kMaxWindows);
+    const size_t o_qh = round_up(in_bytes, 256);
+    const size_t o_qv = o_qh + round_up(sizeof(QHead) * nq, 256);
+    const size_t o_it = o_qv + round_up(sizeof(QVar) * std::max(nvars, 1), 256);
+    const size_t o_cl = o_it + round_up(sizeof(Item) * max_items, 256);
+    const size_t o_cc = o_cl + round_up(sizeof(uint32_t) * nq, 256);
+    const size_t o_sc = o_cc + round_up(sizeof(int32_t) * kClasses, 256);
+    const size_t o_ct = o_sc + round_up(sizeof(int64_t) * nq, 256);  // n_items_eff, next item (zeroed)
+    const size_t o_sum = o_ct + 256;
+    const size_t total = o_sum + round_up(sizeof(DPlanSummary), 256);
+    cudaError_t e = c->dplan_buf.ensure(total);
+    if (e != cudaSuccess) return cuda_fail(e, "device plan buffer");
+    uint8_t *d = (uint8_t *)c->dplan_buf.p;
+    e = cudaMemcpyAsync(d, h, in_bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->stage[c->bank].ev, c->stream);
+    // class counts, the item counters and the summary start from zero
+    if (e == cudaSuccess) e = cudaMemsetAsync(d + o_cc, 0, o_sc - o_cc, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d + o_ct, 0, total - o_ct, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "device plan upload");
+
+    DPlanParams P{};
+    P.var_off = (const int32_t *)d;
+    P.vars = (const int32_t *)(d + b_off);
+    P.base0 = var_off[0];
+    P.user_off = table_off ? (const int64_t *)(d + b_off + b_vars) : nullptr;
+    P.entropy = (const double *)(d + b_off + b_vars + b_user);
+    P.arity = c->d_arity;
+    P.soff = c->d_soff;
+    P.n = c->n;
+    P.nq = nq;
+    P.rows = (double)c->m;
+    P.chunks = (double)((c->m + kChunkRows - 1) / kChunkRows);
+    P.hist_row = (double)o.hist_cost_row;
+    P.hist_var = (double)o.hist_cost_var;
+    P.flush = (double)o.flush_cost;
+    P.bitmap_node = (double)o.bitmap_cost;
+    P.bitmap_chunk = (double)o.bitmap_chunk_cost;
+    P.small_unit = (double)o.small_cost;
+    P.bitmap_small = o.bitmap_small;
+    P.stage_slots = std::max(1, std::min(o.stage_slots, (c->max_smem_optin - 1024) /
+                                                            (16 * std::max(32, std::min(256, o.bitmap_threads / 32 * 32)))));
+    P.force_hist = o.strategy == FC_STRAT_HIST;
+    P.window_max = std::min(o.window_max, kMaxWindows);
+    P.small_cells = kSmallCells;
+    P.max_cells = max_cells;
+    P.min_hist = grid * 4;
+    P.qh = (QHead *)(d + o_qh);
+    P.qv = (QVar *)(d + o_qv);
+    P.items = (Item *)(d + o_it);
+    P.cls = (uint32_t *)(d + o_cl);
+    P.class_count = (int32_t *)(d + o_cc);
+    P.n_items_eff = (int32_t *)(d + o_ct);
+    P.sum = (DPlanSummary *)(d + o_sum);
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((nq + threads - 1) / threads, (int64_t)c->num_sms * 8);
+    dplan_describe<<<blocks, threads, 0, c->stream>>>(P);
+    dplan_finish<<<1, 1024, 0, c->stream>>>(P, (int64_t *)(d + o_sc));
+    dplan_items<<<blocks, threads, 0, c->stream>>>(P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "device plan launch");
+
+    // the count launch in the small shape; its item count comes from the planner
+    void *direct = o.zero_copy && table_off ? device_view(tables, sizeof(int32_t) * (size_t)table_off[nq]) : nullptr;
+    const size_t out_bytes = table_off ? sizeof(int32_t) * (size_t)table_off[nq] : 0;
+    int32_t *dtab = (int32_t *)direct;
+    if (!dtab) {
+        if (!table_off) {
+            // the packed size is known only after planning: read the summary first
+            DPlanSummary s{};
+            e = cudaMemcpyAsync(&s, P.sum, sizeof s, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "device plan summary");
+            if (s.bad || s.n_items == 0) return FC_OK;
+            e = c->io[0].ensure(sizeof(int32_t) * std::max<int64_t>(s.out_cells, 1));
+            if (e != cudaSuccess) return cuda_fail(e, "output buffer");
+            dtab = (int32_t *)c->io[0].p;
+        } else {
+            e = c->io[0].ensure(std::max<size_t>(out_bytes, 4));
+            if (e != cudaSuccess) return cuda_fail(e, "output buffer");
+            dtab = (int32_t *)c->io[0].p;
+        }
+    }
+    CountParams C{};
+    C.D = c->d_D;
+    C.m_pad = c->m_pad;
+    C.m = c->m;
+    C.bits = c->d_bits;
+    C.wstride = c->wstride;
+    C.qh = P.qh;
+    C.qv = P.qv;
+    C.items = P.items;
+    C.n_items = INT32_MAX;  // bounded by *n_items_dev
+    C.n_items_dev = P.n_items_eff;
+    C.next_item = P.n_items_eff + 1;
+    C.tables = dtab;
+    C.marg = c->d_marg;
+    C.ess = 1.0;
+    C.write_tables = 1;
+    C.smem_cells = kSmallCells;
+    C.hist_copies = o.hist_copies;
+    C.small_paths = o.bitmap_small;
+    e = launch_count(C, grid, kSmallThreads, (size_t)kSmallCells * 4, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "count launch");
+    DPlanSummary s{};
+    e = cudaMemcpyAsync(&s, P.sum, sizeof s, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "device plan run");
+    if (s.bad || s.n_items == 0) return FC_OK;
+    if (!direct) {
+        const size_t bytes = table_off ? out_bytes : sizeof(int32_t) * (size_t)s.out_cells;
+        if (bytes > 0) {
+            e = cudaMemcpyAsync(tables, dtab, bytes, cudaMemcpyDeviceToHost, c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "copy outputs");
+        }
+    }
+    const int rc = read_status(c, c->stream);
+    if (rc == FC_OK) *done = true;
+    return rc;
+}
+
+}  // namespace fc

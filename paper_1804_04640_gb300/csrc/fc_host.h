@@ -90,7 +90,6 @@ struct Options {
     int32_t hist_copies = 4;
     int64_t min_part_rows = 8192;
     int64_t pair_chunk_rows = 1 << 16;
-    int32_t pair_producer_warps = 16; // warps of the all-pairs kernel that build operands (16, 24, 31)
     int32_t use_graph = 1;
     int64_t wait_limit = 1 << 22;
     int64_t sort_min_cells = 1 << 25;
@@ -117,6 +116,9 @@ struct Options {
     // host memory let the kernels store into it directly (no device buffer,
     // no copy) when no output cell is accumulated
     int32_t zero_copy = 1;
+    // large count batches whose queries all count in shared memory are
+    // planned on the device (fc_dplan.cu)
+    int32_t device_plan = 1;
 };
 
 // Host arrays of the count planner, kept by the context between plan builds
@@ -217,6 +219,7 @@ struct fc_ctx {
     // scratch of the host-buffer entry points
     fc::DBuf io[3];
     fc::DBuf marg_delta;     // marginal counts of the instances an append adds (R int64)
+    fc::DBuf dplan_buf;      // inputs, descriptors and items of device-planned batches
     std::vector<int64_t> h_marg_delta;
     // buffers lent to one-shot plans (descriptors, counters, tables, sort,
     // pairs), in two banks so that a synchronous call can have a plan
@@ -233,8 +236,6 @@ struct fc_ctx {
     uint32_t epoch = 0;
     uint64_t generation = 0;  // bumped by every append; plans of older generations refuse to run
     std::vector<fc_plan *> live_plans;  // orphaned (device memory released) if the context goes first
-    // pinned staging of plan descriptors: written on the host, copied by DMA;
-    // the event marks the end of the last copy out of it
     // pinned staging of plan descriptors, one per bank; `ev` marks the end
     // of the last upload from it
     struct Stage {
@@ -352,6 +353,14 @@ struct BorrowScope {
 // descriptors, free of any copy still reading it; nullptr on failure
 // (fc_ctx.cu).
 uint8_t *stage_host(fc_ctx *c, size_t bytes);
+// A count batch planned and counted on the device when every query counts in
+// shared memory (fc_dplan.cu); *done is clear when the host planner must
+// take the batch.
+int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int32_t *vars,
+                       const int64_t *table_off, int32_t *tables, bool *done);
+// Device address of a page-locked host buffer the kernels can store to, or
+// nullptr (fc_plan.cu).
+void *device_view(const void *h, size_t bytes);
 // Grows the staging buffer to `bytes`, keeping its first `keep` bytes.
 uint8_t *stage_grow(fc_ctx *c, size_t bytes, size_t keep);
 // Copies `bytes` of the staging buffer to dst on the context stream and marks

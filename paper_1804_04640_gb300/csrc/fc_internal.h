@@ -72,6 +72,7 @@ struct CountParams {
     const QVar *qv;
     const Item *items;
     int32_t n_items;
+    const int32_t *n_items_dev;  // if set, the item count is read here (a plan built on the device)
     int32_t *next_item;      // work counter, zero before the launch
     int32_t *tables;         // table buffer (output, or plan scratch for scores)
     int32_t *tickets;        // per query, zero before the launch (nparts > 1 scoring)
@@ -190,7 +191,9 @@ constexpr int kMaxSplitK = 16;  // itemset size limit of the all-splits mode
 cudaError_t launch_support(const SupportParams &p, int grid, int threads, size_t smem,
                            cudaStream_t s);
 cudaError_t launch_support_confidence(const SupportParams &p, cudaStream_t s);
-const void *support_kernel_ptr(int mode);  // 0 leave-one-out, 1 full only, 2 all splits
+// 0 leave-one-out, 1 full only, 2 all splits (the instantiation that runs
+// `threads` threads per CTA)
+const void *support_kernel_ptr(int mode, int threads);
 
 // All-pairs one-hot co-occurrence on tcgen05 tensor cores.
 //
@@ -220,7 +223,6 @@ struct PairsParams {
     int32_t nregions;
     const PairsRegion *regions;  // device array, cta0 ascending
     int32_t grid;            // CTAs of the launch (sum of the regions' ksplit)
-    int32_t producer_warps;  // warps expanding operands: 16, 24 or 31
     int32_t *status;
     int64_t wait_limit;
 };

@@ -45,6 +45,9 @@ constexpr int kN = 256;                      // columns of one MMA
 constexpr int kRegion = 256;                 // a CTA's region of C is kRegion x kRegion
 constexpr int kKStage = 128;                 // instances per stage = bytes per operand row
 constexpr int kStages = 3;
+constexpr int kProducerWarps = 16;
+constexpr int kProducers = kProducerWarps * 32;
+constexpr int kThreads = kProducers + 32;    // + the MMA / TMEM warp
 constexpr int kABytes = kRegion * kKStage;   // two A halves of 128 rows, 32 KiB
 constexpr int kBBytes = kN * kKStage;        // 32 KiB
 constexpr int kStageBytes = kABytes + kBBytes;
@@ -144,13 +147,8 @@ __device__ __forceinline__ void store_row_word(uint8_t *tile, int row, int half,
     }
 }
 
-// PW producer warps expand the operands; warp PW issues the MMAs and owns
-// the tensor memory; warps 0..3 also read the accumulators back.
-template <int PW>
-__global__ void __launch_bounds__(PW * 32 + 32, 1) pairs_gemm_kernel(const PairsParams P)
+__global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsParams P)
 {
-    constexpr int kProducerWarps = PW;
-    constexpr int kProducers = kProducerWarps * 32;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = (uint64_t *)(smem + kStages * kStageBytes);  // full[S], empty[S], acc
@@ -393,24 +391,13 @@ __global__ void wait_selftest_kernel(int32_t *status, int64_t limit)
 
 }  // namespace
 
-template <int PW>
-cudaError_t launch_pairs_pw(const PairsParams &p, cudaStream_t s)
-{
-    cudaError_t e = cudaFuncSetAttribute(pairs_gemm_kernel<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemBytes);
-    if (e != cudaSuccess) return e;
-    pairs_gemm_kernel<PW><<<p.grid, PW * 32 + 32, kSmemBytes, s>>>(p);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_pairs_gemm(const PairsParams &p, cudaStream_t s)
 {
     if (p.R_pad % kRegion != 0 || p.nregions < 1 || p.grid < 1) return cudaErrorInvalidValue;
-    switch (p.producer_warps) {
-    case 24: return launch_pairs_pw<24>(p, s);
-    case 31: return launch_pairs_pw<31>(p, s);
-    default: return launch_pairs_pw<16>(p, s);
-    }
+    cudaError_t e = cudaFuncSetAttribute(pairs_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    pairs_gemm_kernel<<<p.grid, kThreads, kSmemBytes, s>>>(p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pairs_extract(const int32_t *C, int32_t R_pad, int32_t n, const int32_t *d_arity,

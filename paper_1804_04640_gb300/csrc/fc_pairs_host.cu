@@ -134,7 +134,6 @@ extern "C" int fc_plan_pairs(fc_ctx *c, fc_plan **out)
     P.nregions = (int32_t)regs.size();
     P.regions = (const PairsRegion *)((uint8_t *)p->pairs_meta.p + reg_off);
     P.grid = (int32_t)cta;
-    P.producer_warps = c->opt.pair_producer_warps;
     P.chunk_words = (int32_t)chunk_words;
     P.wait_limit = c->opt.wait_limit;
     *out = p;

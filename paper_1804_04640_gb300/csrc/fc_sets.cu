@@ -100,7 +100,7 @@ int support_ctas_per_sm(int mode, int threads)
         if (cache[dev][mode][ti] > 0) return cache[dev][mode][ti];
     }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, support_kernel_ptr(mode), threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, support_kernel_ptr(mode, threads), threads, 0);
     per_sm = std::max(1, per_sm);
     if (dev >= 0 && dev < 64 && mode >= 0 && mode < 3) {
         std::lock_guard<std::mutex> lk(mu);
@@ -202,6 +202,9 @@ int build_set_plan(fc_ctx *c, int32_t nq, const int32_t *set_off, const int32_t 
     int64_t nparts = std::max<int64_t>(1, (c->words + part_words - 1) / part_words);
     const int64_t want = (2 * (int64_t)p->sup_grid + ngroups - 1) / ngroups;
     nparts = std::max(nparts, std::min(want, std::max<int64_t>(1, (c->words + 63) / 64)));
+    // the all-splits kernel keeps 16-bit counts per lane: a work item spans
+    // at most 511 steps of 64 words
+    if (mode == 2) nparts = std::max<int64_t>(nparts, (c->words + 511 * 64 - 1) / (511 * 64));
     P.nparts = (int32_t)std::min<int64_t>(nparts, 1 << 20);
     P.words_per_part = (int32_t)round_up((c->words + P.nparts - 1) / P.nparts, 64);
     *out = p;

