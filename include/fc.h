@@ -189,9 +189,11 @@ int fc_count_assignment_batch(fc_ctx *ctx, int32_t nq, const int32_t *var_off, c
  * or more runs in two parts: the second part is planned while the first
  * one's kernels run, and each part's tables are copied back while the GPU
  * goes on (a bad query in the second part is reported after the first part
- * ran).  `tables` is best in pinned memory (cudaHostAlloc): the copies can
- * overlap it, and a part whose kernels store every cell of its tables (no
- * cell accumulated; option "zero_copy") writes it directly, with no copy.
+ * ran); batches whose queries all count in shared memory are planned on the
+ * device instead (option "device_plan").  `tables` is best in pinned memory
+ * (cudaHostAlloc): the copies can overlap it, and a part whose kernels store
+ * every cell of its tables (no cell accumulated; option "zero_copy") writes
+ * it directly, with no copy.
  * Cells between tables (when table_off leaves gaps) are unspecified after
  * the call. */
 int fc_count_batch(fc_ctx *ctx, int32_t nq, const int32_t *var_off, const int32_t *vars,
@@ -426,7 +428,13 @@ int fc_sync(fc_ctx *ctx, void *stream);
  *                       mapping) and no output cell is accumulated, the
  *                       kernels store the outputs into it directly instead
  *                       of into a device buffer that is copied afterwards;
- *                       0 = always copy. */
+ *                       0 = always copy
+ *   "device_plan"       1 (default) = an fc_count_batch of 4096 queries or
+ *                       more whose queries all count in shared memory (on a
+ *                       database of fewer than 2^19 instances) is planned on
+ *                       the device (validation, strategy, work order); any
+ *                       other batch, or an invalid one, is planned on the
+ *                       host, which reports the error; 0 = always the host. */
 int fc_set_option(fc_ctx *ctx, const char *key, int64_t value);
 
 /* Current value of an option (or -1 for an unknown key). */
