@@ -485,6 +485,10 @@ def roofline(name: str, ms: float, work: dict, pk: dict, resident_bytes: int, pl
                          "queries; its time is in the denominator, its work is not")
         if name == "tiny":
             r["note"] = "launch- and latency-bound: 92 queries of 1,000 instances"
+        if name == "large":
+            r["note"] = ("tables beyond shared memory, counted window by window: every row is keyed once per "
+                         "window and only the keys inside it are counted, so the launch is bound by the key "
+                         "arithmetic (ALU), not by the atomics this fraction counts")
         return r
     # families, rules, append: byte-bound work
     achieved = work["alg_bytes"] / sec / 1e9

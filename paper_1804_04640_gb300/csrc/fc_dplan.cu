@@ -383,6 +383,7 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
     void *direct = o.zero_copy && table_off ? device_view(tables, sizeof(int32_t) * (size_t)table_off[nq]) : nullptr;
     const size_t out_bytes = table_off ? sizeof(int32_t) * (size_t)table_off[nq] : 0;
     int32_t *dtab = (int32_t *)direct;
+    int64_t known_cells = 0;
     if (!dtab) {
         if (!table_off) {
             // the packed size is known only after planning: read the summary first
@@ -391,6 +392,7 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             if (e != cudaSuccess) return cuda_fail(e, "device plan summary");
             if (s.bad || s.n_items == 0) return FC_OK;
+            known_cells = s.out_cells;
             e = c->io[0].ensure(sizeof(int32_t) * std::max<int64_t>(s.out_cells, 1));
             if (e != cudaSuccess) return cuda_fail(e, "output buffer");
             dtab = (int32_t *)c->io[0].p;
@@ -421,21 +423,24 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
     C.small_paths = o.bitmap_small;
     e = launch_count(C, grid, kSmallThreads, (size_t)kSmallCells * 4, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "count launch");
+    // the outputs (when they are not stored in place), the summary and the
+    // status word come back together, after one synchronisation; a batch
+    // the fast path refused leaves the caller's buffer to the host planner's run
+    if (!direct) {
+        const size_t bytes = table_off ? out_bytes : sizeof(int32_t) * (size_t)known_cells;
+        if (bytes > 0) e = cudaMemcpyAsync(tables, dtab, bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copy outputs");
+    }
     DPlanSummary s{};
+    int32_t st[2] = {0, 0};
     e = cudaMemcpyAsync(&s, P.sum, sizeof s, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st, c->d_status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "device plan run");
+    if (st[0] != kStatusOk) return read_status(c, c->stream);  // reports (and clears) the status
     if (s.bad || s.n_items == 0) return FC_OK;
-    if (!direct) {
-        const size_t bytes = table_off ? out_bytes : sizeof(int32_t) * (size_t)s.out_cells;
-        if (bytes > 0) {
-            e = cudaMemcpyAsync(tables, dtab, bytes, cudaMemcpyDeviceToHost, c->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "copy outputs");
-        }
-    }
-    const int rc = read_status(c, c->stream);
-    if (rc == FC_OK) *done = true;
-    return rc;
+    *done = true;
+    return FC_OK;
 }
 
 }  // namespace fc
