@@ -3,8 +3,9 @@
 Each test builds its workload with bench.make_workload, plans it the way the
 benchmark does (batch autotuner, device-resident plan, CUDA-graph replay on a
 side stream, twice) and compares with the oracle: every table of the
-10,000-query batch, and seeded samples (plus properties that hold at any size)
-for the larger workloads.
+10,000-query batch (also through the end-to-end call the bench times), and
+seeded samples (plus properties that hold at any size) for the larger
+workloads.
 """
 import concurrent.futures as cf
 import os
@@ -58,6 +59,15 @@ def test_random_batch_as_benchmarked():
     want = _pool_map(orc.table, queries)
     for q, t in enumerate(want):
         assert np.array_equal(tables[toff[q]:toff[q + 1]].astype(np.int64), t), q
+    # the end-to-end call the bench times: host lists, the device planner,
+    # tables stored straight into a page-locked buffer, twice in a row
+    pinned = torch.empty(int(toff[-1]), dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        pinned.fill_(-1)
+        fc.fc_count_batch(ctx, off, flat, toff, out=pinned)
+        got = pinned.numpy()
+        for q, t in enumerate(want):
+            assert np.array_equal(got[toff[q]:toff[q + 1]].astype(np.int64), t), q
 
 
 def test_scores_batch_as_benchmarked():
