@@ -26,6 +26,7 @@
 // runs the regular planner, which also produces the error messages.
 #include "fc_host.h"
 
+#include <cstddef>
 #include <cstring>
 
 namespace fc {
@@ -37,7 +38,8 @@ struct DPlanSummary {
     int32_t mid;        // tables the planner's large shape would hold whole (8192 < cells <= 16384)
     int32_t hist;       // histogram queries
     int64_t out_cells;  // cells of the packed tables (no caller offsets)
-    int32_t pad[2];
+    uint32_t cls_lo;    // span of the cost classes present (set to [max, 0] before planning)
+    uint32_t cls_hi;
 };
 
 namespace {
@@ -59,6 +61,7 @@ struct DPlanParams {
     int32_t small_cells;  // table area of the small launch shape
     int32_t max_cells;    // table area of the large shape
     int32_t min_hist;     // histogram queries needed for one item per query
+    int32_t stage_vars;   // 1: dplan_describe stages the variables' tables in shared memory
     QHead *qh;
     QVar *qv;
     Item *items;
@@ -66,6 +69,13 @@ struct DPlanParams {
     int32_t *class_count;  // kClasses
     int32_t *n_items_eff;  // the count launch's item count
     DPlanSummary *sum;
+};
+
+// The variables' arity, state offset and entropy, staged in shared memory
+// for the CTA (the per-query loops look them up once per variable).
+struct VarInfo {
+    int32_t arity, soff;
+    double entropy;
 };
 
 __device__ __forceinline__ uint32_t cost_class_dev(double v)
@@ -78,16 +88,26 @@ __device__ __forceinline__ uint32_t cost_class_dev(double v)
 // Cost of the bitmap strategy for a query of k <= kMaxBitmapK variables (its
 // variables in ascending entropy, as its kernel walks them), or a huge value
 // when the bitmap kernel cannot take it.  Mirrors the host planner's model.
-__device__ double bitmap_cost(const DPlanParams &P, const QVar *v, int k)
+__device__ __forceinline__ int arity_of(const DPlanParams &P, const VarInfo *sv, int v)
+{
+    return P.stage_vars ? sv[v].arity : P.arity[v];
+}
+
+__device__ __forceinline__ double entropy_of(const DPlanParams &P, const VarInfo *sv, int v)
+{
+    return P.stage_vars ? sv[v].entropy : P.entropy[v];
+}
+
+__device__ double bitmap_cost(const DPlanParams &P, const VarInfo *sv, const QVar *v, int k)
 {
     if (k < 1 || k > kMaxBitmapK) return 1e300;
     QVar o[kMaxBitmapK];
     for (int t = 0; t < k; ++t) o[t] = v[t];
     for (int i = 1; i < k; ++i) {  // stable insertion sort by entropy
         const QVar x = o[i];
-        const double h = P.entropy[x.var];
+        const double h = entropy_of(P, sv, x.var);
         int j = i - 1;
-        while (j >= 0 && P.entropy[o[j].var] > h) {
+        while (j >= 0 && entropy_of(P, sv, o[j].var) > h) {
             o[j + 1] = o[j];
             --j;
         }
@@ -113,141 +133,185 @@ __device__ double bitmap_cost(const DPlanParams &P, const QVar *v, int k)
     return P.chunks * (P.bitmap_chunk + nodes * P.bitmap_node);
 }
 
-__global__ void dplan_describe(const DPlanParams P)
+// One query: validation, QVars, head and strategy.  Returns 0 and sets
+// *cls / *nwin for a query the fast path takes, else the reason bit for the
+// summary (1 invalid, 2 bitmap strategy, 4 beyond the mixed launch's windows).
+__device__ int describe_one(const DPlanParams &P, const VarInfo *s_var, int32_t q, uint32_t *cls, int32_t *nwin_out,
+                            bool *is_hist, bool *is_mid)
 {
-    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < P.nq; q += gridDim.x * blockDim.x) {
-        const int32_t a = P.var_off[q], b = P.var_off[q + 1];
-        const int32_t k = b - a;
-        // the host planner reports every invalid query; here it only stops the fast path
-        if (a < P.base0 || b > P.var_off[P.nq] || k < 0 || k > P.n || k > 48) {
-            atomicOr(&P.sum->bad, 1);
-            continue;
-        }
-        const int32_t *vars = P.vars + (a - P.base0);
-        int64_t cells = 1;
-        bool bad = false;
-        for (int t = 0; t < k && !bad; ++t) {
-            const int v = vars[t];
-            if (v < 0 || v >= P.n) {
-                bad = true;
-                break;
-            }
-            cells *= P.arity[v];
-            if (cells > INT32_MAX) bad = true;
-            for (int u = 0; u < t; ++u)
-                if (vars[u] == v) bad = true;
-        }
-        const int64_t base = (int64_t)a - P.base0;
-        if (!bad && P.user_off && (P.user_off[q] < 0 || P.user_off[q + 1] - P.user_off[q] < cells)) bad = true;
-        if (bad) {
-            atomicOr(&P.sum->bad, 1);
-            continue;
-        }
-        // QVars: strides of the caller's order (last fastest), arity-1 variables dropped
-        QVar *out = P.qv + base;
-        int64_t stride = 1;
-        int k_eff = 0;
-        for (int t = k - 1; t >= 0; --t)
-            if (P.arity[vars[t]] > 1) ++k_eff;
-        int w = k_eff;
-        for (int t = k - 1; t >= 0; --t) {
-            const int v = vars[t];
-            if (P.arity[v] > 1) out[--w] = QVar{v, (int32_t)stride, P.arity[v], P.soff[v]};
-            stride *= P.arity[v];
-        }
-        // strategy: the cost model of the host planner, in the small launch
-        // shape; only the shared-memory strategies are taken here
-        const double hist = P.rows * (P.hist_row + (double)k_eff * P.hist_var) + (double)cells * P.flush;
-        int s;
-        double cost;
-        int32_t nwin = 1;
-        if (k_eff == 0) {
+    const int32_t a = P.var_off[q], b = P.var_off[q + 1];
+    const int32_t k = b - a;
+    // the host planner reports every invalid query; here it only stops the fast path
+    if (a < P.base0 || b > P.var_off[P.nq] || k < 0 || k > P.n || k > 48) return 1;
+    const int32_t *vars = P.vars + (a - P.base0);
+    int64_t cells = 1;
+    for (int t = 0; t < k; ++t) {
+        const int v = vars[t];
+        if (v < 0 || v >= P.n) return 1;
+        cells *= arity_of(P, s_var, v);
+        if (cells > INT32_MAX) return 1;
+        for (int u = 0; u < t; ++u)
+            if (vars[u] == v) return 1;
+    }
+    const int64_t base = (int64_t)a - P.base0;
+    if (P.user_off && (P.user_off[q] < 0 || P.user_off[q + 1] - P.user_off[q] < cells)) return 1;
+    // QVars: strides of the caller's order (last fastest), arity-1 variables dropped
+    QVar *out = P.qv + base;
+    int64_t stride = 1;
+    int k_eff = 0;
+    for (int t = k - 1; t >= 0; --t)
+        if (arity_of(P, s_var, vars[t]) > 1) ++k_eff;
+    int w = k_eff;
+    for (int t = k - 1; t >= 0; --t) {
+        const int v = vars[t];
+        const int r = arity_of(P, s_var, v);
+        if (r > 1) out[--w] = QVar{v, (int32_t)stride, r, P.stage_vars ? s_var[v].soff : P.soff[v]};
+        stride *= r;
+    }
+    // strategy: the cost model of the host planner, in the small launch
+    // shape; only the shared-memory strategies are taken here
+    const double hist = P.rows * (P.hist_row + (double)k_eff * P.hist_var) + (double)cells * P.flush;
+    int s;
+    double cost;
+    int32_t nwin = 1;
+    if (k_eff == 0) {
+        s = kHist;
+        cost = hist;
+    } else if (k_eff == 1 && cells <= P.max_cells) {
+        s = kMarginal;
+        cost = (double)cells * P.flush;
+    } else if (cells <= P.max_cells) {
+        if (!P.force_hist && bitmap_cost(P, s_var, out, k_eff) + (double)cells * P.flush < hist) return 2;
+        if (cells <= P.small_cells) {
             s = kHist;
             cost = hist;
-        } else if (k_eff == 1 && cells <= P.max_cells) {
-            s = kMarginal;
-            cost = (double)cells * P.flush;
-        } else if (cells <= P.max_cells) {
-            if (!P.force_hist && bitmap_cost(P, out, k_eff) + (double)cells * P.flush < hist) {
-                atomicOr(&P.sum->bad, 2);  // the bitmap strategy: host planner
-                continue;
-            }
-            if (cells <= P.small_cells) {
-                s = kHist;
-                cost = hist;
-            } else {
-                // beyond the small shape's area: windows of it in the same launch
-                atomicAdd(&P.sum->mid, 1);
-                nwin = (int32_t)((cells + P.small_cells - 1) / P.small_cells);
-                if (nwin > P.window_max) {
-                    atomicOr(&P.sum->bad, 4);
-                    continue;
-                }
-                s = kWindow;
-                cost = (double)nwin * P.rows * (P.hist_row + (double)k_eff * P.hist_var) * 2.0 +
-                       (double)cells * P.flush;
-            }
         } else {
-            atomicOr(&P.sum->bad, 4);  // wide windows, global atomics, sort: host planner
-            continue;
+            // beyond the small shape's area: windows of it in the same launch
+            *is_mid = true;
+            nwin = (int32_t)((cells + P.small_cells - 1) / P.small_cells);
+            if (nwin > P.window_max) return 4;
+            s = kWindow;
+            cost = (double)nwin * P.rows * (P.hist_row + (double)k_eff * P.hist_var) * 2.0 + (double)cells * P.flush;
         }
-        if (s == kHist) atomicAdd(&P.sum->hist, 1);
-        QHead h;
-        h.table_off = P.user_off ? P.user_off[q] : 0;
-        h.cells = (int32_t)cells;
-        h.var_off = (int32_t)base;
-        h.k = (int16_t)k_eff;
-        h.strategy = (int16_t)s;
-        h.nparts = (int16_t)nwin;
-        h.score_kind = (int16_t)kNoScore;
-        h.r_child = 1;
-        h.child_soff = 0;
-        h.score_slot = q;
-        h.nwin = nwin;
-        P.qh[q] = h;
-        const uint32_t cl = cost_class_dev(cost / nwin);
-        P.cls[q] = cl;
-        atomicAdd(&P.class_count[cl], nwin);
+    } else {
+        return 4;  // wide windows, global atomics, sort: host planner
+    }
+    *is_hist = s == kHist;
+    QHead h;
+    h.table_off = P.user_off ? P.user_off[q] : 0;
+    h.cells = (int32_t)cells;
+    h.var_off = (int32_t)base;
+    h.k = (int16_t)k_eff;
+    h.strategy = (int16_t)s;
+    h.nparts = (int16_t)nwin;
+    h.score_kind = (int16_t)kNoScore;
+    h.r_child = 1;
+    h.child_soff = 0;
+    h.score_slot = q;
+    h.nwin = nwin;
+    P.qh[q] = h;
+    *cls = cost_class_dev(cost / nwin);
+    P.cls[q] = *cls;
+    *nwin_out = nwin;
+    return 0;
+}
+
+// A thread per query; the counts a warp adds to the summary go out as one
+// atomic per warp.
+__global__ void __launch_bounds__(128) dplan_describe(DPlanParams P)
+{
+    extern __shared__ VarInfo s_var[];
+    if (P.stage_vars) {
+        for (int v = threadIdx.x; v < P.n; v += blockDim.x) s_var[v] = VarInfo{P.arity[v], P.soff[v], P.entropy[v]};
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    uint32_t lo = 0xFFFFFFFFu, hi = 0u;  // cost classes this thread saw
+    int bad = 0, n_hist = 0, n_mid = 0;
+    for (int32_t q0 = blockIdx.x * blockDim.x; q0 < P.nq; q0 += gridDim.x * blockDim.x) {
+        const int32_t q = q0 + threadIdx.x;
+        uint32_t cl = 0xFFFFFFFFu;
+        int32_t nwin = 0;
+        bool is_hist = false, is_mid = false;
+        if (q < P.nq) {
+            const int why = describe_one(P, s_var, q, &cl, &nwin, &is_hist, &is_mid);
+            if (why) {
+                bad |= why;
+                cl = 0xFFFFFFFFu;
+                nwin = 0;
+                is_hist = false;
+            }
+        }
+        n_hist += is_hist;
+        n_mid += is_mid;
+        if (cl != 0xFFFFFFFFu) {
+            lo = min(lo, cl);
+            hi = max(hi, cl);
+            atomicAdd(&P.class_count[cl], nwin);
+        }
+    }
+    // the warp's summary: fast-path refusals, counts, the span of classes
+    bad = __reduce_or_sync(0xffffffffu, (unsigned)bad);
+    n_hist = __reduce_add_sync(0xffffffffu, (unsigned)n_hist);
+    n_mid = __reduce_add_sync(0xffffffffu, (unsigned)n_mid);
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) {
+        if (bad) atomicOr(&P.sum->bad, bad);
+        if (n_hist) atomicAdd(&P.sum->hist, n_hist);
+        if (n_mid) atomicAdd(&P.sum->mid, n_mid);
+        if (lo <= hi) {
+            atomicMin(&P.sum->cls_lo, lo);
+            atomicMax(&P.sum->cls_hi, hi);
+        }
     }
 }
 
-// Exclusive prefix sum of x[0..n) in place by one CTA, each thread a
-// contiguous run, sums in 64 bits; returns the total to every thread.
+// Exclusive prefix sum of x[0..n) in place by one CTA of 1024 threads, in
+// coalesced tiles of 1024 (warp shuffles, then the warps' sums), sums in 64
+// bits; returns the total to every thread.
 template <class T>
-__device__ int64_t block_scan(T *x, int64_t n, int64_t *red)
+__device__ int64_t block_scan(T *x, int64_t n, int64_t *warp_sum)
 {
-    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
-    const int64_t lo = min(n, per * threadIdx.x), hi = min(n, lo + per);
-    int64_t s = 0;
-    for (int64_t i = lo; i < hi; ++i) s += x[i];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {  // Hillis-Steele over the run sums
-        const int64_t v = threadIdx.x >= (unsigned)off ? red[threadIdx.x - off] : 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t carry = 0;
+    for (int64_t t0 = 0; t0 < n; t0 += blockDim.x) {
+        const int64_t i = t0 + threadIdx.x;
+        const int64_t v = i < n ? (int64_t)x[i] : 0;
+        int64_t incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) warp_sum[warp] = incl;
         __syncthreads();
-        red[threadIdx.x] += v;
+        if (warp == 0) {
+            int64_t w = lane < (int)(blockDim.x >> 5) ? warp_sum[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t u = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += u;
+            }
+            warp_sum[lane] = w;  // inclusive over the warps
+        }
+        __syncthreads();
+        const int64_t before = carry + (warp > 0 ? warp_sum[warp - 1] : 0) + incl - v;
+        if (i < n) x[i] = (T)before;
+        carry += warp_sum[(blockDim.x >> 5) - 1];
         __syncthreads();
     }
-    const int64_t total = red[blockDim.x - 1];
-    int64_t run = red[threadIdx.x] - s;
-    for (int64_t i = lo; i < hi; ++i) {
-        const int64_t v = x[i];
-        x[i] = (T)run;
-        run += v;
-    }
-    __syncthreads();
-    return total;
+    return carry;
 }
 
 __global__ void __launch_bounds__(1024) dplan_finish(const DPlanParams P, int64_t *cells_scan)
 {
-    __shared__ int64_t red[1024];
+    __shared__ int64_t warp_sum[32];
     __shared__ int s_bad;
     // the small launch shape holds the batch only when few tables would fit
     // the large shape whole, and one item per query fills the GPU only with
     // enough histogram queries (the host planner splits rows otherwise)
     if (threadIdx.x == 0)
-        s_bad = P.sum->bad || (int64_t)P.sum->mid * 64 > P.nq || P.sum->hist < P.min_hist;
+        s_bad = P.sum->bad || (int64_t)P.sum->mid * 64 > P.nq || P.sum->hist < P.min_hist ||
+                P.sum->cls_lo > P.sum->cls_hi;
     __syncthreads();
     if (s_bad) {
         if (threadIdx.x == 0) {
@@ -257,8 +321,10 @@ __global__ void __launch_bounds__(1024) dplan_finish(const DPlanParams P, int64_
         }
         return;
     }
-    // positions of the classes' items: ascending class = descending cost
-    const int64_t n_items = block_scan<int32_t>(P.class_count, kClasses, red);
+    // positions of the classes' items over the span present: ascending
+    // class = descending cost
+    const uint32_t lo = P.sum->cls_lo, hi = P.sum->cls_hi;
+    const int64_t n_items = block_scan<int32_t>(P.class_count + lo, (int64_t)(hi - lo) + 1, warp_sum);
     if (threadIdx.x == 0) {
         P.sum->n_items = (int32_t)n_items;
         *P.n_items_eff = (int32_t)n_items;
@@ -267,19 +333,41 @@ __global__ void __launch_bounds__(1024) dplan_finish(const DPlanParams P, int64_
     if (!P.user_off) {
         for (int64_t q = threadIdx.x; q < P.nq; q += blockDim.x) cells_scan[q] = P.qh[q].cells;
         __syncthreads();
-        const int64_t total = block_scan<int64_t>(cells_scan, P.nq, red);
+        const int64_t total = block_scan<int64_t>(cells_scan, P.nq, warp_sum);
         for (int64_t q = threadIdx.x; q < P.nq; q += blockDim.x) P.qh[q].table_off = cells_scan[q];
         if (threadIdx.x == 0) P.sum->out_cells = total;
     }
 }
 
+// Items at their class's next positions; the lanes of a warp with the same
+// class take their positions with one atomic (the first such lane adds the
+// group's items, the others offset by the items of the lanes before them).
 __global__ void dplan_items(const DPlanParams P)
 {
     if (*P.n_items_eff == 0) return;
-    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < P.nq; q += gridDim.x * blockDim.x) {
-        const int32_t nwin = P.qh[q].nwin;
-        const int32_t pos = atomicAdd(&P.class_count[P.cls[q]], nwin);
-        for (int32_t part = 0; part < nwin; ++part) P.items[pos + part] = Item{q, part};
+    const int lane = threadIdx.x & 31;
+    for (int32_t q0 = blockIdx.x * blockDim.x; q0 < P.nq; q0 += gridDim.x * blockDim.x) {
+        const int32_t q = q0 + threadIdx.x;
+        const bool live = q < P.nq;
+        const uint32_t cl = live ? P.cls[q] : 0xFFFFFFFFu;
+        const int32_t nwin = live ? P.qh[q].nwin : 0;
+        const unsigned same = __match_any_sync(0xffffffffu, cl);
+        const int leader = __ffs(same) - 1;
+        // items of the group's lanes before this one, and of the whole group
+        int32_t before = 0, group = 0;
+        for (unsigned m = same; m; m &= m - 1) {
+            const int l = __ffs(m) - 1;
+            const int32_t w = __shfl_sync(same, nwin, l);
+            if (l < lane) before += w;
+            group += w;
+        }
+        int32_t base = 0;
+        if (live && lane == leader) base = atomicAdd(&P.class_count[cl], group);
+        base = __shfl_sync(same, base, leader);
+        if (live) {
+            const int32_t pos = base + before;
+            for (int32_t part = 0; part < nwin; ++part) P.items[pos + part] = Item{q, part};
+        }
     }
 }
 
@@ -337,6 +425,9 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
     // class counts, the item counters and the summary start from zero
     if (e == cudaSuccess) e = cudaMemsetAsync(d + o_cc, 0, o_sc - o_cc, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d + o_ct, 0, total - o_ct, c->stream);
+    // the class span starts empty: lo = all ones, hi = 0
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(d + o_sum + offsetof(DPlanSummary, cls_lo), 0xFF, sizeof(uint32_t), c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "device plan upload");
 
     DPlanParams P{};
@@ -372,9 +463,13 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
     P.class_count = (int32_t *)(d + o_cc);
     P.n_items_eff = (int32_t *)(d + o_ct);
     P.sum = (DPlanSummary *)(d + o_sum);
-    const int threads = 256;
+    // small CTAs spread the per-query chains of dependent loads over the SMs;
+    // each stages the variables' tables when they fit 32 KiB
+    const int threads = 128;
     const int blocks = (int)std::min<int64_t>((nq + threads - 1) / threads, (int64_t)c->num_sms * 8);
-    dplan_describe<<<blocks, threads, 0, c->stream>>>(P);
+    const size_t var_smem = sizeof(VarInfo) * (size_t)c->n;
+    P.stage_vars = var_smem <= 32768 ? 1 : 0;
+    dplan_describe<<<blocks, threads, P.stage_vars ? var_smem : 0, c->stream>>>(P);
     dplan_finish<<<1, 1024, 0, c->stream>>>(P, (int64_t *)(d + o_sc));
     dplan_items<<<blocks, threads, 0, c->stream>>>(P);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "device plan launch");
