@@ -217,6 +217,13 @@ def make_workload(name: str, m: int | None = None, nq: int | None = None, rank: 
     raise ValueError(name)
 
 
+def with_options(config: dict, args) -> dict:
+    """The workload description plus any --option settings the run used."""
+    if getattr(args, "option", None):
+        config = dict(config, options=list(args.option))
+    return config
+
+
 def describe(name: str, w) -> dict:
     c = CONFIGS[name]
     if name in ("tiny", "random", "large"):
@@ -524,6 +531,18 @@ def setup_gpu(args, rank: int, world: int):
     return torch, fc, dist, dev, barrier, pk
 
 
+def set_options(fc, args, ctx):
+    """Apply the --option KEY=VALUE settings to a freshly loaded context."""
+    for kv in getattr(args, "option", None) or []:
+        key, value = kv.split("=", 1)
+        fc.fc_set_option(ctx, key, int(value))
+    return ctx
+
+
+def load_ctx(fc, args, D, arities):
+    return set_options(fc, args, fc.fc_load(D, arities))
+
+
 def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrier, pk,
             steps: int | None, cpu_seconds: float, per_query_n: int, clk, nvtx: bool = False):
     """One workload on this GPU: device-timed steps of its plan, the
@@ -537,7 +556,7 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
     extra = {}
     if name in ("tiny", "random", "large"):
         db, queries = w["db"], w["queries"]
-        ctx = fc.fc_load(db.D, db.arities)
+        ctx = load_ctx(fc, args, db.D, db.arities)
         off, flat = fc.pack_lists(queries)
         if args.autotune:
             fc.fc_autotune_batch(ctx, off, flat)
@@ -569,7 +588,7 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
         strategies = np.bincount(strat, minlength=6).tolist()
     elif name == "scores":
         db = w["db"]
-        ctx = fc.fc_load(db.D, db.arities)
+        ctx = load_ctx(fc, args, db.D, db.arities)
         po, pa = fc.pack_lists(w["parents"])
         if args.autotune:  # the counting work of a score query is the table over (parents..., child)
             fo, ff = fc.pack_lists([list(p) + [c] for p, c in zip(w["parents"], w["child"])])
@@ -592,7 +611,7 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
         strategies = np.bincount(strat, minlength=6).tolist()
     elif name == "families":
         db = w["db"]
-        ctx = fc.fc_load(db.D, db.arities)
+        ctx = load_ctx(fc, args, db.D, db.arities)
         fams = fc.family_list(w["vars"], w["max_parents"])
         po, pa = fc.pack_lists([f[1] for f in fams])
         if args.autotune:
@@ -616,7 +635,7 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
         strategies = None
     elif name == "assign":
         db = w["db"]
-        ctx = fc.fc_load(db.D, db.arities)
+        ctx = load_ctx(fc, args, db.D, db.arities)
         vo, vv = fc.pack_lists([q[0] for q in w["assign"]])
         _, ss = fc.pack_lists([q[1] for q in w["assign"]])
         plan = fc.fc_plan_assignments(ctx, vo, vv, ss)
@@ -633,7 +652,7 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
         strategies = None
     elif name == "pairs":
         db = w["db"]
-        ctx = fc.fc_load(db.D, db.arities)
+        ctx = load_ctx(fc, args, db.D, db.arities)
         plan = fc.fc_plan_pairs(ctx)
         outs = (torch.empty(fc.fc_plan_size(plan, 0), dtype=torch.int32, device="cuda"),
                 torch.empty(fc.fc_plan_size(plan, 1), dtype=torch.float32, device="cuda"))
@@ -649,7 +668,7 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
             fc.load_library().fc_pairs_all(ctx.ptr, fc._ptr(pin_t), fc._ptr(pin_m))
         strategies = None
     else:
-        ctx = fc.fc_load_bits(w["bits"], w["m"])
+        ctx = set_options(fc, args, fc.fc_load_bits(w["bits"], w["m"]))
         so, it = fc.pack_lists(w["sets"])
         splits = name == "splits"
         plan = fc.fc_plan_support_splits(ctx, so, it) if splits else fc.fc_plan_support(ctx, so, it)
@@ -793,7 +812,7 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
             "metric": metric_of(name), "value": value, "unit": UNITS[name], "steps": steps,
             "ms_per_step": ms,
             "dtype": {"pairs": "e4m3 one-hot x f32 accumulate -> int32"}.get(name, "u8/int32"),
-            "config": describe(name, w),
+            "config": with_options(describe(name, w), args),
             "e2e": {"value": units / e2e_s, "unit": UNITS[name], "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": steps * fc.fc_plan_size(plan, 6),
@@ -866,7 +885,7 @@ def run_rules_gpu(args, rank, world, fc, torch, barrier, dist, dev, pk):
     w = make_workload(name, args.m, args.nq, rank, world)
     db = w["db"]
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
-    ctx = fc.fc_load(db.D, db.arities)
+    ctx = load_ctx(fc, args, db.D, db.arities)
     clk = ClockSampler(dev).__enter__()
     for _ in range(args.warmup):
         r = fc.fc_mine_rules(ctx, *w["args"])
@@ -899,7 +918,7 @@ def run_rules_gpu(args, rank, world, fc, torch, barrier, dist, dev, pk):
     for _ in range(max(3, min(steps, 10))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        c2 = fc.fc_load(db.D, db.arities)
+        c2 = load_ctx(fc, args, db.D, db.arities)
         r2 = fc.fc_mine_rules(c2, *w["args"])
         del c2
         e2e_t.append(time.perf_counter() - t0)
@@ -924,7 +943,7 @@ def run_rules_gpu(args, rank, world, fc, torch, barrier, dist, dev, pk):
             "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8/int32",
             "data": "synthetic (seeded random-DAG samples)",
-            "config": describe(name, w),
+            "config": with_options(describe(name, w), args),
             "plan": {"l2": "flushed between timed steps (256 MiB write)",
                      "frequent_itemsets": int(len(sizes)), "rules": int(len(r["rule_set"])),
                      "candidates": int(units), "levels": int(r["levels"]),
@@ -965,7 +984,7 @@ def run_append_gpu(args, rank, world, fc, torch, barrier, dist, dev, pk):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
     hbm, peak_src = pk["hbm_gbs"], pk["src"]
     steps = min(args.steps, 50)
-    ctx = fc.fc_load(D[:, :m0], db.arities)
+    ctx = load_ctx(fc, args, D[:, :m0], db.arities)
     fc.fc_reserve(ctx, m0 + B * (args.warmup + steps + 1))
     block = torch.from_numpy(np.ascontiguousarray(D[:, m0:m0 + B])).cuda()
     clk = ClockSampler(dev).__enter__()
@@ -995,7 +1014,7 @@ def run_append_gpu(args, rank, world, fc, torch, barrier, dist, dev, pk):
 
     # end to end: the block comes from host memory (pinned) each step
     host_block = torch.from_numpy(np.ascontiguousarray(D[:, m0:m0 + B])).pin_memory()
-    e2e_ctx = fc.fc_load(D[:, :m0], db.arities)
+    e2e_ctx = load_ctx(fc, args, D[:, :m0], db.arities)
     fc.fc_reserve(e2e_ctx, m0 + B * 12)
     e2e_t = []
     for _ in range(10):
@@ -1024,7 +1043,7 @@ def run_append_gpu(args, rank, world, fc, torch, barrier, dist, dev, pk):
             "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic (seeded random-DAG samples)",
-            "config": describe(name, w),
+            "config": with_options(describe(name, w), args),
             "plan": {"l2": "flushed between timed steps (256 MiB write)"},
             "e2e": {"value": B / e2e_s, "unit": UNITS[name], "h2d_bytes_per_step": int(db.n * B),
                     "d2h_bytes_per_step": int(8 * R + 4)},
@@ -1134,6 +1153,8 @@ def main():
                          "measures the other benchmark configurations and nests them under 'configs')")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip fc_autotune (strategy thresholds from the default cost model)")
+    ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
+                    help="fc_set_option on every context the bench loads (repeatable)")
     ap.add_argument("--strategy", type=int, default=-1, help="force one counting strategy (-1 = planner's choice)")
     ap.add_argument("--m", type=int, default=None, help="instances (default: the workload's own)")
     ap.add_argument("--nq", type=int, default=None, help="queries / itemsets (default: the workload's own)")

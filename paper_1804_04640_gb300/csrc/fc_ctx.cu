@@ -376,7 +376,6 @@ int grow_storage(fc_ctx *c, int64_t m_need)
     return FC_OK;
 }
 
-// New instance count, marginals and entropies after an append.
 // New instance count, generation and entropies after an append; the host
 // copy of the marginals is read back from the device unless the caller has
 // already brought it up to date.
