@@ -210,8 +210,11 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
         constexpr int kTasksMax = ((kRegion + kN) * 2 + kProducers - 1) / kProducers;
         const int a_rows = diag ? 0 : kRegion;
         const int ntask = (a_rows + G.real_b) * 2;
-        // words of stages st + 1, st + 2, st + 3 in flight while stage st is expanded
-        uint64_t p1[kTasksMax], p2[kTasksMax], p3[kTasksMax];
+        // The words of three stages are in flight: the loop is unrolled by
+        // three so that each buffer keeps its registers (a register copy of a
+        // pending load would wait for it) and is refilled, three stages
+        // ahead, right after its stage has been expanded.
+        uint64_t q0[kTasksMax], q1[kTasksMax], q2[kTasksMax];
         auto load = [&](int64_t st, uint64_t (&dst)[kTasksMax]) {
             const int64_t kw = (st0 + st) * 2;  // first 64-bit word of that stage
 #pragma unroll
@@ -224,26 +227,16 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
                              : 0ull;
             }
         };
-        load(0, p1);
-        load(1, p2);
-        load(2, p3);
-        for (int64_t st = 0; st < nst; ++st) {
+        // expands stage st from cur into its slot; false when the CTA aborts
+        auto stage = [&](int64_t st, const uint64_t (&cur)[kTasksMax]) -> bool {
             const int slot = (int)(st % kStages);
-            uint64_t cur[kTasksMax];
-#pragma unroll
-            for (int j = 0; j < kTasksMax; ++j) {
-                cur[j] = p1[j];
-                p1[j] = p2[j];
-                p2[j] = p3[j];
-            }
-            load(st + 3, p3);
             if (st >= kStages) {
                 if (!mbar_wait(empty0 + 8 * slot, (uint32_t)((st / kStages - 1) & 1), P.wait_limit)) {
                     atomicExch(&s_abort, 1);
-                    break;
+                    return false;
                 }
             }
-            if (*(volatile int *)&s_abort) break;
+            if (*(volatile int *)&s_abort) return false;
             uint8_t *a_tile = smem + slot * kStageBytes;
             uint8_t *b_tile = a_tile + kABytes;
 #pragma unroll
@@ -259,6 +252,18 @@ __global__ void __launch_bounds__(kThreads, 1) pairs_gemm_kernel(const PairsPara
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(full0 + 8 * slot);
+            return true;
+        };
+        load(0, q0);
+        load(1, q1);
+        load(2, q2);
+        for (int64_t st = 0; st < nst; st += 3) {
+            if (!stage(st, q0)) break;
+            load(st + 3, q0);
+            if (st + 1 >= nst || !stage(st + 1, q1)) break;
+            load(st + 4, q1);
+            if (st + 2 >= nst || !stage(st + 2, q2)) break;
+            load(st + 5, q2);
         }
     } else if (lane == 0) {
         // ------------------------------------------------------ MMA issuer
