@@ -434,7 +434,14 @@ int fc_sync(fc_ctx *ctx, void *stream);
  *                       database of fewer than 2^19 instances) is planned on
  *                       the device (validation, strategy, work order); any
  *                       other batch, or an invalid one, is planned on the
- *                       host, which reports the error; 0 = always the host. */
+ *                       host, which reports the error; 0 = always the host.
+ *   "codes4"            1 (default) = on a database whose arities are all at
+ *                       most 16, fc_load keeps a second copy of the columns
+ *                       at 4 bits per value (n x m / 2 bytes more device
+ *                       memory, skipped when that allocation fails) and the
+ *                       shared-memory histogram strategy reads it (half the
+ *                       column bytes); 0 = read the byte columns.  Counts
+ *                       are the same either way. */
 int fc_set_option(fc_ctx *ctx, const char *key, int64_t value);
 
 /* Current value of an option (or -1 for an unknown key). */

@@ -736,9 +736,115 @@ __device__ __forceinline__ void key_rows_swar_bytes_k(const CountParams &P, cons
     }
 }
 
+// key_rows_swar_bytes_k on the 4-bit codes (every arity <= 16): a lane's
+// 16-byte load brings 32 rows of a column instead of 16, so a warp group of
+// 1024 rows is one 512-byte load per column, half the load wavefronts of the
+// byte columns.  Word i of a load holds rows 8i .. 8i + 7, row 2b in the low
+// nibble of byte b; one mask gives the even rows as bytes, a shift and a mask
+// the odd ones.  Consecutive variables are then combined in groups of GS on
+// the packed bytes by Horner's rule (g = g * r + s, one IMAD for four rows;
+// no carry between bytes while a group has at most 256 joint states), and
+// each group enters the 16-bit key lanes once (PRMT + IMAD for two rows) with
+// the stride of its last, fastest variable.  The rows past the last whole
+// group come from the byte columns.
+template <int K, int GS>
+__device__ __forceinline__ void key_rows_swar_nib_k(const CountParams &P, const QVar *vs, int64_t r0, int64_t r1,
+                                                    int lshift, int32_t *tab0)
+{
+    constexpr int NG = (K + GS - 1) / GS;
+    char *smem = reinterpret_cast<char *>(tab0);
+    const uint32_t base_bytes = (uint32_t)((threadIdx.x & ((1 << lshift) - 1)) << 2);
+    const int sshift = 2 + lshift;
+    const uint32_t init = base_bytes | (base_bytes << 16);
+    const int64_t pad4 = P.m_pad / 2;
+    const uint4 *col[K];
+    uint32_t mul[K];
+    uint32_t st[NG];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        col[t] = reinterpret_cast<const uint4 *>(P.D4 + (int64_t)vs[t].var * pad4 + r0 / 2);
+        mul[t] = (uint32_t)vs[t].arity;
+    }
+#pragma unroll
+    for (int gi = 0; gi < NG; ++gi) st[gi] = (uint32_t)vs[min(K, (gi + 1) * GS) - 1].stride << sshift;
+    const int64_t nfull = (r1 - r0) >> 10;
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = threadIdx.x; u < (nfull << 5); u += blockDim.x) {
+        const int64_t vec = ((u >> 5) << 5) + lane;  // 16-byte vector (32 rows) in the range
+        uint32_t acc[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] = init;
+#pragma unroll
+        for (int gi = 0; gi < NG; ++gi) {
+            uint32_t g[8];
+#pragma unroll
+            for (int t = gi * GS; t < (K < (gi + 1) * GS ? K : (gi + 1) * GS); ++t) {
+                const uint4 x = __ldg(col[t] + vec);
+                const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t ev = w[i] & 0x0F0F0F0Fu, od = (w[i] >> 4) & 0x0F0F0F0Fu;
+                    g[2 * i] = t == gi * GS ? ev : g[2 * i] * mul[t] + ev;
+                    g[2 * i + 1] = t == gi * GS ? od : g[2 * i + 1] * mul[t] + od;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                acc[2 * i] += __byte_perm(g[i], 0u, 0x4240) * st[gi];
+                acc[2 * i + 1] += __byte_perm(g[i], 0u, 0x4341) * st[gi];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            atomicAdd(reinterpret_cast<int *>(smem + (acc[j] & 0xFFFFu)), 1);
+            atomicAdd(reinterpret_cast<int *>(smem + (acc[j] >> 16)), 1);
+        }
+    }
+    for (int64_t p = r0 + (nfull << 10) + threadIdx.x; p < r1; p += blockDim.x) {
+        uint32_t key = base_bytes;
+#pragma unroll
+        for (int t = 0; t < K; ++t) key += (uint32_t)P.D[(int64_t)vs[t].var * P.m_pad + p] * ((uint32_t)vs[t].stride << sshift);
+        atomicAdd(reinterpret_cast<int *>(smem + key), 1);
+    }
+}
+
+// Groups of three when every run of three consecutive variables has at most
+// 256 joint states, else of two (always valid for arities <= 16).
+__device__ __forceinline__ bool nib_groups_of_three(const QVar *vs, int k)
+{
+    for (int a = 0; a + 3 <= k; ++a)
+        if (vs[a].arity * vs[a + 1].arity * vs[a + 2].arity > 256) return false;
+    return true;
+}
+
+template <bool kNib>
 __device__ __forceinline__ void key_rows_swar_dispatch(const CountParams &P, const QVar *vs, int k, int64_t r0,
                                                        int64_t r1, int lshift, int32_t *tab0)
 {
+    if constexpr (kNib) {
+        const bool g3 = nib_groups_of_three(vs, k);
+        switch (k) {
+        case 1: key_rows_swar_nib_k<1, 1>(P, vs, r0, r1, lshift, tab0); return;
+        case 2: key_rows_swar_nib_k<2, 2>(P, vs, r0, r1, lshift, tab0); return;
+        case 3:
+            if (g3) key_rows_swar_nib_k<3, 3>(P, vs, r0, r1, lshift, tab0);
+            else key_rows_swar_nib_k<3, 2>(P, vs, r0, r1, lshift, tab0);
+            return;
+        case 4:
+            if (g3) key_rows_swar_nib_k<4, 3>(P, vs, r0, r1, lshift, tab0);
+            else key_rows_swar_nib_k<4, 2>(P, vs, r0, r1, lshift, tab0);
+            return;
+        case 5:
+            if (g3) key_rows_swar_nib_k<5, 3>(P, vs, r0, r1, lshift, tab0);
+            else key_rows_swar_nib_k<5, 2>(P, vs, r0, r1, lshift, tab0);
+            return;
+        case 6:
+            if (g3) key_rows_swar_nib_k<6, 3>(P, vs, r0, r1, lshift, tab0);
+            else key_rows_swar_nib_k<6, 2>(P, vs, r0, r1, lshift, tab0);
+            return;
+        default: break;
+        }
+    }
     switch (k) {
     case 1: key_rows_swar_bytes_k<1>(P, vs, r0, r1, lshift, tab0); break;
     case 2: key_rows_swar_bytes_k<2>(P, vs, r0, r1, lshift, tab0); break;
@@ -927,8 +1033,10 @@ __device__ __forceinline__ void key_rows_window_dispatch(const CountParams &P, c
 // kThreads x kBlocks: 512 x 2 for the mixed launch; 1024 x 1 for windowed
 // tables, whose window then takes the whole shared memory of an SM (and
 // whose keys pair variables into byte digits, a path kept out of the mixed
-// launch's register allocation).
-template <int kThreads, int kBlocks>
+// launch's register allocation).  kNib: the mixed launch's histogram keys
+// read the 4-bit columns (P.D4 set), a separate instantiation so that each
+// key loop gets the registers of its own kernel.
+template <int kThreads, int kBlocks, bool kNib = false>
 __global__ void __launch_bounds__(kThreads, kBlocks) count_kernel(const CountParams P)
 {
     constexpr bool kWide = kThreads == 1024;
@@ -999,7 +1107,7 @@ __global__ void __launch_bounds__(kThreads, kBlocks) count_kernel(const CountPar
             key_rows_window_dispatch<kWide>(P, s_vars, k, r0, r1, w0, wlen, smem_tab);
         } else if constexpr (!kWide) {  // the wide launch holds windows only
             if (lshift >= 0)
-                key_rows_swar_dispatch(P, s_vars, k, r0, r1, lshift, smem_tab);
+                key_rows_swar_dispatch<kNib>(P, s_vars, k, r0, r1, lshift, smem_tab);
             else if (in_smem)
                 key_rows_swar(P, s_vars, k, r0, r1, smem_tab + (warp % copies) * h.cells);
             else
@@ -1147,7 +1255,6 @@ __global__ void score_global_kernel(const QHead *__restrict__ qh, const int32_t 
 
 }  // namespace
 
-const void *count_kernel_ptr() { return (const void *)count_kernel<512, 2>; }
 const void *bitmap_kernel_ptr() { return (const void *)bitmap_kernel; }
 
 size_t bitmap_smem_bytes(int threads, int stage_slots)
@@ -1162,7 +1269,7 @@ size_t bitmap_smem_bytes(int threads, int stage_slots)
 namespace {
 std::mutex g_attr_mu;
 constexpr int kMaxDevices = 64;
-int g_count_smem[kMaxDevices], g_bitmap_smem[kMaxDevices], g_wide_smem[kMaxDevices];
+int g_count_smem[kMaxDevices], g_count4_smem[kMaxDevices], g_bitmap_smem[kMaxDevices], g_wide_smem[kMaxDevices];
 
 cudaError_t ensure_smem_attr(const void *fn, int *cache, size_t smem)
 {
@@ -1207,6 +1314,12 @@ int bitmap_ctas_per_sm(int threads, int stage_slots)
 cudaError_t launch_count(const CountParams &p, int grid, int threads, size_t smem, cudaStream_t s)
 {
     if (threads > 512) return cudaErrorInvalidValue;
+    if (p.D4) {
+        cudaError_t e = ensure_smem_attr((const void *)count_kernel<512, 2, true>, g_count4_smem, smem);
+        if (e != cudaSuccess) return e;
+        count_kernel<512, 2, true><<<grid, threads, smem, s>>>(p);
+        return cudaGetLastError();
+    }
     cudaError_t e = ensure_smem_attr((const void *)count_kernel<512, 2>, g_count_smem, smem);
     if (e != cudaSuccess) return e;
     count_kernel<512, 2><<<grid, threads, smem, s>>>(p);

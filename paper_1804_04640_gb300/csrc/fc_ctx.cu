@@ -169,6 +169,31 @@ int new_ctx(fc_ctx **out, int32_t n, int64_t m)
 
 }  // namespace
 
+namespace {
+// The 4-bit copy of D (fc_ctx::d_D4) for a database whose arities are all at
+// most 16, allocated for the current m_pad and packed for rows [0, m).
+cudaError_t build_codes4(fc_ctx *c)
+{
+    if (c->transactions || c->n > 65535) return cudaSuccess;
+    for (const int32_t r : c->arity)
+        if (r > 16) return cudaSuccess;
+    const size_t bytes = (size_t)c->n * (size_t)(c->m_pad / 2);
+    cudaError_t e = cudaMalloc(&c->d_D4, bytes);
+    if (e == cudaErrorMemoryAllocation) {  // optional: the byte columns serve every query
+        (void)cudaGetLastError();
+        c->d_D4 = nullptr;
+        return cudaSuccess;
+    }
+    if (e != cudaSuccess) {
+        c->d_D4 = nullptr;
+        return e;
+    }
+    e = cudaMemsetAsync(c->d_D4, 0, bytes, c->stream);
+    if (e == cudaSuccess) e = launch_pack_codes4(c->d_D, c->m_pad, c->n, 0, c->m, c->d_D4, c->stream);
+    return e;
+}
+}  // namespace
+
 extern "C" int fc_load(fc_ctx **out, const uint8_t *D, int32_t n, int64_t m,
                        const int32_t *arities, int32_t layout, int32_t where)
 {
@@ -231,6 +256,7 @@ extern "C" int fc_load(fc_ctx **out, const uint8_t *D, int32_t n, int64_t m,
     if (e != cudaSuccess) return bail(cuda_fail(e, "load"));
     if (bad_h) return bail(fail(FC_ERR_RANGE, "fc_load: a stored state is >= its variable's arity"));
     cudaMemsetAsync(c->d_status, 0, 16, c->stream);
+    if ((e = build_codes4(c)) != cudaSuccess) return bail(cuda_fail(e, "4-bit codes"));
     rc = finish_load(c);
     if (rc != FC_OK) return bail(rc);
     *out = c;
@@ -306,6 +332,7 @@ extern "C" void fc_free(fc_ctx *c)
     for (auto &bank : c->pool)
         for (auto &b : bank) b.release();
     cudaFree(c->d_D);
+    cudaFree(c->d_D4);
     cudaFree(c->d_bits);
     cudaFree(c->d_marg);
     cudaFree(c->d_arity);
@@ -351,18 +378,32 @@ int grow_storage(fc_ctx *c, int64_t m_need)
     if (e == cudaSuccess && c->words > 0)
         e = cudaMemcpy2DAsync(nb, sizeof(uint64_t) * new_wstride, c->d_bits, sizeof(uint64_t) * c->wstride,
                               sizeof(uint64_t) * c->words, rows, cudaMemcpyDeviceToDevice, c->stream);
-    uint8_t *nd = nullptr;
+    uint8_t *nd = nullptr, *nd4 = nullptr;
     if (e == cudaSuccess && !c->transactions) {
         const size_t dbytes = (size_t)c->n * new_pad;
         e = cudaMalloc(&nd, dbytes);
         if (e == cudaSuccess) e = cudaMemsetAsync(nd, 0, dbytes, c->stream);
         if (e == cudaSuccess)
             e = cudaMemcpy2DAsync(nd, new_pad, c->d_D, c->m_pad, c->m, c->n, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess && c->d_D4) {
+            e = cudaMalloc(&nd4, dbytes / 2);
+            if (e == cudaErrorMemoryAllocation) {  // drop the optional 4-bit copy instead
+                (void)cudaGetLastError();
+                nd4 = nullptr;
+                e = cudaSuccess;
+            } else if (e == cudaSuccess) {
+                e = cudaMemsetAsync(nd4, 0, dbytes / 2, c->stream);
+            }
+            if (e == cudaSuccess && nd4)
+                e = cudaMemcpy2DAsync(nd4, new_pad / 2, c->d_D4, c->m_pad / 2, (c->m + 1) / 2, c->n,
+                                      cudaMemcpyDeviceToDevice, c->stream);
+        }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cudaFree(nb);
         cudaFree(nd);
+        cudaFree(nd4);
         return cuda_fail(e, "grow storage");
     }
     cudaFree(c->d_bits);
@@ -371,6 +412,10 @@ int grow_storage(fc_ctx *c, int64_t m_need)
     if (!c->transactions) {
         cudaFree(c->d_D);
         c->d_D = nd;
+        if (c->d_D4) {
+            cudaFree(c->d_D4);
+            c->d_D4 = nd4;
+        }
         c->m_pad = new_pad;
     }
     return FC_OK;
@@ -471,6 +516,8 @@ extern "C" int fc_append(fc_ctx *c, const uint8_t *D, int64_t m_new, int32_t lay
     }
     for (int r = 0; r < c->R; ++r) c->marg[r] += c->h_marg_delta[r];
     e = cudaMemcpyAsync(c->d_marg, c->marg.data(), sizeof(int64_t) * c->R, cudaMemcpyHostToDevice, c->stream);
+    // the 4-bit codes of the appended rows (from the 16-row group holding m0)
+    if (e == cudaSuccess && c->d_D4) e = launch_pack_codes4(c->d_D, c->m_pad, c->n, m0, m1, c->d_D4, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "fc_append marginals");
     return finish_append(c, m1, false);
 }

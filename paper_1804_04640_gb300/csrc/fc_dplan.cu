@@ -499,6 +499,7 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
     }
     CountParams C{};
     C.D = c->d_D;
+    C.D4 = c->opt.codes4 ? c->d_D4 : nullptr;
     C.m_pad = c->m_pad;
     C.m = c->m;
     C.bits = c->d_bits;

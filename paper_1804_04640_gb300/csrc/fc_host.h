@@ -119,6 +119,9 @@ struct Options {
     // large count batches whose queries all count in shared memory are
     // planned on the device (fc_dplan.cu)
     int32_t device_plan = 1;
+    // the histogram strategy reads the 4-bit copy of the columns when the
+    // context holds one (every arity <= 16)
+    int32_t codes4 = 1;
 };
 
 // Host arrays of the count planner, kept by the context between plan builds
@@ -209,6 +212,9 @@ struct fc_ctx {
     int32_t R = 0;
     int64_t m_pad = 0, words = 0, wstride = 0;
     uint8_t *d_D = nullptr;
+    // D as 4-bit codes when every arity is at most 16 (else null): the
+    // histogram kernel reads half the column bytes
+    uint8_t *d_D4 = nullptr;
     uint64_t *d_bits = nullptr;
     int64_t *d_marg = nullptr;
     int32_t *d_arity = nullptr, *d_soff = nullptr;

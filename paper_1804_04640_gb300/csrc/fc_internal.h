@@ -65,6 +65,7 @@ struct BTask {
 struct CountParams {
     const uint8_t *D;        // n columns of m_pad bytes
     int64_t m_pad;
+    const uint8_t *D4;       // the same states as 4-bit codes (m_pad / 2 bytes per column), or null
     int64_t m;
     const uint64_t *bits;    // sum(r) rows of wstride words
     int64_t wstride;
@@ -109,6 +110,11 @@ cudaError_t launch_bit_popcounts(const uint64_t *bits, int64_t rows, int64_t wst
                                  int64_t *counts, cudaStream_t s);
 cudaError_t launch_transpose_rows(const uint8_t *Drow, int64_t m, int32_t n, uint8_t *Dcol,
                                   int64_t m_pad, cudaStream_t s);
+// 4-bit codes of rows [row0, row1) (widened to whole 16-row groups) of the
+// n columns of D (all states < 16): column i at D4 + i * m_pad / 2, rows 2b
+// and 2b + 1 in the low and high nibble of byte b.
+cudaError_t launch_pack_codes4(const uint8_t *D, int64_t m_pad, int32_t n, int64_t row0, int64_t row1,
+                               uint8_t *D4, cudaStream_t s);
 cudaError_t launch_mask_tail_bits(uint64_t *bits, int64_t rows, int64_t wstride, int64_t m,
                                   cudaStream_t s);
 
@@ -119,7 +125,6 @@ cudaError_t launch_count_wide(const CountParams &p, int grid, size_t smem, cudaS
 cudaError_t launch_bitmap(const CountParams &p, int grid, int threads, cudaStream_t s);
 size_t bitmap_smem_bytes(int threads, int stage_slots);
 int bitmap_ctas_per_sm(int threads, int stage_slots);
-const void *count_kernel_ptr();
 const void *bitmap_kernel_ptr();
 
 // Sort + run-length path for one query (large tables).

@@ -155,6 +155,30 @@ __global__ void bit_popcount_kernel(const uint64_t *__restrict__ bits, int64_t w
 }
 
 // Row-major (m x n) -> column-major (n x m_pad) through a 32 x 32 byte tile.
+// 4-bit state codes of column blockIdx.y: rows 2b and 2b + 1 in the low and
+// high nibble of byte b, so a 32-bit word holds 8 consecutive rows in order.
+// Each thread packs 16 rows (one 16-byte load, one 8-byte store) from row0 on.
+__global__ void pack_codes4_kernel(const uint8_t *__restrict__ D, int64_t m_pad, int64_t row0, int64_t vecs,
+                                   uint8_t *__restrict__ D4)
+{
+    const uint8_t *col = D + (int64_t)blockIdx.y * m_pad + row0;
+    uint8_t *out = D4 + (int64_t)blockIdx.y * (m_pad / 2) + row0 / 2;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < vecs; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 x = *reinterpret_cast<const uint4 *>(col + v * 16);
+        const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+        uint32_t o[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            // bytes b0..b7 (states < 16) to nibbles n0..n7 of one word
+            const uint32_t lo = w[2 * h], hi = w[2 * h + 1];
+            const uint32_t a = (lo & 0x0F0F0F0Fu) | ((lo >> 4) & 0xF0F0F0F0u);  // bytes (b0|b1<<4) at 0, (b2|b3<<4) at 2
+            const uint32_t b = (hi & 0x0F0F0F0Fu) | ((hi >> 4) & 0xF0F0F0F0u);
+            o[h] = __byte_perm(a, b, 0x6420);
+        }
+        *reinterpret_cast<uint2 *>(out + v * 8) = make_uint2(o[0], o[1]);
+    }
+}
+
 __global__ void transpose_rows_kernel(const uint8_t *__restrict__ Drow, int64_t m, int32_t n,
                                       uint8_t *__restrict__ Dcol, int64_t m_pad)
 {
@@ -284,6 +308,18 @@ cudaError_t launch_bit_popcounts(const uint64_t *bits, int64_t rows, int64_t wst
 {
     if (rows <= 0) return cudaSuccess;
     bit_popcount_kernel<<<(unsigned)rows, 256, 0, s>>>(bits, wstride, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_codes4(const uint8_t *D, int64_t m_pad, int32_t n, int64_t row0, int64_t row1,
+                               uint8_t *D4, cudaStream_t s)
+{
+    row0 &= ~(int64_t)15;
+    row1 = std::min<int64_t>(m_pad, (row1 + 15) & ~(int64_t)15);
+    if (n <= 0 || row1 <= row0) return cudaSuccess;
+    const int64_t vecs = (row1 - row0) / 16;
+    dim3 grid((unsigned)std::min<int64_t>((vecs + 255) / 256, 65535), (unsigned)n);
+    pack_codes4_kernel<<<grid, 256, 0, s>>>(D, m_pad, row0, vecs, D4);
     return cudaGetLastError();
 }
 

@@ -686,6 +686,7 @@ cudaError_t enqueue_count(fc_plan *p, int32_t *tables, float *scores, cudaStream
     if (p->n_items > 0 || p->n_witems > 0 || p->n_btasks > 0) {
         CountParams P{};
         P.D = c->d_D;
+        P.D4 = c->opt.codes4 ? c->d_D4 : nullptr;
         P.m_pad = c->m_pad;
         P.m = c->m;
         P.bits = c->d_bits;

@@ -48,6 +48,7 @@ const OptDesc kOpts[] = {
     {"support_part_words", &Options::support_part_words, nullptr, 64, (int64_t)1 << 40},
     {"zero_copy", nullptr, &Options::zero_copy, 0, 1},
     {"device_plan", nullptr, &Options::device_plan, 0, 1},
+    {"codes4", nullptr, &Options::codes4, 0, 1},
 };
 
 }  // namespace

@@ -536,3 +536,39 @@ def test_device_planned_batches_match_host_planned():
     # the context still answers after the refused batch
     again, _ = fc.fc_count_batch(ctx, off, flat)
     assert np.array_equal(again, host_t)
+
+
+@pytest.mark.parametrize("m", [4096 * 3 + 17, 40_000])
+def test_codes4_matches_byte_columns(m):
+    """On a database whose arities are all <= 16 the histogram strategy reads
+    the 4-bit copy of the columns (option codes4).  Its tables equal the byte
+    columns' and the oracle's: arity 16 (the top code 15 in a nibble), arity
+    1, ragged tails that end inside a 32-row group, and the copy repacked by
+    appends that start at odd rows."""
+    rng = np.random.default_rng(m)
+    n = 9
+    ar = np.array([16, 2, 3, 16, 5, 1, 7, 16, 4], dtype=np.int32)
+    D = np.stack([rng.integers(0, a, size=m) for a in ar]).astype(np.uint8)
+    D[0, -1] = 15
+    D[3, :50] = 15
+    queries = random_queries(n, 400, 1, 4, seed=m + 1) + [[0, 3], [0, 3, 7], [5], [5, 0], list(range(6))]
+    queries = [q for q in queries if int(np.prod(ar[q])) <= 16384]
+    ctx = fc.fc_load(D, ar)
+    fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_HIST)
+    for cut in (0, 1, 33):
+        if cut:
+            extra = np.stack([rng.integers(0, a, size=cut * 7 + 3) for a in ar]).astype(np.uint8)
+            fc.fc_append(ctx, extra)
+            D = np.concatenate([D, extra], axis=1)
+        orc = oracle.DB(D, ar)
+        off, flat = fc.pack_lists(queries)
+        fc.fc_set_option(ctx, "codes4", 0)
+        byte_t, toff = fc.fc_count_batch(ctx, off, flat)
+        fc.fc_set_option(ctx, "codes4", 1)
+        nib_t, toff2 = fc.fc_count_batch(ctx, off, flat)
+        assert np.array_equal(toff, toff2)
+        assert np.array_equal(nib_t, byte_t)
+        for q in range(0, len(queries), 7):
+            assert np.array_equal(nib_t[toff[q]:toff[q + 1]].astype(np.int64), orc.table(queries[q])), queries[q]
+        for q in range(len(queries) - 5, len(queries)):
+            assert np.array_equal(nib_t[toff[q]:toff[q + 1]].astype(np.int64), orc.table(queries[q])), queries[q]
