@@ -485,7 +485,8 @@ def roofline(name: str, ms: float, work: dict, pk: dict, resident_bytes: int, pl
              "duration": "whole step",
              "l2": {"achieved": work["col_bytes"] / sec / 1e9, "peak": l2, "unit": "GB/s",
                     "frac": work["col_bytes"] / sec / 1e9 / l2,
-                    "work": "k column bytes per instance of every keyed query, read from L2"},
+                    "work": "k column values per instance of every keyed query, read from L2 at the "
+                            "width the histogram keys read them (4 bits per value with the 4-bit columns)"},
              "effective_gbs": work["alg_bytes"] / sec / 1e9}
         if name == "scores":
             r["note"] = (f"the step also runs the bitmap launch of {work['queries'] - work['keyed_queries']} "
@@ -569,7 +570,8 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
         keyed = np.isin(strat, [fc.FC_STRAT_HIST, fc.FC_STRAT_WINDOW, fc.FC_STRAT_GATOMIC, fc.FC_STRAT_SORT])
         ks = np.array([len(q) for q in queries])
         work = {"alg_bytes": int(ks.sum()) * db.m + 4 * int(toff[-1]), "atomics": int(keyed.sum()) * db.m,
-                "col_bytes": int(ks[keyed].sum()) * db.m, "keyed_queries": int(keyed.sum()), "queries": units}
+                "col_bytes": int(ks[keyed].sum()) * db.m * fc.fc_info(ctx, 6) // 8,
+                "keyed_queries": int(keyed.sum()), "queries": units}
         pinned = torch.empty(int(toff[-1]), dtype=torch.int32).pin_memory()
         h2d = fc.fc_plan_size(plan, 5) + 4 * (len(off) + len(flat))
         d2h = 4 * int(toff[-1])
@@ -601,7 +603,8 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
         keyed = np.isin(strat, [fc.FC_STRAT_HIST, fc.FC_STRAT_WINDOW, fc.FC_STRAT_GATOMIC, fc.FC_STRAT_SORT])
         ks = np.array([len(p) + 1 for p in w["parents"]])
         work = {"alg_bytes": int(ks.sum()) * db.m, "atomics": int(keyed.sum()) * db.m,
-                "col_bytes": int(ks[keyed].sum()) * db.m, "keyed_queries": int(keyed.sum()), "queries": units}
+                "col_bytes": int(ks[keyed].sum()) * db.m * fc.fc_info(ctx, 6) // 8,
+                "keyed_queries": int(keyed.sum()), "queries": units}
         pinned = torch.empty(units, dtype=torch.float32).pin_memory()
         h2d = fc.fc_plan_size(plan, 5) + 4 * (units + len(po) + len(pa))
         d2h = 4 * units

@@ -116,7 +116,10 @@ void fc_free(fc_ctx *ctx);
 
 /* Basic facts about a context: key 0 = n (variables or items), 1 = m,
  * 2 = sum of arities, 3 = device ordinal, 4 = instances that fit without
- * reallocating (see fc_reserve), 5 = appends so far.  -1 for a bad key. */
+ * reallocating (see fc_reserve), 5 = appends so far, 6 = bits per value of
+ * the columns the shared-memory histogram strategy reads (4 with the 4-bit
+ * copy of option "codes4", else 8; 0 for a context from fc_load_bits).
+ * -1 for a bad key. */
 int64_t fc_info(const fc_ctx *ctx, int32_t key);
 
 /* ---------------------------------------------------- growing a database

@@ -558,6 +558,7 @@ extern "C" int64_t fc_info(const fc_ctx *c, int32_t key)
     case 3: return c->device;
     case 4: return capacity_rows(c);
     case 5: return (int64_t)c->generation;
+    case 6: return c->transactions ? 0 : (c->d_D4 && c->opt.codes4) ? 4 : 8;
     default: return -1;
     }
 }

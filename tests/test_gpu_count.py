@@ -554,6 +554,7 @@ def test_codes4_matches_byte_columns(m):
     queries = random_queries(n, 400, 1, 4, seed=m + 1) + [[0, 3], [0, 3, 7], [5], [5, 0], list(range(6))]
     queries = [q for q in queries if int(np.prod(ar[q])) <= 16384]
     ctx = fc.fc_load(D, ar)
+    assert fc.fc_info(ctx, 6) == 4
     fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_HIST)
     for cut in (0, 1, 33):
         if cut:
@@ -572,3 +573,20 @@ def test_codes4_matches_byte_columns(m):
             assert np.array_equal(nib_t[toff[q]:toff[q + 1]].astype(np.int64), orc.table(queries[q])), queries[q]
         for q in range(len(queries) - 5, len(queries)):
             assert np.array_equal(nib_t[toff[q]:toff[q + 1]].astype(np.int64), orc.table(queries[q])), queries[q]
+
+
+def test_codes4_only_for_arities_up_to_16():
+    """An arity of 17 keeps the byte columns (fc_info key 6 = 8 bits), with
+    the same tables as the oracle; switching the option off does the same on
+    a database that has the 4-bit copy."""
+    rng = np.random.default_rng(5)
+    ar = np.array([17, 3, 4], dtype=np.int32)
+    D = np.stack([rng.integers(0, a, size=9001) for a in ar]).astype(np.uint8)
+    ctx = fc.fc_load(D, ar)
+    assert fc.fc_info(ctx, 6) == 8
+    orc = oracle.DB(D, ar)
+    check_batch(ctx, orc, [[0, 1], [1, 2], [0, 1, 2], [2, 0]])
+    ctx2 = fc.fc_load(D[1:], ar[1:])
+    assert fc.fc_info(ctx2, 6) == 4
+    fc.fc_set_option(ctx2, "codes4", 0)
+    assert fc.fc_info(ctx2, 6) == 8
