@@ -799,6 +799,12 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = float(np.median(e2e_t))
     clk.stop()
+    planner = "host"
+    if name in ("tiny", "random", "large") and fc.fc_info(ctx, 7) == 1:
+        # planned on the device: only the query lists, the caller's table
+        # offsets and the variables' entropies were uploaded
+        planner = "device"
+        h2d = 4 * (len(off) + len(flat)) + 8 * len(toff) + 8 * db.n
 
     plan_sig = "-"
     if strategies is not None:
@@ -817,7 +823,7 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
             "dtype": {"pairs": "e4m3 one-hot x f32 accumulate -> int32"}.get(name, "u8/int32"),
             "config": with_options(describe(name, w), args),
             "e2e": {"value": units / e2e_s, "unit": UNITS[name], "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
+                    "d2h_bytes_per_step": int(d2h), "planner": planner},
             "gpu_launches": steps * fc.fc_plan_size(plan, 6),
             "roofline": roof, "cpu_baseline": cpu,
             "plan": {"kernels_per_step": fc.fc_plan_size(plan, 6), "signature": plan_sig,
@@ -927,6 +933,12 @@ def run_rules_gpu(args, rank, world, fc, torch, barrier, dist, dev, pk):
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = float(np.median(e2e_t))
     clk.stop()
+    planner = "host"
+    if name in ("tiny", "random", "large") and fc.fc_info(ctx, 7) == 1:
+        # planned on the device: only the query lists, the caller's table
+        # offsets and the variables' entropies were uploaded
+        planner = "device"
+        h2d = 4 * (len(off) + len(flat)) + 8 * len(toff) + 8 * db.n
 
     # dominant kernel: the per-level itemset count; algorithmic bytes = one
     # bitmap row of ceil(m/64) words per item of every candidate

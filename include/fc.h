@@ -118,7 +118,9 @@ void fc_free(fc_ctx *ctx);
  * 2 = sum of arities, 3 = device ordinal, 4 = instances that fit without
  * reallocating (see fc_reserve), 5 = appends so far, 6 = bits per value of
  * the columns the shared-memory histogram strategy reads (4 with the 4-bit
- * copy of option "codes4", else 8; 0 for a context from fc_load_bits).
+ * copy of option "codes4", else 8; 0 for a context from fc_load_bits),
+ * 7 = 1 when the last fc_count_batch was planned on the device (only its
+ * query lists, offsets and the entropies were uploaded), else 0.
  * -1 for a bad key. */
 int64_t fc_info(const fc_ctx *ctx, int32_t key);
 

@@ -559,6 +559,7 @@ extern "C" int64_t fc_info(const fc_ctx *c, int32_t key)
     case 4: return capacity_rows(c);
     case 5: return (int64_t)c->generation;
     case 6: return c->transactions ? 0 : (c->d_D4 && c->opt.codes4) ? 4 : 8;
+    case 7: return c->last_batch_on_device;
     default: return -1;
     }
 }

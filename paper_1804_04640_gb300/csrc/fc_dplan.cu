@@ -38,8 +38,8 @@ struct DPlanSummary {
     int32_t mid;        // tables the planner's large shape would hold whole (8192 < cells <= 16384)
     int32_t hist;       // histogram queries
     int64_t out_cells;  // cells of the packed tables (no caller offsets)
-    uint32_t cls_lo;    // span of the cost classes present (set to [max, 0] before planning)
-    uint32_t cls_hi;
+    uint32_t cls_lo_inv;  // span of the cost classes present: ~lo and hi (both zero before
+    uint32_t cls_hi;      // planning, an empty span)
 };
 
 namespace {
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(128) dplan_describe(DPlanParams P)
         if (n_hist) atomicAdd(&P.sum->hist, n_hist);
         if (n_mid) atomicAdd(&P.sum->mid, n_mid);
         if (lo <= hi) {
-            atomicMin(&P.sum->cls_lo, lo);
+            atomicMax(&P.sum->cls_lo_inv, ~lo);
             atomicMax(&P.sum->cls_hi, hi);
         }
     }
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(1024) dplan_finish(const DPlanParams P, int64_
     // enough histogram queries (the host planner splits rows otherwise)
     if (threadIdx.x == 0)
         s_bad = P.sum->bad || (int64_t)P.sum->mid * 64 > P.nq || P.sum->hist < P.min_hist ||
-                P.sum->cls_lo > P.sum->cls_hi;
+                ~P.sum->cls_lo_inv > P.sum->cls_hi;
     __syncthreads();
     if (s_bad) {
         if (threadIdx.x == 0) {
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(1024) dplan_finish(const DPlanParams P, int64_
     }
     // positions of the classes' items over the span present: ascending
     // class = descending cost
-    const uint32_t lo = P.sum->cls_lo, hi = P.sum->cls_hi;
+    const uint32_t lo = ~P.sum->cls_lo_inv, hi = P.sum->cls_hi;
     const int64_t n_items = block_scan<int32_t>(P.class_count + lo, (int64_t)(hi - lo) + 1, warp_sum);
     if (threadIdx.x == 0) {
         P.sum->n_items = (int32_t)n_items;
@@ -398,23 +398,28 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
     const size_t b_user = table_off ? round_up(sizeof(int64_t) * (nq + 1), 256) : 0;
     const size_t b_ent = round_up(sizeof(double) * c->n, 256);
     const size_t in_bytes = b_off + b_vars + b_user + b_ent;
-    uint8_t *h = stage_host(c, in_bytes);
+    // the pinned buffer also receives the summary and the status word at the end
+    static_assert(sizeof(DPlanSummary) + 2 * sizeof(int32_t) <= 256, "return area");
+    uint8_t *h = stage_host(c, in_bytes + 256);
     if (!h) return FC_OK;
+    DPlanSummary *h_sum = (DPlanSummary *)(h + in_bytes);
+    int32_t *h_status = (int32_t *)(h + in_bytes + round_up(sizeof(DPlanSummary), 8));
     std::memcpy(h, var_off, sizeof(int32_t) * (nq + 1));
     std::memcpy(h + b_off, vars + var_off[0], sizeof(int32_t) * nvars);
     if (table_off) std::memcpy(h + b_off + b_vars, table_off, sizeof(int64_t) * (nq + 1));
     std::memcpy(h + b_off + b_vars + b_user, c->entropy.data(), sizeof(double) * c->n);
 
-    // device layout: inputs | heads | QVars | items | classes | class counts |
-    // packed offsets | item count | counter | summary
+    // device layout: inputs | heads | QVars | items | classes | packed
+    // offsets | class counts | item count | counter | summary (the last four
+    // zeroed by one memset)
     const int64_t max_items = (int64_t)nq * std::min(o.window_max, kMaxWindows);
     const size_t o_qh = round_up(in_bytes, 256);
     const size_t o_qv = o_qh + round_up(sizeof(QHead) * nq, 256);
     const size_t o_it = o_qv + round_up(sizeof(QVar) * std::max(nvars, 1), 256);
     const size_t o_cl = o_it + round_up(sizeof(Item) * max_items, 256);
-    const size_t o_cc = o_cl + round_up(sizeof(uint32_t) * nq, 256);
-    const size_t o_sc = o_cc + round_up(sizeof(int32_t) * kClasses, 256);
-    const size_t o_ct = o_sc + round_up(sizeof(int64_t) * nq, 256);  // n_items_eff, next item (zeroed)
+    const size_t o_sc = o_cl + round_up(sizeof(uint32_t) * nq, 256);
+    const size_t o_cc = o_sc + round_up(sizeof(int64_t) * nq, 256);
+    const size_t o_ct = o_cc + round_up(sizeof(int32_t) * kClasses, 256);  // n_items_eff, next item
     const size_t o_sum = o_ct + 256;
     const size_t total = o_sum + round_up(sizeof(DPlanSummary), 256);
     cudaError_t e = c->dplan_buf.ensure(total);
@@ -423,11 +428,7 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
     e = cudaMemcpyAsync(d, h, in_bytes, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaEventRecord(c->stage[c->bank].ev, c->stream);
     // class counts, the item counters and the summary start from zero
-    if (e == cudaSuccess) e = cudaMemsetAsync(d + o_cc, 0, o_sc - o_cc, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d + o_ct, 0, total - o_ct, c->stream);
-    // the class span starts empty: lo = all ones, hi = 0
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(d + o_sum + offsetof(DPlanSummary, cls_lo), 0xFF, sizeof(uint32_t), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d + o_cc, 0, total - o_cc, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "device plan upload");
 
     DPlanParams P{};
@@ -482,10 +483,10 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
     if (!dtab) {
         if (!table_off) {
             // the packed size is known only after planning: read the summary first
-            DPlanSummary s{};
-            e = cudaMemcpyAsync(&s, P.sum, sizeof s, cudaMemcpyDeviceToHost, c->stream);
+            e = cudaMemcpyAsync(h_sum, P.sum, sizeof(DPlanSummary), cudaMemcpyDeviceToHost, c->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             if (e != cudaSuccess) return cuda_fail(e, "device plan summary");
+            const DPlanSummary s = *h_sum;
             if (s.bad || s.n_items == 0) return FC_OK;
             known_cells = s.out_cells;
             e = c->io[0].ensure(sizeof(int32_t) * std::max<int64_t>(s.out_cells, 1));
@@ -527,13 +528,14 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
         if (bytes > 0) e = cudaMemcpyAsync(tables, dtab, bytes, cudaMemcpyDeviceToHost, c->stream);
         if (e != cudaSuccess) return cuda_fail(e, "copy outputs");
     }
-    DPlanSummary s{};
-    int32_t st[2] = {0, 0};
-    e = cudaMemcpyAsync(&s, P.sum, sizeof s, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(st, c->d_status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
+    e = cudaMemcpyAsync(h_sum, P.sum, sizeof(DPlanSummary), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h_status, c->d_status, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->stage[c->bank].ev, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "device plan run");
-    if (st[0] != kStatusOk) return read_status(c, c->stream);  // reports (and clears) the status
+    const DPlanSummary s = *h_sum;
+    if (h_status[0] != kStatusOk) return read_status(c, c->stream);  // reports (and clears) the status
     if (s.bad || s.n_items == 0) return FC_OK;
     *done = true;
     return FC_OK;

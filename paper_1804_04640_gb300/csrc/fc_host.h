@@ -212,6 +212,8 @@ struct fc_ctx {
     int32_t R = 0;
     int64_t m_pad = 0, words = 0, wstride = 0;
     uint8_t *d_D = nullptr;
+    // 1 when the last fc_count_batch was planned on the device (fc_info key 7)
+    int32_t last_batch_on_device = 0;
     // D as 4-bit codes when every arity is at most 16 (else null): the
     // histogram kernel reads half the column bytes
     uint8_t *d_D4 = nullptr;

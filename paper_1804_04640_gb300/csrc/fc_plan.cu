@@ -1136,10 +1136,12 @@ extern "C" int fc_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, con
 {
     if (!c || (nq > 0 && !tables)) return fail(FC_ERR_ARG, "fc_count_batch: null argument");
     DevGuard g(c->device);
+    c->last_batch_on_device = 0;
     if (nq >= kPipelineQueries && var_off && vars && !c->transactions) {
         // planned on the device when every query counts in shared memory
         bool done = false;
         const int rc = device_count_batch(c, nq, var_off, vars, table_off, tables, &done);
+        c->last_batch_on_device = rc == FC_OK && done ? 1 : 0;
         if (rc != FC_OK || done) return rc;
         if (table_off && table_off[0] < 0) return fail(FC_ERR_ARG, "table_off must be non-negative");
         std::vector<int64_t> rel;

@@ -488,8 +488,10 @@ def test_device_planned_batches_match_host_planned():
     off, flat = fc.pack_lists(queries)
     fc.fc_set_option(ctx, "device_plan", 0)
     host_t, toff = fc.fc_count_batch(ctx, off, flat)
+    assert fc.fc_info(ctx, 7) == 0
     fc.fc_set_option(ctx, "device_plan", 1)
     dev_t, toff2 = fc.fc_count_batch(ctx, off, flat)
+    assert fc.fc_info(ctx, 7) == 1
     assert np.array_equal(toff, toff2)
     assert np.array_equal(dev_t, host_t)
     for q in range(0, len(queries), 97):
