@@ -789,10 +789,10 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
                                       "note": "one counted table per family (fc_plan_score)"}
 
     # ---- end to end through the host-buffer entry point
-    for _ in range(2):
+    for _ in range(3):
         e2e_call()
     e2e_t = []
-    for _ in range(max(3, min(steps, 10))):
+    for _ in range(max(5, min(steps, 50))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e2e_call()

@@ -52,11 +52,11 @@ struct DPlanParams {
     int32_t base0;            // var_off[0]
     const int64_t *user_off;  // nq + 1, or null (tables packed in query order)
     const int32_t *arity, *soff;
-    const double *entropy;
+    const float *entropy;
     int32_t n, nq;
-    double rows, chunks;
+    float rows, chunks;  // the cost model in FP32 (the FP64 pipe is slow)
     // cost model (femtoseconds) and the planner's limits
-    double hist_row, hist_var, flush, bitmap_node, bitmap_chunk, small_unit;
+    float hist_row, hist_var, flush, bitmap_node, bitmap_chunk, small_unit;
     int32_t bitmap_small, stage_slots, force_hist, window_max;
     int32_t small_cells;  // table area of the small launch shape
     int32_t max_cells;    // table area of the large shape
@@ -75,14 +75,14 @@ struct DPlanParams {
 // for the CTA (the per-query loops look them up once per variable).
 struct VarInfo {
     int32_t arity, soff;
-    double entropy;
+    float entropy;
 };
 
-__device__ __forceinline__ uint32_t cost_class_dev(double v)
+__device__ __forceinline__ uint32_t cost_class_dev(float v)
 {
-    if (!(v > 0.0)) v = 0.0;
-    const uint64_t b = (uint64_t)__double_as_longlong(v);
-    return ((1u << 14) - 1u) - (uint32_t)(b >> (52 - 3));
+    if (!(v > 0.0f)) v = 0.0f;
+    const uint32_t b = __float_as_uint(v);  // exponent and 3 mantissa bits: 1/8-octave classes
+    return ((1u << 14) - 1u) - (b >> (23 - 3));
 }
 
 // Cost of the bitmap strategy for a query of k <= kMaxBitmapK variables (its
@@ -93,19 +93,19 @@ __device__ __forceinline__ int arity_of(const DPlanParams &P, const VarInfo *sv,
     return P.stage_vars ? sv[v].arity : P.arity[v];
 }
 
-__device__ __forceinline__ double entropy_of(const DPlanParams &P, const VarInfo *sv, int v)
+__device__ __forceinline__ float entropy_of(const DPlanParams &P, const VarInfo *sv, int v)
 {
     return P.stage_vars ? sv[v].entropy : P.entropy[v];
 }
 
-__device__ double bitmap_cost(const DPlanParams &P, const VarInfo *sv, const QVar *v, int k)
+__device__ float bitmap_cost(const DPlanParams &P, const VarInfo *sv, const QVar *v, int k)
 {
-    if (k < 1 || k > kMaxBitmapK) return 1e300;
+    if (k < 1 || k > kMaxBitmapK) return 3e38f;
     QVar o[kMaxBitmapK];
     for (int t = 0; t < k; ++t) o[t] = v[t];
     for (int i = 1; i < k; ++i) {  // stable insertion sort by entropy
         const QVar x = o[i];
-        const double h = entropy_of(P, sv, x.var);
+        const float h = entropy_of(P, sv, x.var);
         int j = i - 1;
         while (j >= 0 && entropy_of(P, sv, o[j].var) > h) {
             o[j + 1] = o[j];
@@ -115,17 +115,16 @@ __device__ double bitmap_cost(const DPlanParams &P, const VarInfo *sv, const QVa
     }
     int slots = 0;
     for (int t = 1; t < k; ++t) slots += o[t].arity;
-    if (slots > P.stage_slots) return 1e300;
+    if (slots > P.stage_slots) return 3e38f;
     auto ok = [](int r) { return r >= 2 && r <= 5; };
     const bool small = P.bitmap_small && ((k == 2 && ok(o[0].arity) && ok(o[1].arity)) ||
                                           (k == 3 && ok(o[1].arity) && ok(o[2].arity)));
     if (small) {
-        const double units = k == 2 ? (double)o[0].arity * o[1].arity + o[0].arity + o[1].arity
-                                    : (double)o[0].arity * (1.0 + o[1].arity + o[2].arity +
-                                                            (double)o[1].arity * o[2].arity);
+        const float units = k == 2 ? (float)(o[0].arity * o[1].arity + o[0].arity + o[1].arity)
+                                   : (float)(o[0].arity * (1 + o[1].arity + o[2].arity + o[1].arity * o[2].arity));
         return P.chunks * (P.bitmap_chunk + units * P.small_unit);
     }
-    double nodes = 0.0, level = 1.0;
+    float nodes = 0.0f, level = 1.0f;
     for (int t = 0; t < k; ++t) {
         level *= o[t].arity;
         nodes += level;
@@ -170,18 +169,18 @@ __device__ int describe_one(const DPlanParams &P, const VarInfo *s_var, int32_t 
     }
     // strategy: the cost model of the host planner, in the small launch
     // shape; only the shared-memory strategies are taken here
-    const double hist = P.rows * (P.hist_row + (double)k_eff * P.hist_var) + (double)cells * P.flush;
+    const float hist = P.rows * (P.hist_row + (float)k_eff * P.hist_var) + (float)cells * P.flush;
     int s;
-    double cost;
+    float cost;
     int32_t nwin = 1;
     if (k_eff == 0) {
         s = kHist;
         cost = hist;
     } else if (k_eff == 1 && cells <= P.max_cells) {
         s = kMarginal;
-        cost = (double)cells * P.flush;
+        cost = (float)cells * P.flush;
     } else if (cells <= P.max_cells) {
-        if (!P.force_hist && bitmap_cost(P, s_var, out, k_eff) + (double)cells * P.flush < hist) return 2;
+        if (!P.force_hist && bitmap_cost(P, s_var, out, k_eff) + (float)cells * P.flush < hist) return 2;
         if (cells <= P.small_cells) {
             s = kHist;
             cost = hist;
@@ -191,7 +190,7 @@ __device__ int describe_one(const DPlanParams &P, const VarInfo *s_var, int32_t 
             nwin = (int32_t)((cells + P.small_cells - 1) / P.small_cells);
             if (nwin > P.window_max) return 4;
             s = kWindow;
-            cost = (double)nwin * P.rows * (P.hist_row + (double)k_eff * P.hist_var) * 2.0 + (double)cells * P.flush;
+            cost = (float)nwin * P.rows * (P.hist_row + (float)k_eff * P.hist_var) * 2.0f + (float)cells * P.flush;
         }
     } else {
         return 4;  // wide windows, global atomics, sort: host planner
@@ -396,7 +395,7 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
     const size_t b_off = round_up(sizeof(int32_t) * (nq + 1), 256);
     const size_t b_vars = round_up(sizeof(int32_t) * std::max(nvars, 1), 256);
     const size_t b_user = table_off ? round_up(sizeof(int64_t) * (nq + 1), 256) : 0;
-    const size_t b_ent = round_up(sizeof(double) * c->n, 256);
+    const size_t b_ent = round_up(sizeof(float) * c->n, 256);
     const size_t in_bytes = b_off + b_vars + b_user + b_ent;
     // the pinned buffer also receives the summary and the status word at the end
     static_assert(sizeof(DPlanSummary) + 2 * sizeof(int32_t) <= 256, "return area");
@@ -407,7 +406,8 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
     std::memcpy(h, var_off, sizeof(int32_t) * (nq + 1));
     std::memcpy(h + b_off, vars + var_off[0], sizeof(int32_t) * nvars);
     if (table_off) std::memcpy(h + b_off + b_vars, table_off, sizeof(int64_t) * (nq + 1));
-    std::memcpy(h + b_off + b_vars + b_user, c->entropy.data(), sizeof(double) * c->n);
+    float *h_ent = (float *)(h + b_off + b_vars + b_user);
+    for (int i = 0; i < c->n; ++i) h_ent[i] = (float)c->entropy[i];
 
     // device layout: inputs | heads | QVars | items | classes | packed
     // offsets | class counts | item count | counter | summary (the last four
@@ -436,19 +436,19 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
     P.vars = (const int32_t *)(d + b_off);
     P.base0 = var_off[0];
     P.user_off = table_off ? (const int64_t *)(d + b_off + b_vars) : nullptr;
-    P.entropy = (const double *)(d + b_off + b_vars + b_user);
+    P.entropy = (const float *)(d + b_off + b_vars + b_user);
     P.arity = c->d_arity;
     P.soff = c->d_soff;
     P.n = c->n;
     P.nq = nq;
-    P.rows = (double)c->m;
-    P.chunks = (double)((c->m + kChunkRows - 1) / kChunkRows);
-    P.hist_row = (double)o.hist_cost_row;
-    P.hist_var = (double)o.hist_cost_var;
-    P.flush = (double)o.flush_cost;
-    P.bitmap_node = (double)o.bitmap_cost;
-    P.bitmap_chunk = (double)o.bitmap_chunk_cost;
-    P.small_unit = (double)o.small_cost;
+    P.rows = (float)c->m;
+    P.chunks = (float)((c->m + kChunkRows - 1) / kChunkRows);
+    P.hist_row = (float)o.hist_cost_row;
+    P.hist_var = (float)o.hist_cost_var;
+    P.flush = (float)o.flush_cost;
+    P.bitmap_node = (float)o.bitmap_cost;
+    P.bitmap_chunk = (float)o.bitmap_chunk_cost;
+    P.small_unit = (float)o.small_cost;
     P.bitmap_small = o.bitmap_small;
     P.stage_slots = std::max(1, std::min(o.stage_slots, (c->max_smem_optin - 1024) /
                                                             (16 * std::max(32, std::min(256, o.bitmap_threads / 32 * 32)))));

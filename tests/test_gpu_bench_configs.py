@@ -59,8 +59,10 @@ def test_random_batch_as_benchmarked():
     want = _pool_map(orc.table, queries)
     for q, t in enumerate(want):
         assert np.array_equal(tables[toff[q]:toff[q + 1]].astype(np.int64), t), q
-    # the end-to-end call the bench times: host lists, the device planner,
-    # tables stored straight into a page-locked buffer, twice in a row
+    # the end-to-end call the bench times: host lists, planned on the device
+    # when the tuned cost model keeps every query in shared memory (the bench
+    # line's e2e.planner says which), tables stored straight into a
+    # page-locked buffer, twice in a row
     pinned = torch.empty(int(toff[-1]), dtype=torch.int32).pin_memory()
     for _ in range(2):
         pinned.fill_(-1)

@@ -486,6 +486,10 @@ def test_device_planned_batches_match_host_planned():
     orc = oracle.DB(db.D, db.arities)
     queries = random_queries(db.n, 6000, 1, 6, seed=72)
     off, flat = fc.pack_lists(queries)
+    # a cost model under which no query prefers the bitmap strategy (as the
+    # autotuner sets it on this kind of batch): the fast path's condition
+    for key in ("bitmap_cost", "bitmap_chunk_cost", "small_cost"):
+        fc.fc_set_option(ctx, key, 10 ** 9)
     fc.fc_set_option(ctx, "device_plan", 0)
     host_t, toff = fc.fc_count_batch(ctx, off, flat)
     assert fc.fc_info(ctx, 7) == 0
@@ -505,6 +509,7 @@ def test_device_planned_batches_match_host_planned():
         if pin:
             out = out.pin_memory()
         fc.fc_count_batch(ctx, off, flat, padded, out=out if pin else out.numpy())
+        assert fc.fc_info(ctx, 7) == 1
         got = out.numpy()
         for q in range(len(queries)):
             assert np.array_equal(got[padded[q]:padded[q] + cells[q]], host_t[toff[q]:toff[q + 1]])
@@ -514,11 +519,13 @@ def test_device_planned_batches_match_host_planned():
     rc = lib.fc_count_batch(ctx.ptr, len(queries), fc._ptr(off, fc._i32p), fc._ptr(flat, fc._i32p), None,
                             fc._ptr(packed))
     assert rc == fc.FC_OK, fc.fc_last_error()
+    assert fc.fc_info(ctx, 7) == 1
     assert np.array_equal(packed, host_t[: int(toff[-1])])
     # the host planner takes batches the fast path does not: a forced bitmap
     # strategy, and a table beyond the small shape's windows
     fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_BITMAP)
     bm_t, _ = fc.fc_count_batch(ctx, off, flat)
+    assert fc.fc_info(ctx, 7) == 0
     assert np.array_equal(bm_t, host_t)
     fc.fc_set_option(ctx, "strategy", fc.FC_STRAT_AUTO)
     wide = list(queries)
@@ -526,6 +533,7 @@ def test_device_planned_batches_match_host_planned():
     wide[17] = big
     o3, f3 = fc.pack_lists(wide)
     w_t, wto = fc.fc_count_batch(ctx, o3, f3)
+    assert fc.fc_info(ctx, 7) == 0
     assert np.array_equal(w_t[wto[17]:wto[18]].astype(np.int64), orc.table(big))
     assert np.array_equal(w_t[wto[18]:wto[19]], host_t[toff[18]:toff[19]])
     # an invalid query: the host planner's error, with its index
