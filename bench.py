@@ -792,7 +792,7 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
     for _ in range(3):
         e2e_call()
     e2e_t = []
-    for _ in range(max(5, min(steps, 50))):
+    for _ in range(max(5, min(steps, 50, int(2000.0 / max(ms, 1e-3))))):  # about 2 s at most
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e2e_call()
