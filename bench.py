@@ -412,13 +412,16 @@ def run_reference(args, rank: int, world: int):
     rate, sample = oracle_rate(args.workload, w, args.ref_seconds, cores)
     if args.workload in ("rules", "append"):
         cores = 1  # these oracle legs run on one thread
+    k = args.steps if args.steps is not None else 20
+    # each step a bounded sample, the whole run about a minute at most
+    per_step = max(0.05, min(args.ref_seconds / 4, 60.0 / max(1, args.warmup + k)))
     steps = []
-    for _ in range(args.warmup + args.steps):
-        steps.append(oracle_rate(args.workload, w, max(0.5, args.ref_seconds / 4), cores)[0])
-    value = statistics.median(steps[args.warmup:]) if args.steps else rate
+    for _ in range(args.warmup + k):
+        steps.append(oracle_rate(args.workload, w, per_step, cores)[0])
+    value = statistics.median(steps[args.warmup:]) if k else rate
     unit = UNITS[args.workload]
     line = {"impl": "reference", "metric": metric_of(args.workload),
-            "value": value, "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "value": value, "unit": unit, "n_gpus": world, "steps": k, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64/f64",
             "data": "synthetic (seeded)", "config": describe(args.workload, w),
             "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
@@ -501,9 +504,13 @@ def roofline(name: str, ms: float, work: dict, pk: dict, resident_bytes: int, pl
     # families, rules, append: byte-bound work
     achieved = work["alg_bytes"] / sec / 1e9
     if resident_bytes < L2_BYTES and name != "append":
-        return {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
-                "traffic": traffic, "peak_source": "measured by fc_probe_rate(FC_PROBE_L2_READ) on this GPU",
-                "duration": "whole step"}
+        r = {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+             "traffic": traffic, "peak_source": "measured by fc_probe_rate(FC_PROBE_L2_READ) on this GPU",
+             "duration": "whole step"}
+        if name == "families":
+            r["work"] = ("the columns of every variable set counted once, at the width the histogram keys "
+                         "read them (4 bits per value with the 4-bit columns)")
+        return r
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": traffic, "peak_source": f"{pk['src']} hbm_gbs", "duration": "whole step"}
 
@@ -625,7 +632,9 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
         outs = (torch.empty(units, dtype=torch.float32, device="cuda"),)
         nv, dmax = len(w["vars"]), min(w["max_parents"], len(w["vars"]) - 1)
         import math
-        work = {"alg_bytes": sum(math.comb(nv, sz) * sz for sz in range(1, dmax + 2)) * db.m}
+        # every variable set's columns, at the width the histogram keys read them
+        work = {"alg_bytes": sum(math.comb(nv, sz) * sz for sz in range(1, dmax + 2)) * db.m
+                * fc.fc_info(ctx, 6) // 8}
         pinned = torch.empty(units, dtype=torch.float32).pin_memory()
         h2d = fc.fc_plan_size(plan, 5)
         d2h = 4 * units
@@ -723,7 +732,8 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
         t_warm.append(e0.elapsed_time(e1))
     fc.fc_sync(ctx, stream)
     if steps is None:
-        steps = int(max(3, min(args.steps, 1000.0 / max(min(t_warm), 1e-3))))
+        cap = args.steps if args.steps is not None else 2000
+        steps = int(max(3, min(cap, 1000.0 / max(min(t_warm), 1e-3))))
 
     # ---- timed region: K steps, L2 flushed between steps, events on the launch stream
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -900,7 +910,7 @@ def run_rules_gpu(args, rank, world, fc, torch, barrier, dist, dev, pk):
         r = fc.fc_mine_rules(ctx, *w["args"])
     torch.cuda.synchronize()
     units = r["candidates"]
-    steps = min(args.steps, 50)
+    steps = args.steps if args.steps is not None else 50
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     dev_ns = []
@@ -998,7 +1008,9 @@ def run_append_gpu(args, rank, world, fc, torch, barrier, dist, dev, pk):
     D = np.ascontiguousarray(db.D)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
     hbm, peak_src = pk["hbm_gbs"], pk["src"]
-    steps = min(args.steps, 50)
+    # every step grows the database by a block: at most 50 steps (3.4 GB of D
+    # and bitmaps per 50 blocks at n = 64), whatever --steps asks
+    steps = min(args.steps, 50) if args.steps is not None else 50
     ctx = load_ctx(fc, args, D[:, :m0], db.arities)
     fc.fc_reserve(ctx, m0 + B * (args.warmup + steps + 1))
     block = torch.from_numpy(np.ascontiguousarray(D[:, m0:m0 + B])).cuda()
@@ -1153,7 +1165,9 @@ def relaunch_under_torchrun(n: int) -> int:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: as many as take about a second, 3 to 2000; "
+                         "given, exactly that many)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="random", choices=list(CONFIGS))
