@@ -70,3 +70,15 @@ def test_oracle_family_enumeration():
     assert len(fams) == 4 * 7
     assert (0, []) in fams and (3, [0, 1]) in fams and (1, [0, 2]) in fams
     assert all(c not in pa for c, pa in fams)
+
+
+def test_options_are_echoed_only_when_given():
+    """--option settings appear under config.options; without them the GPU
+    arm's config is the reference arm's (describe) unchanged."""
+    import argparse
+    w = bench.make_workload("tiny")
+    base = bench.describe("tiny", w)
+    assert bench.with_options(base, argparse.Namespace(option=[])) == base
+    got = bench.with_options(base, argparse.Namespace(option=["codes4=0", "device_plan=1"]))
+    assert got["options"] == ["codes4=0", "device_plan=1"]
+    assert {k: v for k, v in got.items() if k != "options"} == base
