@@ -582,9 +582,13 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
         pinned = torch.empty(int(toff[-1]), dtype=torch.int32).pin_memory()
         h2d = fc.fc_plan_size(plan, 5) + 4 * (len(off) + len(flat))
         d2h = 4 * int(toff[-1])
+        # the step's inputs in page-locked host memory, as the caller would hold them
+        p_off = torch.from_numpy(np.ascontiguousarray(off, dtype=np.int32)).pin_memory()
+        p_flat = torch.from_numpy(np.ascontiguousarray(flat, dtype=np.int32)).pin_memory()
+        p_toff = torch.from_numpy(np.ascontiguousarray(toff, dtype=np.int64)).pin_memory()
 
         def e2e_call():
-            fc.fc_count_batch(ctx, off, flat, toff, out=pinned)
+            fc.fc_count_batch(ctx, p_off, p_flat, p_toff, out=pinned)
 
         if name == "random" and per_query_n > 0:
             per_plans, pq_outs = [], []
@@ -811,10 +815,10 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
     clk.stop()
     planner = "host"
     if name in ("tiny", "random", "large") and fc.fc_info(ctx, 7) == 1:
-        # planned on the device: only the query lists, the caller's table
-        # offsets and the variables' entropies were uploaded
+        # planned on the device: only the query lists and the caller's table
+        # offsets are uploaded (the entropies stay on the device)
         planner = "device"
-        h2d = 4 * (len(off) + len(flat)) + 8 * len(toff) + 8 * db.n
+        h2d = 4 * (len(off) + len(flat)) + 8 * len(toff)
 
     plan_sig = "-"
     if strategies is not None:
@@ -943,12 +947,6 @@ def run_rules_gpu(args, rank, world, fc, torch, barrier, dist, dev, pk):
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = float(np.median(e2e_t))
     clk.stop()
-    planner = "host"
-    if name in ("tiny", "random", "large") and fc.fc_info(ctx, 7) == 1:
-        # planned on the device: only the query lists, the caller's table
-        # offsets and the variables' entropies were uploaded
-        planner = "device"
-        h2d = 4 * (len(off) + len(flat)) + 8 * len(toff) + 8 * db.n
 
     # dominant kernel: the per-level itemset count; algorithmic bytes = one
     # bitmap row of ceil(m/64) words per item of every candidate

@@ -391,23 +391,23 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
     if (max_cells <= kSmallCells) return FC_OK;
     const int grid = c->num_sms * kSmallCtas;
 
-    // host inputs into the pinned staging buffer, one upload
+    // The caller's lists go into the pinned staging buffer and up in one
+    // copy (reading them in place from page-locked memory measured slower:
+    // the describe kernel's chains of dependent loads then cross the link).
+    // The staging buffer also receives the summary and the status word at
+    // the end.
     const size_t b_off = round_up(sizeof(int32_t) * (nq + 1), 256);
     const size_t b_vars = round_up(sizeof(int32_t) * std::max(nvars, 1), 256);
     const size_t b_user = table_off ? round_up(sizeof(int64_t) * (nq + 1), 256) : 0;
-    const size_t b_ent = round_up(sizeof(float) * c->n, 256);
-    const size_t in_bytes = b_off + b_vars + b_user + b_ent;
-    // the pinned buffer also receives the summary and the status word at the end
+    const size_t in_bytes = b_off + b_vars + b_user;
     static_assert(sizeof(DPlanSummary) + 2 * sizeof(int32_t) <= 256, "return area");
     uint8_t *h = stage_host(c, in_bytes + 256);
-    if (!h) return FC_OK;
+    if (!h || !c->d_entropy_f) return FC_OK;
     DPlanSummary *h_sum = (DPlanSummary *)(h + in_bytes);
     int32_t *h_status = (int32_t *)(h + in_bytes + round_up(sizeof(DPlanSummary), 8));
     std::memcpy(h, var_off, sizeof(int32_t) * (nq + 1));
     std::memcpy(h + b_off, vars + var_off[0], sizeof(int32_t) * nvars);
     if (table_off) std::memcpy(h + b_off + b_vars, table_off, sizeof(int64_t) * (nq + 1));
-    float *h_ent = (float *)(h + b_off + b_vars + b_user);
-    for (int i = 0; i < c->n; ++i) h_ent[i] = (float)c->entropy[i];
 
     // device layout: inputs | heads | QVars | items | classes | packed
     // offsets | class counts | item count | counter | summary (the last four
@@ -436,7 +436,7 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
     P.vars = (const int32_t *)(d + b_off);
     P.base0 = var_off[0];
     P.user_off = table_off ? (const int64_t *)(d + b_off + b_vars) : nullptr;
-    P.entropy = (const float *)(d + b_off + b_vars + b_user);
+    P.entropy = c->d_entropy_f;
     P.arity = c->d_arity;
     P.soff = c->d_soff;
     P.n = c->n;

@@ -513,6 +513,19 @@ def test_device_planned_batches_match_host_planned():
         got = out.numpy()
         for q in range(len(queries)):
             assert np.array_equal(got[padded[q]:padded[q] + cells[q]], host_t[toff[q]:toff[q + 1]])
+    # the caller's lists in page-locked memory
+    p_off = torch.from_numpy(np.ascontiguousarray(off, dtype=np.int32)).pin_memory()
+    p_flat = torch.from_numpy(np.ascontiguousarray(flat, dtype=np.int32)).pin_memory()
+    p_to = torch.from_numpy(np.ascontiguousarray(padded, dtype=np.int64)).pin_memory()
+    for pin_out in (False, True):
+        out = torch.full((int(padded[-1]),), -5, dtype=torch.int32)
+        if pin_out:
+            out = out.pin_memory()
+        fc.fc_count_batch(ctx, p_off, p_flat, p_to, out=out if pin_out else out.numpy())
+        assert fc.fc_info(ctx, 7) == 1
+        got = out.numpy()
+        for q in range(len(queries)):
+            assert np.array_equal(got[padded[q]:padded[q] + cells[q]], host_t[toff[q]:toff[q + 1]])
     # packed offsets through the C ABI (table_off NULL)
     lib = fc.load_library()
     packed = np.zeros(int(toff[-1]), dtype=np.int32)
