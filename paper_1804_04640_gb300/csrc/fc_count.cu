@@ -808,6 +808,89 @@ __device__ __forceinline__ void key_rows_swar_nib_k(const CountParams &P, const 
     }
 }
 
+// key_rows_swar_nib_k for variables of at most 4 states each: consecutive
+// variables are first paired on the packed nibbles (a * r + b stays below 16:
+// one IMAD for eight rows, no carry between nibbles), each pair is unpacked
+// to bytes once, and two pairs combine on the bytes (at most 256 joint
+// states) before entering the key lanes, so one PRMT + IMAD per two rows
+// carries the digit of up to four variables.
+template <int K>
+__device__ __forceinline__ void key_rows_swar_nib4_k(const CountParams &P, const QVar *vs, int64_t r0, int64_t r1,
+                                                     int lshift, int32_t *tab0)
+{
+    constexpr int NC = (K + 3) / 4;  // byte digits: runs of up to four variables
+    char *smem = reinterpret_cast<char *>(tab0);
+    const uint32_t base_bytes = (uint32_t)((threadIdx.x & ((1 << lshift) - 1)) << 2);
+    const int sshift = 2 + lshift;
+    const uint32_t init = base_bytes | (base_bytes << 16);
+    const int64_t pad4 = P.m_pad / 2;
+    const uint4 *col[K];
+    uint32_t mul[K];
+    uint32_t st[NC];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        col[t] = reinterpret_cast<const uint4 *>(P.D4 + (int64_t)vs[t].var * pad4 + r0 / 2);
+        mul[t] = (uint32_t)vs[t].arity;
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) st[c] = (uint32_t)vs[min(K, 4 * c + 4) - 1].stride << sshift;
+    const int64_t nfull = (r1 - r0) >> 10;
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = threadIdx.x; u < (nfull << 5); u += blockDim.x) {
+        const int64_t vec = ((u >> 5) << 5) + lane;  // 16-byte vector (32 rows) in the range
+        uint32_t acc[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] = init;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            uint32_t g[8];
+#pragma unroll
+            for (int t0 = 4 * c; t0 < (K < 4 * c + 4 ? K : 4 * c + 4); t0 += 2) {
+                const bool two = t0 + 1 < (K < 4 * c + 4 ? K : 4 * c + 4);
+                const uint4 x = __ldg(col[t0] + vec);
+                uint32_t w[4] = {x.x, x.y, x.z, x.w};
+                uint32_t pr = mul[t0];
+                if (two) {
+                    const uint4 y = __ldg(col[t0 + 1] + vec);
+                    const uint32_t v[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) w[i] = w[i] * mul[t0 + 1] + v[i];
+                    pr *= mul[t0 + 1];
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t ev = w[i] & 0x0F0F0F0Fu, od = (w[i] >> 4) & 0x0F0F0F0Fu;
+                    g[2 * i] = t0 == 4 * c ? ev : g[2 * i] * pr + ev;
+                    g[2 * i + 1] = t0 == 4 * c ? od : g[2 * i + 1] * pr + od;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                acc[2 * i] += __byte_perm(g[i], 0u, 0x4240) * st[c];
+                acc[2 * i + 1] += __byte_perm(g[i], 0u, 0x4341) * st[c];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            atomicAdd(reinterpret_cast<int *>(smem + (acc[j] & 0xFFFFu)), 1);
+            atomicAdd(reinterpret_cast<int *>(smem + (acc[j] >> 16)), 1);
+        }
+    }
+    for (int64_t p = r0 + (nfull << 10) + threadIdx.x; p < r1; p += blockDim.x) {
+        uint32_t key = base_bytes;
+#pragma unroll
+        for (int t = 0; t < K; ++t) key += (uint32_t)P.D[(int64_t)vs[t].var * P.m_pad + p] * ((uint32_t)vs[t].stride << sshift);
+        atomicAdd(reinterpret_cast<int *>(smem + key), 1);
+    }
+}
+
+__device__ __forceinline__ bool all_arities_at_most_4(const QVar *vs, int k)
+{
+    for (int t = 0; t < k; ++t)
+        if (vs[t].arity > 4) return false;
+    return true;
+}
+
 // Groups of three when every run of three consecutive variables has at most
 // 256 joint states, else of two (always valid for arities <= 16).
 __device__ __forceinline__ bool nib_groups_of_three(const QVar *vs, int k)
@@ -822,6 +905,15 @@ __device__ __forceinline__ void key_rows_swar_dispatch(const CountParams &P, con
                                                        int64_t r1, int lshift, int32_t *tab0)
 {
     if constexpr (kNib) {
+        if (k >= 2 && k <= 6 && all_arities_at_most_4(vs, k)) {
+            switch (k) {
+            case 2: key_rows_swar_nib4_k<2>(P, vs, r0, r1, lshift, tab0); return;
+            case 3: key_rows_swar_nib4_k<3>(P, vs, r0, r1, lshift, tab0); return;
+            case 4: key_rows_swar_nib4_k<4>(P, vs, r0, r1, lshift, tab0); return;
+            case 5: key_rows_swar_nib4_k<5>(P, vs, r0, r1, lshift, tab0); return;
+            default: key_rows_swar_nib4_k<6>(P, vs, r0, r1, lshift, tab0); return;
+            }
+        }
         const bool g3 = nib_groups_of_three(vs, k);
         switch (k) {
         case 1: key_rows_swar_nib_k<1, 1>(P, vs, r0, r1, lshift, tab0); return;

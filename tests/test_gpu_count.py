@@ -561,20 +561,23 @@ def test_device_planned_batches_match_host_planned():
     assert np.array_equal(again, host_t)
 
 
-@pytest.mark.parametrize("m", [4096 * 3 + 17, 40_000])
-def test_codes4_matches_byte_columns(m):
+@pytest.mark.parametrize("m,ar", [(4096 * 3 + 17, [16, 2, 3, 16, 5, 1, 7, 16, 4]),
+                                  (40_000, [16, 2, 3, 16, 5, 1, 7, 16, 4]),
+                                  (4096 * 5 + 999, [4, 2, 3, 4, 4, 1, 2, 3, 4])])
+def test_codes4_matches_byte_columns(m, ar):
     """On a database whose arities are all <= 16 the histogram strategy reads
     the 4-bit copy of the columns (option codes4).  Its tables equal the byte
     columns' and the oracle's: arity 16 (the top code 15 in a nibble), arity
-    1, ragged tails that end inside a 32-row group, and the copy repacked by
-    appends that start at odd rows."""
+    1, ragged tails that end inside a 32-row group, the copy repacked by
+    appends that start at odd rows, and (all arities <= 4) the keys that pair
+    variables on the packed nibbles."""
     rng = np.random.default_rng(m)
     n = 9
-    ar = np.array([16, 2, 3, 16, 5, 1, 7, 16, 4], dtype=np.int32)
+    ar = np.array(ar, dtype=np.int32)
     D = np.stack([rng.integers(0, a, size=m) for a in ar]).astype(np.uint8)
-    D[0, -1] = 15
-    D[3, :50] = 15
-    queries = random_queries(n, 400, 1, 4, seed=m + 1) + [[0, 3], [0, 3, 7], [5], [5, 0], list(range(6))]
+    D[0, -1] = ar[0] - 1
+    D[3, :50] = ar[3] - 1
+    queries = random_queries(n, 400, 1, 6, seed=m + 1) + [[0, 3], [0, 3, 7], [5], [5, 0], list(range(6))]
     queries = [q for q in queries if int(np.prod(ar[q])) <= 16384]
     ctx = fc.fc_load(D, ar)
     assert fc.fc_info(ctx, 6) == 4
