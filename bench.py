@@ -582,10 +582,11 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
         pinned = torch.empty(int(toff[-1]), dtype=torch.int32).pin_memory()
         h2d = fc.fc_plan_size(plan, 5) + 4 * (len(off) + len(flat))
         d2h = 4 * int(toff[-1])
-        # the step's inputs in page-locked host memory, as the caller would hold them
-        p_off = torch.from_numpy(np.ascontiguousarray(off, dtype=np.int32)).pin_memory()
-        p_flat = torch.from_numpy(np.ascontiguousarray(flat, dtype=np.int32)).pin_memory()
-        p_toff = torch.from_numpy(np.ascontiguousarray(toff, dtype=np.int64)).pin_memory()
+        # the step's inputs in page-locked host memory, as the caller would
+        # hold them (numpy views of pinned tensors: no per-call conversion)
+        pin_in = [torch.from_numpy(np.ascontiguousarray(a, dtype=t)).pin_memory()
+                  for a, t in ((off, np.int32), (flat, np.int32), (toff, np.int64))]
+        p_off, p_flat, p_toff = (t.numpy() for t in pin_in)
 
         def e2e_call():
             fc.fc_count_batch(ctx, p_off, p_flat, p_toff, out=pinned)
