@@ -428,7 +428,8 @@ int fc_sync(fc_ctx *ctx, void *stream);
  *   "support_warps", "support_sets_per_warp", "support_part_words"
  *                       launch shape of the itemset-support kernels
  *   "zero_copy"         1 (default) = when the output buffer of fc_count,
- *                       fc_count_batch or fc_score_batch is page-locked host
+ *                       fc_count_batch or fc_score_batch (or every output
+ *                       buffer fc_pairs_all is given) is page-locked host
  *                       memory (cudaHostAlloc, or cudaHostRegister with
  *                       mapping) and no output cell is accumulated, the
  *                       kernels store the outputs into it directly instead

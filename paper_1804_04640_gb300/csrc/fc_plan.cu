@@ -824,7 +824,7 @@ void *device_view(const void *h, size_t bytes)
 // copied afterwards.
 bool stores_only(const fc_plan *p)
 {
-    if (p->kind == kPlanScore) return true;
+    if (p->kind == kPlanScore || p->kind == kPlanPairs) return true;  // pairs: the extraction kernel stores
     return p->kind == kPlanCount && !p->zero_tables && p->sort_jobs.empty();
 }
 
@@ -837,10 +837,18 @@ int run_to_host(fc_plan *p, void *h0, size_t b0, void *h1, size_t b1, void *h2, 
     void *hs[3] = {h0, h1, h2};
     size_t bs[3] = {b0, b1, b2};
     void *ds[3] = {nullptr, nullptr, nullptr};
-    if (c->opt.zero_copy && stores_only(p) && b1 == 0 && b2 == 0) {
-        void *dv = device_view(h0, b0);
-        if (dv) {
-            int rc = run_plan(p, dv, nullptr, nullptr, c->stream, false);
+    if (c->opt.zero_copy && stores_only(p)) {
+        // every output the caller wants is page-locked: the kernels store into it
+        void *dv[3] = {nullptr, nullptr, nullptr};
+        bool all = false;
+        for (int i = 0; i < 3; ++i) {
+            if (!hs[i] || bs[i] == 0) continue;
+            dv[i] = device_view(hs[i], bs[i]);
+            all = dv[i] != nullptr;
+            if (!all) break;
+        }
+        if (all) {
+            int rc = run_plan(p, dv[0], dv[1], dv[2], c->stream, false);
             if (rc != FC_OK) return rc;
             return read_status(c, c->stream);
         }

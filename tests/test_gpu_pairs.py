@@ -96,3 +96,27 @@ def test_pairs_plan_replay_and_chunked_accumulation():
         fc.fc_plan_run(plan, out_t, out_m, stream=cur)
         fc.fc_sync(ctx, cur)
         assert np.array_equal(out_t.cpu().numpy(), t1)
+
+
+def test_pairs_into_page_locked_outputs():
+    """fc_pairs_all into page-locked buffers: the extraction kernel stores the
+    tables and the MI straight into them (option zero_copy); the results
+    equal the copied ones, for both outputs, either one alone, and with the
+    option off."""
+    torch = pytest.importorskip("torch")
+    db = random_dag_database(40, 100_003, 2, 4, 2, 0.5, seed=9)
+    ctx = fc.fc_load(db.D, db.arities)
+    t0, m0 = fc.fc_pairs_all(ctx)
+    lib = fc.load_library()
+    for zc in (1, 0):
+        fc.fc_set_option(ctx, "zero_copy", zc)
+        for want_t, want_m in ((True, True), (True, False), (False, True)):
+            pt = torch.full((len(t0),), -7, dtype=torch.int32).pin_memory() if want_t else None
+            pm = torch.full((len(m0),), -7.0, dtype=torch.float32).pin_memory() if want_m else None
+            rc = lib.fc_pairs_all(ctx.ptr, fc._ptr(pt), fc._ptr(pm))
+            assert rc == fc.FC_OK, fc.fc_last_error()
+            if want_t:
+                assert np.array_equal(pt.numpy(), t0)
+            if want_m:
+                assert np.array_equal(pm.numpy(), m0)
+    fc.fc_set_option(ctx, "zero_copy", 1)
