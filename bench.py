@@ -847,7 +847,7 @@ def measure(name: str, args, rank: int, world: int, torch, fc, dist, dev, barrie
         if strategies is not None:
             rec["plan"]["strategies"] = dict(zip(STRATEGY_NAMES, strategies))
             rec["plan"]["cost_model_fs"] = {k: fc.fc_get_option(ctx, k) for k in
-                                            ("bitmap_cost", "bitmap_chunk_cost", "small_cost", "hist_cost_row",
+                                            ("bitmap_cost", "bitmap_chunk_cost", "small_cost", "small3_cost", "hist_cost_row",
                                              "hist_cost_var")}
         rec.update(extra)
     del plan, ctx

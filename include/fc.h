@@ -422,7 +422,7 @@ int fc_sync(fc_ctx *ctx, void *stream);
  *   "stage_slots"       bitmap rows a warp of the bitmap kernel stages per chunk
  *   "bitmap_small"      1 = register-blocked bitmap path for 2-3 small variables
  *   "sort_min_cells"    tables at least this large take the sort strategy
- *   "bitmap_cost", "bitmap_chunk_cost", "small_cost", "hist_cost_row",
+ *   "bitmap_cost", "bitmap_chunk_cost", "small_cost", "small3_cost", "hist_cost_row",
  *   "hist_cost_var", "flush_cost"
  *                       cost-model coefficients (femtoseconds) used by AUTO
  *   "support_warps", "support_sets_per_warp", "support_part_words"

@@ -56,7 +56,7 @@ struct DPlanParams {
     int32_t n, nq;
     float rows, chunks;  // the cost model in FP32 (the FP64 pipe is slow)
     // cost model (femtoseconds) and the planner's limits
-    float hist_row, hist_var, flush, bitmap_node, bitmap_chunk, small_unit;
+    float hist_row, hist_var, flush, bitmap_node, bitmap_chunk, small_unit, small_unit3;
     int32_t bitmap_small, stage_slots, force_hist, window_max;
     int32_t small_cells;  // table area of the small launch shape
     int32_t max_cells;    // table area of the large shape
@@ -122,7 +122,7 @@ __device__ float bitmap_cost(const DPlanParams &P, const VarInfo *sv, const QVar
     if (small) {
         const float units = k == 2 ? (float)(o[0].arity * o[1].arity + o[0].arity + o[1].arity)
                                    : (float)(o[0].arity * (1 + o[1].arity + o[2].arity + o[1].arity * o[2].arity));
-        return P.chunks * (P.bitmap_chunk + units * P.small_unit);
+        return P.chunks * units * (k == 2 ? P.small_unit : P.small_unit3);
     }
     float nodes = 0.0f, level = 1.0f;
     for (int t = 0; t < k; ++t) {
@@ -449,6 +449,7 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
     P.bitmap_node = (float)o.bitmap_cost;
     P.bitmap_chunk = (float)o.bitmap_chunk_cost;
     P.small_unit = (float)o.small_cost;
+    P.small_unit3 = (float)o.small3_cost;
     P.bitmap_small = o.bitmap_small;
     P.stage_slots = std::max(1, std::min(o.stage_slots, (c->max_smem_optin - 1024) /
                                                             (16 * std::max(32, std::min(256, o.bitmap_threads / 32 * 32)))));

@@ -105,7 +105,8 @@ struct Options {
     int64_t flush_cost = 160;
     // register-blocked bitmap path (2-3 variables of arity 2..5): per work
     // unit (cell or state row) per 4096-row chunk
-    int64_t small_cost = 12000;
+    int64_t small_cost = 12000;   // per work unit of a two-variable table
+    int64_t small3_cost = 12000;  // per work unit of a three-variable table
     int32_t bitmap_small = 1;
     int32_t stage_slots = 16;         // bitmap rows a warp stages per chunk
     int32_t bitmap_threads = 256;
@@ -123,6 +124,10 @@ struct Options {
     // context holds one (every arity <= 16)
     int32_t codes4 = 1;
 };
+
+// Smallest synchronous count batch that is pipelined in parts or planned on
+// the device.
+constexpr int32_t kDevicePlanMinQueries = 4096;
 
 // Host arrays of the count planner, kept by the context between plan builds
 // so that a steady stream of batches allocates (and page-faults) nothing.

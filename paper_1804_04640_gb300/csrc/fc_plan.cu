@@ -151,7 +151,9 @@ QPlan choose(const fc_ctx *c, QVar *v, int k, int64_t cells, int32_t smem_cells,
     const double hist = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) + flush;
     double bitmap = bm ? chunks * ((double)o.bitmap_chunk_cost + nodes * o.bitmap_cost) + flush : 1e300;
     if (bm && o.bitmap_small && small_ok(ord, k))
-        bitmap = chunks * ((double)o.bitmap_chunk_cost + small_units(ord, k) * o.small_cost) + flush;
+        // the fitted unit cost of the register-blocked path includes its
+        // per-chunk overhead (no separate chunk term)
+        bitmap = chunks * small_units(ord, k) * (double)(k == 2 ? o.small_cost : o.small3_cost) + flush;
     const double gatomic = rows * (o.hist_cost_row + (double)k * o.hist_cost_var) * 2.0 + (double)cells * 4.0;
     // one pass over the rows per window of the cell range, scalar keys
     const double windows = (double)((cells + win_cells - 1) / win_cells);
@@ -1061,7 +1063,7 @@ namespace {
 // Batches at least this large run a synchronous call in parts (10,000
 // count queries: 0.68 ms per call in two parts, 0.76 ms in three equal ones,
 // whose smaller plans use fewer host threads and launch more often).
-constexpr int32_t kPipelineQueries = 4096;
+constexpr int32_t kPipelineQueries = kDevicePlanMinQueries;
 
 // A synchronous call in parts of its batch: each part after the first is
 // planned on the host while the previous part's kernels run, and each part's

@@ -40,6 +40,7 @@ const OptDesc kOpts[] = {
     {"hist_cost_var", &Options::hist_cost_var, nullptr, 0, (int64_t)1 << 40},
     {"flush_cost", &Options::flush_cost, nullptr, 0, (int64_t)1 << 40},
     {"small_cost", &Options::small_cost, nullptr, 0, (int64_t)1 << 40},
+    {"small3_cost", &Options::small3_cost, nullptr, 0, (int64_t)1 << 40},
     {"bitmap_small", nullptr, &Options::bitmap_small, 0, 1},
     {"stage_slots", nullptr, &Options::stage_slots, 1, 64},
     {"bitmap_threads", nullptr, &Options::bitmap_threads, 32, 256},
@@ -238,11 +239,13 @@ extern "C" int fc_autotune(fc_ctx *c, int32_t budget_ms)
     }
     // register-blocked path: batches of 2- and 3-variable queries over
     // variables of arity 2..5, timed with the bitmap strategy forced;
-    // small_cost = (time - chunk costs) / (chunks x work units)
+    // small_cost (2 variables) and small3_cost (3) = time / (chunks x work
+    // units), fitted apart and with the path's per-chunk overhead folded in
+    // (the tree walk's chunk cost, fitted above, does not carry over)
     std::vector<int32_t> small_vars;
     for (int v = 0; v < c->n; ++v)
         if (c->arity[v] >= 2 && c->arity[v] <= 5) small_vars.push_back(v);
-    double num = 0.0, den = 0.0;
+    double num[4] = {0, 0, 0, 0}, den[4] = {0, 0, 0, 0};
     for (int k = 2; k <= 3 && (int)small_vars.size() >= k; ++k) {
         std::vector<int32_t> off{0}, vars;
         double units = 0.0;
@@ -279,13 +282,14 @@ extern "C" int fc_autotune(fc_ctx *c, int32_t budget_ms)
         }
         if (all) {
             const double tf = time_plan(p, out.p, 3) * 1e12;
-            num += std::max(0.0, tf - (double)nq * chunks * (double)c->opt.bitmap_chunk_cost);
-            den += units * chunks;
+            num[k] += tf;
+            den[k] += units * chunks;
         }
         out.release();
         fc_plan_free(p);
     }
-    if (den > 0.0) c->opt.small_cost = (int64_t)std::max(1.0, num / den);
+    if (den[2] > 0.0) c->opt.small_cost = (int64_t)std::max(1.0, num[2] / den[2]);
+    if (den[3] > 0.0) c->opt.small3_cost = (int64_t)std::max(1.0, num[3] / den[3]);
     return FC_OK;
 }
 
@@ -301,13 +305,14 @@ extern "C" int fc_autotune_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, 
     DevGuard g(c->device);
     const Options base = c->opt;
     const double scales[] = {0.25, 0.5, 1.0, 2.0, 4.0, -1.0};  // -1: bitmap never chosen
-    double best_t = 1e30;
-    Options best = base;
+    double best_t = 1e30, no_bitmap_t = 1e30;
+    Options best = base, no_bitmap = base;
     for (double sc : scales) {
         c->opt = base;
         c->opt.bitmap_cost = sc < 0 ? ((int64_t)1 << 50) : (int64_t)std::max(1.0, base.bitmap_cost * sc);
         c->opt.bitmap_chunk_cost = sc < 0 ? ((int64_t)1 << 50) : (int64_t)(base.bitmap_chunk_cost * sc);
         c->opt.small_cost = sc < 0 ? ((int64_t)1 << 50) : (int64_t)std::max(1.0, base.small_cost * sc);
+        c->opt.small3_cost = sc < 0 ? ((int64_t)1 << 50) : (int64_t)std::max(1.0, base.small3_cost * sc);
         fc_plan *p = nullptr;
         if ((rc = fc_plan_count(c, nq, var_off, vars, nullptr, &p)) != FC_OK) {
             c->opt = base;
@@ -326,7 +331,18 @@ extern "C" int fc_autotune_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, 
             best_t = t;
             best = c->opt;
         }
+        if (sc < 0) {
+            no_bitmap_t = t;
+            no_bitmap = c->opt;
+        }
     }
+    // A synchronous fc_count_batch of such a batch is planned on the device
+    // only when no query takes the bitmap strategy, which saves the host
+    // planner's ~30 ns per query; a setting with bitmap queries must beat the
+    // one without by more than that to be kept.
+    const bool device_plannable = base.device_plan && base.strategy == FC_STRAT_AUTO && base.shape_auto &&
+                                  base.window_wide && c->m < (1 << 19) && nq >= kDevicePlanMinQueries;
+    if (device_plannable && no_bitmap_t - best_t < 3e-5 * (double)nq) best = no_bitmap;
     c->opt = best;
     return FC_OK;
 }

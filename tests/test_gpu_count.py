@@ -488,7 +488,7 @@ def test_device_planned_batches_match_host_planned():
     off, flat = fc.pack_lists(queries)
     # a cost model under which no query prefers the bitmap strategy (as the
     # autotuner sets it on this kind of batch): the fast path's condition
-    for key in ("bitmap_cost", "bitmap_chunk_cost", "small_cost"):
+    for key in ("bitmap_cost", "bitmap_chunk_cost", "small_cost", "small3_cost"):
         fc.fc_set_option(ctx, key, 10 ** 9)
     fc.fc_set_option(ctx, "device_plan", 0)
     host_t, toff = fc.fc_count_batch(ctx, off, flat)
