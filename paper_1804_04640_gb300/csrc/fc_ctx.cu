@@ -120,16 +120,6 @@ void fc::run_host_threads(fc_ctx *c, int n, const std::function<void(int)> &f)
 
 namespace {
 
-// The entropies as FP32 on the device, for the device planner.
-int upload_entropy(fc_ctx *c)
-{
-    if (c->transactions) return FC_OK;
-    if (!c->d_entropy_f) FC_CUDA(cudaMalloc(&c->d_entropy_f, sizeof(float) * std::max(c->n, 1)), "cudaMalloc entropies");
-    std::vector<float> f(c->entropy.begin(), c->entropy.end());
-    FC_CUDA(cudaMemcpy(c->d_entropy_f, f.data(), sizeof(float) * c->n, cudaMemcpyHostToDevice), "upload entropies");
-    return FC_OK;
-}
-
 int finish_load(fc_ctx *c)
 {
     // marginal counts per (variable, state) and entropies (DFS order, Sec. 3.2)
@@ -151,7 +141,8 @@ int finish_load(fc_ctx *c)
         }
     }
     c->mark.assign(c->n, 0u);
-    return upload_entropy(c);
+    c->entropy_stale = true;
+    return FC_OK;
 }
 
 int new_ctx(fc_ctx **out, int32_t n, int64_t m)
@@ -455,7 +446,8 @@ int finish_append(fc_ctx *c, int64_t m_total, bool read_marginals = true)
             }
             c->entropy[i] = h;
         }
-    return upload_entropy(c);
+    c->entropy_stale = true;
+    return FC_OK;
 }
 
 }  // namespace

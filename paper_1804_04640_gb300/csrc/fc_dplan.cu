@@ -402,7 +402,18 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
     const size_t in_bytes = b_off + b_vars + b_user;
     static_assert(sizeof(DPlanSummary) + 2 * sizeof(int32_t) <= 256, "return area");
     uint8_t *h = stage_host(c, in_bytes + 256);
-    if (!h || !c->d_entropy_f) return FC_OK;
+    if (!h) return FC_OK;
+    if (c->entropy_stale) {  // the FP32 entropies after a load or an append
+        if (!c->d_entropy_f && cudaMalloc(&c->d_entropy_f, sizeof(float) * std::max(c->n, 1)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            c->d_entropy_f = nullptr;
+            return FC_OK;  // the host planner takes the batch
+        }
+        std::vector<float> f(c->entropy.begin(), c->entropy.end());
+        cudaError_t e = cudaMemcpy(c->d_entropy_f, f.data(), sizeof(float) * c->n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "upload entropies");
+        c->entropy_stale = false;
+    }
     DPlanSummary *h_sum = (DPlanSummary *)(h + in_bytes);
     int32_t *h_status = (int32_t *)(h + in_bytes + round_up(sizeof(DPlanSummary), 8));
     std::memcpy(h, var_off, sizeof(int32_t) * (nq + 1));

@@ -220,8 +220,10 @@ struct fc_ctx {
     // 1 when the last fc_count_batch was planned on the device (fc_info key 7)
     int32_t last_batch_on_device = 0;
     // the variables' entropies in FP32 on the device (the device planner's
-    // cost model), refreshed at load and after every append
+    // cost model), uploaded by the first device-planned batch after a load or
+    // an append (entropy_stale)
     float *d_entropy_f = nullptr;
+    bool entropy_stale = true;
     // D as 4-bit codes when every arity is at most 16 (else null): the
     // histogram kernel reads half the column bytes
     uint8_t *d_D4 = nullptr;
