@@ -143,29 +143,79 @@ __device__ int describe_one(const DPlanParams &P, const VarInfo *s_var, int32_t 
     // the host planner reports every invalid query; here it only stops the fast path
     if (a < P.base0 || b > P.var_off[P.nq] || k < 0 || k > P.n || k > 48) return 1;
     const int32_t *vars = P.vars + (a - P.base0);
-    int64_t cells = 1;
-    for (int t = 0; t < k; ++t) {
-        const int v = vars[t];
-        if (v < 0 || v >= P.n) return 1;
-        cells *= arity_of(P, s_var, v);
-        if (cells > INT32_MAX) return 1;
-        for (int u = 0; u < t; ++u)
-            if (vars[u] == v) return 1;
-    }
     const int64_t base = (int64_t)a - P.base0;
-    if (P.user_off && (P.user_off[q] < 0 || P.user_off[q + 1] - P.user_off[q] < cells)) return 1;
-    // QVars: strides of the caller's order (last fastest), arity-1 variables dropped
     QVar *out = P.qv + base;
-    int64_t stride = 1;
+    int64_t cells = 1;
     int k_eff = 0;
-    for (int t = k - 1; t >= 0; --t)
-        if (arity_of(P, s_var, vars[t]) > 1) ++k_eff;
-    int w = k_eff;
-    for (int t = k - 1; t >= 0; --t) {
-        const int v = vars[t];
-        const int r = arity_of(P, s_var, v);
-        if (r > 1) out[--w] = QVar{v, (int32_t)stride, r, P.stage_vars ? s_var[v].soff : P.soff[v]};
-        stride *= r;
+    // the cost model reads the QVars back: a copy in registers for short lists
+    constexpr int kFast = 8;
+    QVar fq[kFast];
+    const bool fast = k <= kFast;
+    if (fast) {
+        // every variable of the list loaded at once (one memory latency, not k)
+        int32_t lv[kFast];
+#pragma unroll
+        for (int t = 0; t < kFast; ++t) lv[t] = t < k ? vars[t] : 0;
+        int ar[kFast];
+        bool bad = false;
+#pragma unroll
+        for (int t = 0; t < kFast; ++t) {
+            ar[t] = 1;
+            if (t < k) {
+                bad |= lv[t] < 0 || lv[t] >= P.n;
+                if (!bad) ar[t] = arity_of(P, s_var, lv[t]);
+#pragma unroll
+                for (int u = 0; u < t; ++u) bad |= lv[u] == lv[t];
+            }
+        }
+        if (bad) return 1;
+        bool over = false;
+#pragma unroll
+        for (int t = 0; t < kFast; ++t) {
+            cells *= ar[t];
+            over |= cells > INT32_MAX;
+            if (over) cells = (int64_t)INT32_MAX + 1;  // no int64 overflow on the next product
+        }
+        if (over) return 1;
+        if (P.user_off && (P.user_off[q] < 0 || P.user_off[q + 1] - P.user_off[q] < cells)) return 1;
+        // QVars: strides of the caller's order (last fastest), arity-1 variables dropped
+#pragma unroll
+        for (int t = 0; t < kFast; ++t) k_eff += t < k && ar[t] > 1 ? 1 : 0;
+        int64_t stride = 1;
+        int w = k_eff;
+#pragma unroll
+        for (int t = kFast - 1; t >= 0; --t) {
+            if (t < k && ar[t] > 1) {
+                const QVar x{lv[t], (int32_t)stride, ar[t], P.stage_vars ? s_var[lv[t]].soff : P.soff[lv[t]]};
+                --w;
+#pragma unroll
+                for (int j = 0; j < kFast; ++j)
+                    if (j == w) fq[j] = x;
+                out[w] = x;
+            }
+            stride *= ar[t];
+        }
+    } else {
+        for (int t = 0; t < k; ++t) {
+            const int v = vars[t];
+            if (v < 0 || v >= P.n) return 1;
+            cells *= arity_of(P, s_var, v);
+            if (cells > INT32_MAX) return 1;
+            for (int u = 0; u < t; ++u)
+                if (vars[u] == v) return 1;
+        }
+        if (P.user_off && (P.user_off[q] < 0 || P.user_off[q + 1] - P.user_off[q] < cells)) return 1;
+        // QVars: strides of the caller's order (last fastest), arity-1 variables dropped
+        int64_t stride = 1;
+        for (int t = k - 1; t >= 0; --t)
+            if (arity_of(P, s_var, vars[t]) > 1) ++k_eff;
+        int w = k_eff;
+        for (int t = k - 1; t >= 0; --t) {
+            const int v = vars[t];
+            const int r = arity_of(P, s_var, v);
+            if (r > 1) out[--w] = QVar{v, (int32_t)stride, r, P.stage_vars ? s_var[v].soff : P.soff[v]};
+            stride *= r;
+        }
     }
     // strategy: the cost model of the host planner, in the small launch
     // shape; only the shared-memory strategies are taken here
@@ -180,7 +230,7 @@ __device__ int describe_one(const DPlanParams &P, const VarInfo *s_var, int32_t 
         s = kMarginal;
         cost = (float)cells * P.flush;
     } else if (cells <= P.max_cells) {
-        if (!P.force_hist && bitmap_cost(P, s_var, out, k_eff) + (float)cells * P.flush < hist) return 2;
+        if (!P.force_hist && bitmap_cost(P, s_var, fast ? fq : out, k_eff) + (float)cells * P.flush < hist) return 2;
         if (cells <= P.small_cells) {
             s = kHist;
             cost = hist;
@@ -370,6 +420,18 @@ __global__ void dplan_items(const DPlanParams P)
     }
 }
 
+// The planner's summary and the status word into the caller's pinned
+// return area (one small kernel instead of two copies).
+__global__ void dplan_return(const DPlanSummary *sum, const int32_t *status, DPlanSummary *h_sum,
+                             int32_t *h_status)
+{
+    if (threadIdx.x == 0) {
+        *h_sum = *sum;
+        h_status[0] = status[0];
+        h_status[1] = status[1];
+    }
+}
+
 }  // namespace
 
 // Plans and runs a count batch on the device (see the top of this file).
@@ -540,9 +602,16 @@ int device_count_batch(fc_ctx *c, int32_t nq, const int32_t *var_off, const int3
         if (bytes > 0) e = cudaMemcpyAsync(tables, dtab, bytes, cudaMemcpyDeviceToHost, c->stream);
         if (e != cudaSuccess) return cuda_fail(e, "copy outputs");
     }
-    e = cudaMemcpyAsync(h_sum, P.sum, sizeof(DPlanSummary), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h_status, c->d_status, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    DPlanSummary *z_sum = (DPlanSummary *)device_view(h_sum, sizeof(DPlanSummary));
+    int32_t *z_status = z_sum ? (int32_t *)device_view(h_status, 2 * sizeof(int32_t)) : nullptr;
+    if (z_sum && z_status) {
+        dplan_return<<<1, 32, 0, c->stream>>>(P.sum, c->d_status, z_sum, z_status);
+        e = cudaGetLastError();
+    } else {
+        e = cudaMemcpyAsync(h_sum, P.sum, sizeof(DPlanSummary), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_status, c->d_status, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(c->stage[c->bank].ev, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "device plan run");
